@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Benchmark of the event-parallel parton shower on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic events
+(the paper's workload is itself generated, so synthetic inputs are the
+workload): LO matrix element, the plain per-cycle shower (one launch per veto
+cycle, host all-done check), validation, observables (Durham y23..y56, 1-T,
+rho_H) and histograms.  Default workload: 10^6 LEP events at sqrt(s) = 91.2
+GeV, alpha_s(m_Z) = 0.118, t_C = 1 GeV^2, seed 2, 128 parton slots.
+
+Prints one JSON line (rank 0).  `--impl reference` times the oracle (the plain
+serial CPU implementation) on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "showered events/sec on 1 GB300 (10^6 LEP events) vs plain GPU; p50/p99 job latency"
+UNIT = "events/s"
+
+# Algorithmic FP64 work of the veto algorithm as the oracle computes it, in
+# DFMA-equivalent operations per unit (+, -, x and a fused a*b+c count 1;
+# division, square root, log and exp count their measured cost on this GPU
+# relative to one DFMA: 6.6, 9.6, 31, 17).  Units are counted exactly by the
+# kernel: dipoles evaluated, trials, winners and accepted emissions.
+OPS_PER_DIPOLE = 65.0     # Q^2, z+-, ln(z+/z-)
+OPS_PER_TRIAL = 61.0      # c, t r^(1/c) via log and exp, comparison
+OPS_PER_WINNER = 168.0    # z inversion, y, alpha_s(t), P / P^over, veto
+OPS_PER_EMISSION = 206.0  # azimuth, transverse frame, dipole map
+FP64_PEAK_DFMA_PER_S = 5.03e11  # measured DFMA throughput of this GB300 (pipe probe)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gaps", choices=["gaps", "reference"])
+    ap.add_argument("--events", type=int, default=1_000_000)
+    ap.add_argument("--capacity", type=int, default=128)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle events for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload_config(args, world):
+    return {"workload": f"LEP e+e- -> q qbar, sqrt(s)=91.2 GeV, alpha_s(mZ)=0.118, t_C=1 GeV^2, "
+                        f"{args.events} events per GPU, seed {args.seed}, {args.capacity} parton slots, "
+                        f"plain per-cycle shower + observables + histograms",
+            "events_per_gpu": args.events, "capacity": args.capacity, "seed": args.seed,
+            "shower_form": "plain (one launch per veto cycle, host all-done check)",
+            "parallelism": f"event ranges, {world} GPU(s), no collective on the data path",
+            "l2": "flushed (512 MiB write) before every timed step; the event record is also larger than L2"}
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="gaps_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------- CPU oracle
+def oracle_rate(seed, n_events, capacity, threads, first_event=0):
+    from oracle import oracle as O
+    p = O.make_params(seed=seed, capacity=capacity)
+    t0 = time.perf_counter()
+    O.run(p, first_event, n_events, threads=threads, want_obs=True, want_hist=True)
+    dt = time.perf_counter() - t0
+    return n_events / dt, dt
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores as the reference arm: every step showers
+    a bounded sample of the same workload (same seed, event ids continuing
+    from step to step)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.lib()
+    cores = host_cores()
+    sample = max(1000, args.cpu_sample // 2)
+    for w in range(args.warmup):
+        oracle_rate(args.seed, sample // 10, args.capacity, cores, first_event=w * sample)
+    times = []
+    for k in range(args.steps):
+        _, dt = oracle_rate(args.seed, sample, args.capacity, cores, first_event=k * sample)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * sample / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (generated events; the paper's workload is itself generated)",
+            "config": workload_config(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} events per step of the same workload (seed {args.seed}), "
+                                       f"event ranges split over {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2403_08692_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    g.load()
+    dev = torch.device("cuda", local_rank)
+    p = g.make_params(seed=args.seed)
+    n = args.events
+    ws = g.Workspace(n, args.capacity, first_event=rank * n, device=dev)
+    hist_dev = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device=dev)
+    stats_dev = torch.zeros(16, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.generate_me(p, ws, stream)
+        rc, launches, kms = g.shower_timed(p, ws, g.SHOWER_PLAIN, stream)
+        g.validate(p, ws, stream)
+        g.observables(p, ws, stream)
+        g.histograms(p, ws, hist_dev, stream)
+        return launches, kms
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        hist_dev.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms, launches_total, kernel_ms_total = [], 0, 0.0
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        hist_dev.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches, kms = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        launches_total += launches
+        kernel_ms_total += kms
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # per-event work units of one pass (identical every step)
+    g.reduce_stats(ws, stats_dev, stream)
+    st = g.Stats.from_buffer_copy(stats_dev.cpu().numpy().tobytes()[:len(bytes(g.Stats()))])
+    ops_per_pass = (OPS_PER_DIPOLE * st.sum_dipoles + OPS_PER_TRIAL * st.sum_trials +
+                    OPS_PER_WINNER * st.sum_winners + OPS_PER_EMISSION * st.sum_emissions)
+    launches_per_pass = launches_total / args.steps
+    kernel_s_per_launch = kernel_ms_total / 1e3 / launches_total
+    achieved_tflops = 2.0 * ops_per_pass / (kernel_ms_total / 1e3 / args.steps) / 1e12
+    peak_tflops = 2.0 * FP64_PEAK_DFMA_PER_S / 1e12
+
+    # end to end through the C ABI with host buffers: params in, histograms and
+    # statistics out, every step
+    host_hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.run(p, ws, host_hist, g.SHOWER_PLAIN, stream)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * n * len(e2e_times) / sum(e2e_times)
+
+    value = world * n * args.steps / (total_ms / 1e3)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, dt = oracle_rate(args.seed, args.cpu_sample, args.capacity, cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} events of the same workload (seed {args.seed}), full "
+                         f"pipeline (ME, shower, validation, observables, histograms), event ranges over "
+                         f"{cores} threads, {dt:.1f} s wall"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (generated events; the paper's workload is itself generated)",
+        "config": workload_config(args, world),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48,
+                "d2h_bytes_per_step": 8 * g.HIST_DOUBLES + len(bytes(g.Stats())),
+                "api": "gaps_run (parameters from host, histograms and statistics back to host)"},
+        "gpu_launches": int(args.steps * 4 + launches_total),
+        "roofline": {"bound": "alu", "kernel": "k_step_plain (fused veto cycle)",
+                     "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "peak_source": "FP64 DFMA throughput measured on this GB300 by a pipe probe "
+                                    "(MEASURED_PEAKS.json has no FP64 entry)",
+                     "work_model": "FP64 DFMA-equivalent ops of the oracle's formulas per dipole, trial, "
+                                   "winner and emission, x2 flops",
+                     "launches_per_pass": launches_per_pass,
+                     "avg_launch_ms": kernel_s_per_launch * 1e3},
+        "clocks": clocks,
+        "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
+                   "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,
+                                      "winners": st.sum_winners, "emissions": st.sum_emissions},
+                   "max_steps": st.max_steps, "mean_partons": st.sum_partons / max(1, st.n_events)},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

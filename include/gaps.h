@@ -1,0 +1,207 @@
+/* gaps.h -- C ABI of the event-parallel parton-shower library (sm_103a).
+ *
+ * The library implements the event-parallel Sudakov veto algorithm of
+ * Seymour & Sule, "An Algorithm to Parallelise Parton Showers on a GPU"
+ * (Sec. 2, Fig. 2, App. C): many independent e+e- -> q qbar events are
+ * showered at once, every veto cycle running for all events in lock-step.
+ * Around it sit the LO matrix element that creates the events (App. B) and
+ * the observables computed on the finished events (Sec. 3.1: Durham jet
+ * rates, thrust, heavy-jet mass) with their histograms.
+ *
+ * Memory model.  The caller owns all device memory: one workspace of
+ * gaps_workspace_bytes(n_events, capacity) bytes, 256-byte aligned, holds the
+ * structure-of-arrays event records and every per-event scalar, laid out as
+ * gaps_workspace_layout() reports.  No compute entry point allocates, frees
+ * or keeps device memory between calls, so the workspace may come from any
+ * allocator (PyTorch's caching allocator in the Python binding).  Host
+ * pointers are only read or written during the call.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Compute calls are asynchronous on that stream unless
+ * stated otherwise; their host arguments may be reused as soon as the call
+ * returns.
+ *
+ * Errors.  Every call returns GAPS_OK (0) or a negative gaps_status code;
+ * gaps_strerror() names it.  Invalid arguments are reported before any work
+ * is enqueued.  A CUDA launch or copy failure returns GAPS_ERR_CUDA and the
+ * CUDA error string is available from gaps_last_cuda_error().
+ *
+ * Random numbers.  Every draw is Philox4x32-10 (Salmon et al., SC'11) keyed
+ * by the 64-bit seed, with counter (event id, veto cycle, slot, purpose), so
+ * an event's history depends only on (seed, event id) and never on the
+ * launch configuration, the shower form, or the other events in the batch.
+ */
+#ifndef GAPS_H
+#define GAPS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gaps_status {
+  GAPS_OK = 0,
+  GAPS_ERR_INVALID = -1,    /* bad parameters, sizes or pointers */
+  GAPS_ERR_CUDA = -2,       /* a CUDA call failed */
+  GAPS_ERR_STEP_LIMIT = -3, /* some event hit max_steps veto cycles */
+  GAPS_ERR_NO_DEVICE = -4   /* no usable sm_103 device */
+} gaps_status;
+
+/* Physics parameters as the paper states them: sqrt(s) = 91.2 GeV for LEP
+ * (Sec. 1, Sec. 3), alpha_s(m_Z) = 0.118 and t_C = 1 (Fig. 4 caption; t_C in
+ * GeV^2), the number of quark flavours drawn by the matrix element (App. B,
+ * random(1, 5)), and the Philox seed. */
+typedef struct gaps_params {
+  double sqrt_s;        /* centre-of-mass energy in GeV, > 0 */
+  double alphas_mz;     /* strong coupling at the Z mass, > 0 */
+  double t_cutoff;      /* shower cutoff t_C in GeV^2, 0 < t_C < s/4, alpha_s(t_C) finite */
+  uint64_t seed;        /* Philox key */
+  int32_t n_flavours;   /* 1..5 */
+  int32_t fixed_alphas; /* 0: one-loop running alpha_s(t); 1: alpha_s fixed at alpha_s(m_Z) */
+  int32_t max_steps;    /* veto cycles allowed per event (>= 1); more sets the step-limit status */
+  int32_t reserved;     /* must be 0 */
+} gaps_params;
+
+/* One batch of events inside a caller-owned device workspace.  Event j of
+ * the batch has id first_event + j (the Philox counter's event word). */
+typedef struct gaps_batch {
+  void* workspace;      /* device pointer, 256-byte aligned, gaps_workspace_bytes() long */
+  int64_t n_events;     /* 0 .. 2^31-1 */
+  int32_t capacity;     /* parton slots per event, 4..255; the paper uses 50 (App. C) */
+  uint32_t first_event; /* id of the batch's first event */
+} gaps_batch;
+
+/* Byte offsets, from the workspace base, of every array in the workspace.
+ * Parton arrays are slot-major, [capacity][n_events]: element (slot i, event
+ * e) is at index i * n_events + e, so a warp of consecutive events reads one
+ * contiguous segment per slot. */
+typedef struct gaps_layout {
+  int64_t px, py, pz, e;  /* double [capacity][n_events], GeV */
+  int64_t flav;           /* int8   [capacity][n_events]: PDG id, 21 = gluon */
+  int64_t col, acol;      /* int16  [capacity][n_events]: colour / anticolour line, 0 = none */
+  int64_t link;           /* uint8  [2][capacity][n_events]: colour partner slot on side 0
+                             (colour line) and side 1 (anticolour line), 255 = none */
+  int64_t t;              /* double [n_events]: evolution scale t (GeV^2) */
+  int64_t weight;         /* double [n_events]: matrix-element weight (pb) */
+  int64_t hash;           /* uint64 [n_events]: FNV-1a of the veto decisions */
+  int64_t n_partons;      /* int32  [n_events] */
+  int64_t status;         /* int32  [n_events]: 0 active, 1 done, 2 overflow, 3 step limit */
+  int64_t n_steps;        /* int32  [n_events]: veto cycles run */
+  int64_t n_emissions;    /* int32  [n_events] */
+  int64_t n_winners;      /* int32  [n_events]: cycles with a trial above t_C */
+  int64_t n_trials;       /* int32  [n_events]: trial emissions generated */
+  int64_t n_dipoles;      /* int32  [n_events]: dipoles evaluated (Q^2 >= 4 t_C), over all cycles */
+  int64_t next_colour;    /* int32  [n_events] */
+  int64_t me_flavour;     /* int32  [n_events] */
+  int64_t valid;          /* int32  [n_events]: validation bits, 0 = valid */
+  int64_t obs;            /* double [6][n_events]: y23, y34, y45, y56, 1-T, rho_H (-1 = undefined) */
+  int64_t counters;       /* uint64 [16]: device counters (word 0 = finished events) */
+  int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
+  int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
+  int64_t total_bytes;
+} gaps_layout;
+
+/* Event status values. */
+enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3 };
+
+/* Histograms: GAPS_N_OBS observables x GAPS_HIST_ROW bins (underflow, 100
+ * bins, overflow) x (sum w, sum w^2, entries), double.  Binning: log10 y23,
+ * y34, y45, y56 on [-4.3, -0.3]; 1-T and rho_H on [0, 0.5]. */
+enum { GAPS_N_OBS = 6, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102 };
+#define GAPS_HIST_DOUBLES (GAPS_N_OBS * GAPS_HIST_ROW * 3)
+
+/* Totals over a batch, reduced on the device. */
+typedef struct gaps_stats {
+  int64_t n_events;
+  int64_t n_done, n_overflow, n_step_limit, n_invalid;
+  int64_t sum_steps, max_steps, sum_trials, sum_winners, sum_emissions, sum_partons, sum_dipoles;
+  int64_t launches;  /* shower launches made by the shower call of gaps_run */
+  double sum_weight;
+  double sum_weight2;
+} gaps_stats;
+
+/* Shower forms for gaps_shower(). */
+enum {
+  GAPS_SHOWER_PLAIN = 0 /* one launch per veto cycle over all events, host all-done check (App. C) */
+};
+
+/* ---------------------------------------------------------------- sizing */
+
+/* Bytes of workspace for a batch; 0 if the sizes are out of range. */
+size_t gaps_workspace_bytes(int64_t n_events, int32_t capacity);
+/* Fill *out with the layout of a workspace for these sizes. */
+int gaps_workspace_layout(int64_t n_events, int32_t capacity, gaps_layout* out);
+/* GAPS_OK if the parameters are physical (see gaps_params). */
+int gaps_check_params(const gaps_params* params);
+
+/* ------------------------------------------------------------- hot path */
+
+/* App. B: draw each event's flavour, cos(theta) and phi, set the quark and
+ * antiquark back to back at E = sqrt(s)/2, and the weight w = n_f * 2 *
+ * d sigma / d cos(theta) in pb (LO gamma/Z with interference).  Also the
+ * shower's initial state (App. C listing, main program): t = s, two partons
+ * on one colour line, status active.  Asynchronous. */
+int gaps_generate_me(const gaps_params* params, const gaps_batch* batch, void* stream);
+
+/* Sec. 2 / App. C: run the veto algorithm until every event has reached the
+ * cutoff (or overflowed its capacity, or hit max_steps).  Each cycle selects,
+ * per event, the winning trial emission over every colour-connected dipole
+ * and matching splitting kernel (Eq. A.6), checks the cutoff, applies the
+ * veto (Eq. A.8, A.9) and performs the accepted splitting.  mode =
+ * GAPS_SHOWER_PLAIN.  Synchronises the stream once per cycle (the host
+ * all-done check).  *launches_out (may be NULL) receives the number of
+ * cycle launches.  Returns GAPS_ERR_STEP_LIMIT if any event stopped at
+ * max_steps (the other events are complete). */
+int gaps_shower(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
+                void* stream);
+
+/* gaps_shower that also measures the shower kernels: *kernel_ms_out (may be
+ * NULL) receives the summed device time of the cycle launches, timed with
+ * CUDA events recorded on `stream` around every launch. */
+int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
+                      double* kernel_ms_out, void* stream);
+
+/* One veto cycle of the plain form for every active event (one launch). */
+int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* stream);
+
+/* Validation of the finished record (the paper's "Validate Events" stage):
+ * sets valid bits 1 momentum not conserved to 1e-10 GeV, 2 a parton off
+ * shell (|p^2| > 1e-10 E^2), 4 non-positive energy, 8 broken colour flow,
+ * 16 flavour imbalance, 32 non-finite momentum.  Asynchronous. */
+int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream);
+
+/* Sec. 3.1: Durham y23..y56 (E-scheme), thrust 1-T (exact) and heavy-jet
+ * mass rho_H for every event that reached the cutoff; -1 where undefined.
+ * Asynchronous. */
+int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* stream);
+
+/* Sec. 3.2 (atomic histogramming): add the batch's observables, weighted by
+ * the ME weight, to hist_device (GAPS_HIST_DOUBLES doubles, device memory,
+ * not cleared by this call).  Only events with status GAPS_DONE and valid ==
+ * 0 are filled.  Asynchronous. */
+int gaps_histograms(const gaps_params* params, const gaps_batch* batch, double* hist_device,
+                    void* stream);
+
+/* Reduce the batch's per-event counters into *stats_device (device memory,
+ * one gaps_stats).  Asynchronous. */
+int gaps_reduce_stats(const gaps_batch* batch, gaps_stats* stats_device, void* stream);
+
+/* The whole pipeline through host buffers: ME, shower (mode), validation,
+ * observables, histograms and statistics, then copies the histograms into
+ * host_hist (GAPS_HIST_DOUBLES doubles) and the statistics into
+ * *host_stats (may be NULL), and synchronises the stream.  The histogram
+ * and statistics accumulators live in the workspace and are cleared first. */
+int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, double* host_hist,
+             gaps_stats* host_stats, void* stream);
+
+/* --------------------------------------------------------------- misc */
+const char* gaps_strerror(int status);
+const char* gaps_last_cuda_error(void);
+/* Library version as major * 10000 + minor * 100 + patch. */
+int gaps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAPS_H */

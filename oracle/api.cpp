@@ -44,7 +44,7 @@ void run_range(const oracle_params& p, uint32_t first_event, int64_t begin, int6
       r.n_emissions = ev.n_emissions;
       r.n_winners = ev.n_winners;
       r.valid = valid;
-      r.pad = 0;
+      r.n_dipoles = ev.n_dipoles;
     }
     if (mom) {
       double* dst = mom + j * p.capacity * 4;

@@ -47,7 +47,7 @@ class Params(C.Structure):
 EVENT_DTYPE = np.dtype([
     ("weight", "f8"), ("t_first", "f8"), ("t_final", "f8"), ("hash", "u8"), ("n_trials", "i8"),
     ("me_flavour", "i4"), ("n_partons", "i4"), ("status", "i4"), ("n_steps", "i4"),
-    ("n_emissions", "i4"), ("n_winners", "i4"), ("valid", "i4"), ("pad", "i4"),
+    ("n_emissions", "i4"), ("n_winners", "i4"), ("valid", "i4"), ("n_dipoles", "i4"),
 ])
 assert EVENT_DTYPE.itemsize == 72
 

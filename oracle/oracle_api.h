@@ -46,7 +46,7 @@ typedef struct oracle_event_out {
   int32_t n_emissions;
   int32_t n_winners; /* cycles with a trial above t_C */
   int32_t valid;     /* validation error bits (0 = valid) */
-  int32_t pad;
+  int32_t n_dipoles; /* dipoles evaluated (colour-connected, Q^2 >= 4 t_C), summed over cycles */
 } oracle_event_out;
 
 /* Status codes of an event. */

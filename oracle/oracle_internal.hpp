@@ -27,6 +27,7 @@ struct Event {
   int n_emissions = 0;
   int n_winners = 0;
   int64_t n_trials = 0;
+  int n_dipoles = 0;
   uint64_t hash = 0;
   int next_colour = 0;
 };

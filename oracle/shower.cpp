@@ -112,6 +112,7 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
   ev.status = 0;
   ev.n_steps = ev.n_emissions = ev.n_winners = 0;
   ev.n_trials = 0;
+  ev.n_dipoles = 0;
   ev.t_first = 0.0;
 
   while (ev.status == 0) {
@@ -133,6 +134,7 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
         if (q2 < 4.0 * tc) continue;  // no phase space above the cutoff
         const double zp = 0.5 * (1.0 + std::sqrt(1.0 - 4.0 * tc / q2));
         const double zm = 1.0 - zp;
+        ++ev.n_dipoles;
         KernelRef kernels[8];
         const int nk = kernels_for(ev.partons[i].flav, p.n_flavours, kernels);
         for (int kappa = 0; kappa < nk; ++kappa) {

@@ -1,0 +1,14 @@
+"""Event-parallel parton shower on GB300 (sm_103a).
+
+A from-scratch implementation of the event-parallel Sudakov veto algorithm of
+Seymour & Sule, "An Algorithm to Parallelise Parton Showers on a GPU": the LO
+e+e- -> q qbar matrix element, the final-state dipole shower run for millions
+of events at once, and the Durham / thrust / heavy-jet-mass observables with
+their histograms.  The compute path is the CUDA library libgaps.so (C ABI in
+include/gaps.h); this package is its thin Python binding.
+"""
+from .gaps import (  # noqa: F401
+    ACTIVE, DONE, OVERFLOW, STEP_LIMIT, SHOWER_PLAIN, HIST_DOUBLES, N_OBS, HIST_ROW,
+    GapsError, Params, Stats, Workspace, check_params, generate_me, histograms, layout, load, shower_timed,
+    make_params, observables, reduce_stats, run, shower, shower_step, validate, workspace_bytes,
+)

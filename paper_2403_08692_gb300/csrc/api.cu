@@ -1,0 +1,320 @@
+// C ABI entry points (include/gaps.h): argument checks, workspace layout,
+// launch sequencing and the host all-done loop of the plain shower form.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "gaps_launch.hpp"
+
+namespace gaps {
+
+namespace {
+
+thread_local char g_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e) {
+  std::snprintf(g_cuda_error, sizeof(g_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return GAPS_ERR_CUDA;
+}
+
+constexpr int64_t kAlign = 256;
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool sizes_ok(int64_t n_events, int32_t capacity) {
+  return n_events >= 0 && n_events <= 0x7fffffffLL && capacity >= 4 && capacity <= 255;
+}
+
+void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  const int64_t pc = static_cast<int64_t>(cap) * n;
+  L->px = take(8 * pc);
+  L->py = take(8 * pc);
+  L->pz = take(8 * pc);
+  L->e = take(8 * pc);
+  L->flav = take(pc);
+  L->col = take(2 * pc);
+  L->acol = take(2 * pc);
+  L->link = take(2 * pc);
+  L->t = take(8 * n);
+  L->weight = take(8 * n);
+  L->hash = take(8 * n);
+  L->n_partons = take(4 * n);
+  L->status = take(4 * n);
+  L->n_steps = take(4 * n);
+  L->n_emissions = take(4 * n);
+  L->n_winners = take(4 * n);
+  L->n_trials = take(4 * n);
+  L->n_dipoles = take(4 * n);
+  L->next_colour = take(4 * n);
+  L->me_flavour = take(4 * n);
+  L->valid = take(4 * n);
+  L->obs = take(8 * 6 * n);
+  L->counters = take(8 * 16);
+  L->hist = take(8 * GAPS_HIST_DOUBLES);
+  L->stats = take(sizeof(gaps_stats));
+  L->total_bytes = off;
+}
+
+int check_batch(const gaps_batch* b) {
+  if (!b || !sizes_ok(b->n_events, b->capacity)) return GAPS_ERR_INVALID;
+  if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % kAlign) != 0) return GAPS_ERR_INVALID;
+  if (static_cast<uint64_t>(b->first_event) + static_cast<uint64_t>(b->n_events) > 0x100000000ull)
+    return GAPS_ERR_INVALID;
+  return GAPS_OK;
+}
+
+}  // namespace
+
+DevParams make_dev_params(const gaps_params& p) {
+  DevParams d{};
+  d.sqrt_s = p.sqrt_s;
+  d.s = p.sqrt_s * p.sqrt_s;
+  d.tc = p.t_cutoff;
+  d.alphas_mz = p.alphas_mz;
+  d.nf = p.n_flavours;
+  d.fixed = p.fixed_alphas ? 1 : 0;
+  d.max_steps = p.max_steps;
+  d.b0 = (33.0 - 2.0 * p.n_flavours) / (12.0 * kPi);
+  d.as_over = d.fixed ? p.alphas_mz
+                      : p.alphas_mz / (1.0 + p.alphas_mz * d.b0 * std::log(p.t_cutoff / (kMZ * kMZ)));
+  d.seed_lo = static_cast<uint32_t>(p.seed);
+  d.seed_hi = static_cast<uint32_t>(p.seed >> 32);
+  return d;
+}
+
+Events make_events(const gaps_batch& b) {
+  gaps_layout L;
+  compute_layout(b.n_events, b.capacity, &L);
+  char* base = static_cast<char*>(b.workspace);
+  Events E;
+  E.px = reinterpret_cast<double*>(base + L.px);
+  E.py = reinterpret_cast<double*>(base + L.py);
+  E.pz = reinterpret_cast<double*>(base + L.pz);
+  E.e = reinterpret_cast<double*>(base + L.e);
+  E.flav = reinterpret_cast<int8_t*>(base + L.flav);
+  E.col = reinterpret_cast<int16_t*>(base + L.col);
+  E.acol = reinterpret_cast<int16_t*>(base + L.acol);
+  E.link = reinterpret_cast<uint8_t*>(base + L.link);
+  E.t = reinterpret_cast<double*>(base + L.t);
+  E.weight = reinterpret_cast<double*>(base + L.weight);
+  E.hash = reinterpret_cast<unsigned long long*>(base + L.hash);
+  E.n_partons = reinterpret_cast<int32_t*>(base + L.n_partons);
+  E.status = reinterpret_cast<int32_t*>(base + L.status);
+  E.n_steps = reinterpret_cast<int32_t*>(base + L.n_steps);
+  E.n_emissions = reinterpret_cast<int32_t*>(base + L.n_emissions);
+  E.n_winners = reinterpret_cast<int32_t*>(base + L.n_winners);
+  E.n_trials = reinterpret_cast<int32_t*>(base + L.n_trials);
+  E.n_dipoles = reinterpret_cast<int32_t*>(base + L.n_dipoles);
+  E.next_colour = reinterpret_cast<int32_t*>(base + L.next_colour);
+  E.me_flavour = reinterpret_cast<int32_t*>(base + L.me_flavour);
+  E.valid = reinterpret_cast<int32_t*>(base + L.valid);
+  E.obs = reinterpret_cast<double*>(base + L.obs);
+  E.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
+  E.hist = reinterpret_cast<double*>(base + L.hist);
+  E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
+  E.n = b.n_events;
+  E.cap = b.capacity;
+  E.first = b.first_event;
+  return E;
+}
+
+}  // namespace gaps
+
+using namespace gaps;
+
+extern "C" {
+
+size_t gaps_workspace_bytes(int64_t n_events, int32_t capacity) {
+  if (!sizes_ok(n_events, capacity)) return 0;
+  gaps_layout L;
+  compute_layout(n_events, capacity, &L);
+  return static_cast<size_t>(L.total_bytes);
+}
+
+int gaps_workspace_layout(int64_t n_events, int32_t capacity, gaps_layout* out) {
+  if (!out || !sizes_ok(n_events, capacity)) return GAPS_ERR_INVALID;
+  compute_layout(n_events, capacity, out);
+  return GAPS_OK;
+}
+
+int gaps_check_params(const gaps_params* p) {
+  if (!p) return GAPS_ERR_INVALID;
+  if (!(p->sqrt_s > 0.0) || !std::isfinite(p->sqrt_s)) return GAPS_ERR_INVALID;
+  if (!(p->alphas_mz > 0.0) || !std::isfinite(p->alphas_mz)) return GAPS_ERR_INVALID;
+  if (!(p->t_cutoff > 0.0) || !(p->t_cutoff < 0.25 * p->sqrt_s * p->sqrt_s)) return GAPS_ERR_INVALID;
+  if (p->n_flavours < 1 || p->n_flavours > 5) return GAPS_ERR_INVALID;
+  if (p->max_steps < 1 || p->reserved != 0) return GAPS_ERR_INVALID;
+  if (!p->fixed_alphas) {
+    const double b0 = (33.0 - 2.0 * p->n_flavours) / (12.0 * kPi);
+    if (!(1.0 + p->alphas_mz * b0 * std::log(p->t_cutoff / (kMZ * kMZ)) > 0.0)) return GAPS_ERR_INVALID;
+  }
+  return GAPS_OK;
+}
+
+int gaps_generate_me(const gaps_params* params, const gaps_batch* batch, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_me(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e =
+      launch_step_plain(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+namespace {
+
+int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
+                double* kernel_ms_out, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  if (mode != GAPS_SHOWER_PLAIN) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevParams P = make_dev_params(*params);
+  const Events E = make_events(*batch);
+  int64_t launches = 0;
+  if (launches_out) *launches_out = 0;
+  if (kernel_ms_out) *kernel_ms_out = 0.0;
+  if (E.n == 0) return GAPS_OK;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (kernel_ms_out) {
+    e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  struct EventGuard {
+    cudaEvent_t a, b;
+    ~EventGuard() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } guard{ev0, ev1};
+  e = cudaMemsetAsync(E.counters, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  // The host loop of App. C: one cycle for every event per launch, then the
+  // finished-event counter is read back; an event stops after max_steps
+  // cycles, so the loop ends after at most max_steps + 1 launches.
+  unsigned long long cnt[2] = {0, 0};  // finished events, events stopped at max_steps
+  double total_ms = 0.0;
+  while (cnt[0] < static_cast<unsigned long long>(E.n)) {
+    if (launches > static_cast<int64_t>(P.max_steps)) break;
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
+    e = launch_step_plain(P, E, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
+    ++launches;
+    e = cudaMemcpyAsync(cnt, E.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ev0) {
+      float ms = 0.0f;
+      e = cudaEventElapsedTime(&ms, ev0, ev1);
+      if (e != cudaSuccess) return cuda_fail(e);
+      total_ms += ms;
+    }
+  }
+  if (launches_out) *launches_out = launches;
+  if (kernel_ms_out) *kernel_ms_out = total_ms;
+  return cnt[1] > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
+}
+
+}  // namespace
+
+int gaps_shower(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
+                void* stream) {
+  return shower_impl(params, batch, mode, launches_out, nullptr, stream);
+}
+
+int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
+                      double* kernel_ms_out, void* stream) {
+  return shower_impl(params, batch, mode, launches_out, kernel_ms_out, stream);
+}
+
+int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e =
+      launch_validate(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e =
+      launch_observables(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_histograms(const gaps_params* params, const gaps_batch* batch, double* hist_device, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !hist_device)
+    return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_histograms(make_events(*batch), hist_device, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_reduce_stats(const gaps_batch* batch, gaps_stats* stats_device, void* stream) {
+  if (check_batch(batch) != GAPS_OK || !stats_device) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(stats_device, 0, sizeof(gaps_stats), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_stats(make_events(*batch), stats_device, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, double* host_hist,
+             gaps_stats* host_stats, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !host_hist)
+    return GAPS_ERR_INVALID;
+  if (mode != GAPS_SHOWER_PLAIN) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Events E = make_events(*batch);
+  cudaError_t e = cudaMemsetAsync(E.hist, 0, sizeof(double) * GAPS_HIST_DOUBLES, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int rc = gaps_generate_me(params, batch, stream);
+  if (rc != GAPS_OK) return rc;
+  int64_t launches = 0;
+  rc = gaps_shower(params, batch, mode, &launches, stream);
+  if (rc != GAPS_OK && rc != GAPS_ERR_STEP_LIMIT) return rc;
+  rc = gaps_validate(params, batch, stream);
+  if (rc != GAPS_OK) return rc;
+  rc = gaps_observables(params, batch, stream);
+  if (rc != GAPS_OK) return rc;
+  rc = gaps_histograms(params, batch, E.hist, stream);
+  if (rc != GAPS_OK) return rc;
+  rc = gaps_reduce_stats(batch, E.stats, stream);
+  if (rc != GAPS_OK) return rc;
+  e = cudaMemcpyAsync(host_hist, E.hist, sizeof(double) * GAPS_HIST_DOUBLES, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  gaps_stats st{};
+  e = cudaMemcpyAsync(&st, E.stats, sizeof(gaps_stats), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  st.launches = launches;
+  if (host_stats) *host_stats = st;
+  return st.n_step_limit > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
+}
+
+const char* gaps_strerror(int status) {
+  switch (status) {
+    case GAPS_OK: return "ok";
+    case GAPS_ERR_INVALID: return "invalid argument";
+    case GAPS_ERR_CUDA: return "CUDA error";
+    case GAPS_ERR_STEP_LIMIT: return "an event reached the veto-cycle limit";
+    case GAPS_ERR_NO_DEVICE: return "no usable device";
+    default: return "unknown status";
+  }
+}
+
+const char* gaps_last_cuda_error(void) { return g_cuda_error; }
+
+int gaps_version(void) { return 100; }
+
+}  // extern "C"

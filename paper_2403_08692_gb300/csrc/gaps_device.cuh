@@ -1,0 +1,220 @@
+// Device-side building blocks of the shower library (sm_103a): the Philox
+// counter generator, the event-record view over the workspace, physics
+// constants, the LO matrix element, the running coupling, the splitting
+// kernels and the final-final dipole map.
+#pragma once
+#include <cstdint>
+
+#include "gaps.h"
+
+namespace gaps {
+
+// ------------------------------------------------------------ constants
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCF = 4.0 / 3.0;
+constexpr double kCA = 3.0;
+constexpr double kTR = 0.5;
+constexpr double kNc = 3.0;
+// Electroweak inputs of the LO matrix element; the paper names none, these
+// are the values this library adopts.
+constexpr double kMZ = 91.1876;
+constexpr double kGammaZ = 2.4952;
+constexpr double kAlphaQED = 1.0 / 128.802;
+constexpr double kSin2W = 0.222;
+constexpr double kGeV2ToPb = 0.389379e9;
+constexpr int kGluon = 21;
+constexpr uint8_t kNoLink = 255;
+
+enum : uint32_t { kDrawME = 1, kDrawTrial = 2, kDrawWinner = 3 };
+enum : int { kQtoQG = 0, kGtoGG = 1, kGtoQQ = 2 };
+
+// Parameters of one launch, derived once on the host from gaps_params.
+struct DevParams {
+  double sqrt_s, s, tc;
+  double alphas_mz, as_over;  // alpha_s(m_Z) and the overestimate alpha_s(t_C)
+  double b0;                  // one-loop beta_0 = (33 - 2 n_f) / (12 pi)
+  uint32_t seed_lo, seed_hi;
+  int nf, fixed, max_steps;
+};
+
+// Pointers into the workspace (gaps_layout) for one batch.
+struct Events {
+  double *px, *py, *pz, *e;
+  int8_t* flav;
+  int16_t *col, *acol;
+  uint8_t* link;  // [2][cap][n]
+  double *t, *weight;
+  unsigned long long* hash;
+  int32_t *n_partons, *status, *n_steps, *n_emissions, *n_winners, *n_trials, *n_dipoles, *next_colour,
+      *me_flavour, *valid;
+  double* obs;  // [6][n]
+  unsigned long long* counters;
+  double* hist;
+  gaps_stats* stats;
+  int64_t n;
+  int cap;
+  uint32_t first;
+
+  __device__ __forceinline__ size_t at(int slot, int64_t ev) const {
+    return static_cast<size_t>(slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
+  }
+  __device__ __forceinline__ size_t link_at(int side, int slot, int64_t ev) const {
+    return (static_cast<size_t>(side) * cap + slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
+  }
+};
+
+// --------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with a Weyl-sequence key schedule.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// 52-bit uniform strictly inside (0, 1): the top 26 bits of each word, plus
+// one half, times 2^-52 (exact in binary64).
+__device__ __forceinline__ double to_unit(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = (static_cast<unsigned long long>(hi >> 6) << 26) | (lo >> 6);
+  return (static_cast<double>(m) + 0.5) * 0x1p-52;
+}
+
+struct Uniforms {
+  double a, b;
+};
+
+__device__ __forceinline__ Uniforms draw2(const DevParams& P, uint32_t ev, uint32_t step, uint32_t slot,
+                                          uint32_t purpose) {
+  const U4 r = philox10(ev, step, slot, purpose, P.seed_lo, P.seed_hi);
+  return Uniforms{to_unit(r.x, r.y), to_unit(r.z, r.w)};
+}
+
+// FNV-1a, 64 bit, over the eight little-endian bytes of a decision word.
+__device__ __forceinline__ unsigned long long fnv1a64(unsigned long long h, unsigned long long word) {
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    h ^= (word >> (8 * b)) & 0xFFull;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+constexpr unsigned long long kFnvBasis = 14695981039346656037ull;
+
+// ------------------------------------------------------------- physics
+// One-loop running coupling alpha_s(t); the fixed mode returns alpha_s(m_Z).
+__device__ __forceinline__ double alpha_s(const DevParams& P, double t) {
+  if (P.fixed) return P.alphas_mz;
+  return P.alphas_mz / (1.0 + P.alphas_mz * P.b0 * log(t / (kMZ * kMZ)));
+}
+
+// Splitting kernel P(z, y) and its overestimate P^over(z).
+__device__ __forceinline__ double kernel_p(int kind, double z, double y) {
+  if (kind == kQtoQG) return kCF * (2.0 / (1.0 - z * (1.0 - y)) - (1.0 + z));
+  if (kind == kGtoGG) return 0.5 * kCA * (2.0 / (1.0 - z * (1.0 - y)) - 2.0 + z * (1.0 - z));
+  return 0.5 * kTR * (1.0 - 2.0 * z * (1.0 - z));
+}
+__device__ __forceinline__ double kernel_over(int kind, double z) {
+  if (kind == kQtoQG) return 2.0 * kCF / (1.0 - z);
+  if (kind == kGtoGG) return kCA / (1.0 - z);
+  return 0.5 * kTR;
+}
+// Coefficient K of the kernel's overestimate: P^over = K / (1 - z) for the
+// soft kernels, K for g -> q qbar.
+__device__ __forceinline__ double kernel_k(int kind) {
+  return kind == kQtoQG ? 2.0 * kCF : (kind == kGtoGG ? kCA : 0.5 * kTR);
+}
+
+// Minkowski product.
+__device__ __forceinline__ double mdot(double ae, double ax, double ay, double az, double be, double bx,
+                                       double by, double bz) {
+  return ae * be - ax * bx - ay * by - az * bz;
+}
+
+struct V4 {
+  double e, x, y, z;
+};
+
+__device__ __forceinline__ double mdot(const V4& a, const V4& b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
+
+__device__ __forceinline__ double det3(double a1, double a2, double a3, double b1, double b2, double b3,
+                                       double c1, double c2, double c3) {
+  return a1 * (b2 * c3 - b3 * c2) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2 - b2 * c1);
+}
+
+// Catani-Seymour final-final map for massless splitter a and spectator b:
+// p_i = z a + (1-z) y b + k, p_j = (1-z) a + z y b - k, p_b' = (1-y) b,
+// k = sqrt(z(1-z) y Q^2) (cos phi n1 + sin phi n2), with n1, n2 unit
+// spacelike vectors orthogonal to a, b and each other: n1 projects the
+// first of the references (1,1,0,0), (1,0,1,0), (1,0,0,1) whose projection
+// has |n1^2| >= 1e-4, n2 is the Minkowski-orthogonal complement of (a, b,
+// n1) (cofactor expansion of det[X; a; b; n1]).
+__device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, double y, double cphi,
+                                           double sphi, V4& pi, V4& pj, V4& pb) {
+  const double ab = mdot(a, b);
+  const double q2 = 2.0 * ab;
+  V4 n1{0, 0, 0, 0};
+  for (int r = 0; r < 3; ++r) {
+    const V4 ref{1.0, r == 0 ? 1.0 : 0.0, r == 1 ? 1.0 : 0.0, r == 2 ? 1.0 : 0.0};
+    const double cb = mdot(ref, b) / ab;
+    const double ca = mdot(ref, a) / ab;
+    n1 = V4{ref.e - cb * a.e - ca * b.e, ref.x - cb * a.x - ca * b.x, ref.y - cb * a.y - ca * b.y,
+            ref.z - cb * a.z - ca * b.z};
+    if (fabs(mdot(n1, n1)) >= 1e-4) break;
+  }
+  const double s1 = 1.0 / sqrt(-mdot(n1, n1));
+  n1 = V4{n1.e * s1, n1.x * s1, n1.y * s1, n1.z * s1};
+  const double c0 = det3(a.x, a.y, a.z, b.x, b.y, b.z, n1.x, n1.y, n1.z);
+  const double c1 = -det3(a.e, a.y, a.z, b.e, b.y, b.z, n1.e, n1.y, n1.z);
+  const double c2 = det3(a.e, a.x, a.z, b.e, b.x, b.z, n1.e, n1.x, n1.z);
+  const double c3 = -det3(a.e, a.x, a.y, b.e, b.x, b.y, n1.e, n1.x, n1.y);
+  V4 n2{c0, -c1, -c2, -c3};
+  const double s2 = 1.0 / sqrt(-mdot(n2, n2));
+  n2 = V4{n2.e * s2, n2.x * s2, n2.y * s2, n2.z * s2};
+  const double kt = sqrt(z * (1.0 - z) * y * q2);
+  const double kc = kt * cphi, ks = kt * sphi;
+  const V4 k{kc * n1.e + ks * n2.e, kc * n1.x + ks * n2.x, kc * n1.y + ks * n2.y, kc * n1.z + ks * n2.z};
+  const double fa_i = z, fb_i = (1.0 - z) * y, fa_j = 1.0 - z, fb_j = z * y;
+  pi = V4{fa_i * a.e + fb_i * b.e + k.e, fa_i * a.x + fb_i * b.x + k.x, fa_i * a.y + fb_i * b.y + k.y,
+          fa_i * a.z + fb_i * b.z + k.z};
+  pj = V4{fa_j * a.e + fb_j * b.e - k.e, fa_j * a.x + fb_j * b.x - k.x, fa_j * a.y + fb_j * b.y - k.y,
+          fa_j * a.z + fb_j * b.z - k.z};
+  const double r = 1.0 - y;
+  pb = V4{r * b.e, r * b.x, r * b.y, r * b.z};
+}
+
+// d sigma / d cos(theta) for e+e- -> q qbar (flavour f, PDG 1..5) at LO with
+// photon and Z exchange and their interference, in pb; theta is the quark's
+// angle to the electron beam.
+__device__ __forceinline__ double dsigma_dcos(double s, int f, double cth) {
+  const bool up = (f == 2 || f == 4);
+  const double qf = up ? 2.0 / 3.0 : -1.0 / 3.0;
+  const double af = up ? 0.5 : -0.5;
+  const double vf = af - 2.0 * qf * kSin2W;
+  const double qe = -1.0, ae = -0.5, ve = -0.5 + 2.0 * kSin2W;
+  const double kappa = 1.0 / (4.0 * kSin2W * (1.0 - kSin2W));
+  const double mz2 = kMZ * kMZ;
+  const double den = (s - mz2) * (s - mz2) + kGammaZ * kGammaZ * mz2;
+  const double chi1 = kappa * s * (s - mz2) / den;
+  const double chi2 = kappa * kappa * s * s / den;
+  const double even = qe * qe * qf * qf + 2.0 * qe * qf * ve * vf * chi1 + (ae * ae + ve * ve) * (af * af + vf * vf) * chi2;
+  const double odd = 2.0 * qe * qf * ae * af * chi1 + 4.0 * ae * ve * af * vf * chi2;
+  return kPi * kAlphaQED * kAlphaQED / (2.0 * s) * kNc * ((1.0 + cth * cth) * even + 2.0 * cth * odd) * kGeV2ToPb;
+}
+
+}  // namespace gaps

@@ -1,0 +1,19 @@
+// Host-side launchers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gaps_device.cuh"
+
+namespace gaps {
+
+DevParams make_dev_params(const gaps_params& p);
+Events make_events(const gaps_batch& b);
+
+cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);
+cudaError_t launch_step_plain(const DevParams& P, const Events& E, cudaStream_t s);
+cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s);
+cudaError_t launch_observables(const DevParams& P, const Events& E, cudaStream_t s);
+cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s);
+cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s);
+
+}  // namespace gaps

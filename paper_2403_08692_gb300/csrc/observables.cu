@@ -1,0 +1,360 @@
+// Event validation, observables (Sec. 3.1: Durham jet resolutions, thrust,
+// heavy-jet mass), atomic histogramming (Sec. 3.2) and batch statistics.
+#include "gaps_launch.hpp"
+
+namespace gaps {
+
+namespace {
+
+// ------------------------------------------------------------ validation
+// One thread per event.  Bits: 1 momentum not conserved to 1e-10 GeV, 2 a
+// parton off shell, 4 non-positive energy, 8 broken colour flow, 16 flavour
+// imbalance, 32 non-finite momentum.
+__global__ void __launch_bounds__(128) k_validate(DevParams P, Events E) {
+  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (ev >= E.n) return;
+  const int n = E.n_partons[ev];
+  int bits = 0;
+  double se = 0, sx = 0, sy = 0, sz = 0;
+  int fsum[6] = {0, 0, 0, 0, 0, 0};
+  bool colour_ok = true;
+  int n_quarks = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t a = E.at(i, ev);
+    const double e = E.e[a], x = E.px[a], y = E.py[a], z = E.pz[a];
+    if (!isfinite(e) || !isfinite(x) || !isfinite(y) || !isfinite(z)) bits |= 32;
+    se += e;
+    sx += x;
+    sy += y;
+    sz += z;
+    if (!(e > 0.0)) bits |= 4;
+    if (fabs(e * e - x * x - y * y - z * z) > 1e-10 * e * e) bits |= 2;
+    const int fl = E.flav[a];
+    const int c = E.col[a], ac = E.acol[a];
+    const int l0 = E.link[E.link_at(0, i, ev)], l1 = E.link[E.link_at(1, i, ev)];
+    if (fl == kGluon) {
+      colour_ok &= c > 0 && ac > 0;
+    } else if (fl >= 1 && fl <= 5) {
+      colour_ok &= c > 0 && ac == 0;
+      fsum[fl] += 1;
+      ++n_quarks;
+    } else if (fl <= -1 && fl >= -5) {
+      colour_ok &= c == 0 && ac > 0;
+      fsum[-fl] -= 1;
+    } else {
+      colour_ok = false;
+    }
+    // Colour line c must continue on the partner's anticolour side and back.
+    if (c > 0) {
+      colour_ok &= l0 != kNoLink && l0 < n;
+      if (l0 != kNoLink && l0 < n) {
+        colour_ok &= E.acol[E.at(l0, ev)] == c;
+        colour_ok &= E.link[E.link_at(1, l0, ev)] == i;
+      }
+    } else {
+      colour_ok &= l0 == kNoLink;
+    }
+    if (ac > 0) {
+      colour_ok &= l1 != kNoLink && l1 < n;
+      if (l1 != kNoLink && l1 < n) {
+        colour_ok &= E.col[E.at(l1, ev)] == ac;
+        colour_ok &= E.link[E.link_at(0, l1, ev)] == i;
+      }
+    } else {
+      colour_ok &= l1 == kNoLink;
+    }
+  }
+  // Every chain runs from a quark to an antiquark; together they visit all
+  // partons (no closed gluon loops).
+  if (colour_ok) {
+    int visited = 0;
+    for (int i = 0; i < n && colour_ok; ++i) {
+      const int fl = E.flav[E.at(i, ev)];
+      if (!(fl >= 1 && fl <= 5)) continue;
+      int cur = i;
+      for (int guard = 0; guard <= n; ++guard) {
+        ++visited;
+        const int nxt = E.link[E.link_at(0, cur, ev)];
+        if (nxt == kNoLink) break;
+        cur = nxt;
+      }
+      const int fl_end = E.flav[E.at(cur, ev)];
+      colour_ok &= fl_end <= -1 && fl_end >= -5;
+    }
+    colour_ok &= visited == n;
+  }
+  if (!colour_ok) bits |= 8;
+  if (fabs(se - P.sqrt_s) > 1e-10 || fabs(sx) > 1e-10 || fabs(sy) > 1e-10 || fabs(sz) > 1e-10) bits |= 1;
+  for (int f = 1; f <= 5; ++f)
+    if (fsum[f] != 0) bits |= 16;
+  (void)n_quarks;
+  E.valid[ev] = bits;
+}
+
+// ----------------------------------------------------------- observables
+// One thread per event; the event's momenta are copied into a per-thread
+// array of MAXJ entries (MAXJ >= capacity).
+template <int MAXJ>
+__global__ void __launch_bounds__(128) k_observables(DevParams P, Events E) {
+  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (ev >= E.n) return;
+  double* obs = E.obs;
+  const int64_t N = E.n;
+  if (E.status[ev] != GAPS_DONE) {
+    for (int h = 0; h < 6; ++h) obs[h * N + ev] = -1.0;
+    return;
+  }
+  const int n = E.n_partons[ev];
+  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
+  for (int i = 0; i < n; ++i) {
+    const size_t a = E.at(i, ev);
+    je[i] = E.e[a];
+    jx[i] = E.px[a];
+    jy[i] = E.py[a];
+    jz[i] = E.pz[a];
+  }
+  const double s = P.s;
+
+  // Thrust (exact): planes through every pair (j, k) with p_j x p_k != 0,
+  // the other momenta signed by their side, the pair tried with both signs.
+  double sum_abs = 0.0;
+  for (int i = 0; i < n; ++i) sum_abs += sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+  double best2 = -1.0, bx = 0.0, by = 0.0, bz = 0.0;
+  for (int j = 0; j < n; ++j) {
+    for (int k = j + 1; k < n; ++k) {
+      const double nx = jy[j] * jz[k] - jz[j] * jy[k];
+      const double ny = jz[j] * jx[k] - jx[j] * jz[k];
+      const double nz = jx[j] * jy[k] - jy[j] * jx[k];
+      if (nx == 0.0 && ny == 0.0 && nz == 0.0) continue;
+      double px = 0.0, py = 0.0, pz = 0.0;
+      for (int i = 0; i < n; ++i) {
+        if (i == j || i == k) continue;
+        const double d = jx[i] * nx + jy[i] * ny + jz[i] * nz;
+        const double sg = d >= 0.0 ? 1.0 : -1.0;
+        px += sg * jx[i];
+        py += sg * jy[i];
+        pz += sg * jz[i];
+      }
+      for (int c = 0; c < 4; ++c) {
+        const double fj = (c & 2) ? -1.0 : 1.0;
+        const double fk = (c & 1) ? -1.0 : 1.0;
+        const double cx = px + fj * jx[j] + fk * jx[k];
+        const double cy = py + fj * jy[j] + fk * jy[k];
+        const double cz = pz + fj * jz[j] + fk * jz[k];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        if (c2 > best2) {
+          best2 = c2;
+          bx = cx;
+          by = cy;
+          bz = cz;
+        }
+      }
+    }
+  }
+  double thrust, ax, ay, az;
+  if (best2 < 0.0) {
+    const double l = sqrt(jx[0] * jx[0] + jy[0] * jy[0] + jz[0] * jz[0]);
+    thrust = 1.0;
+    ax = jx[0] / l;
+    ay = jy[0] / l;
+    az = jz[0] / l;
+  } else {
+    const double l = sqrt(best2);
+    thrust = l / sum_abs;
+    ax = bx / l;
+    ay = by / l;
+    az = bz / l;
+  }
+  // Heavy-jet mass: hemispheres by the sign of p . n_T.
+  double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    double* h = (jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0) ? hp : hm;
+    h[0] += je[i];
+    h[1] += jx[i];
+    h[2] += jy[i];
+    h[3] += jz[i];
+  }
+  const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
+  const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
+  obs[4 * N + ev] = 1.0 - thrust;
+  obs[5 * N + ev] = fmax(mp, mm) / s;
+
+  // Durham (E-scheme): merge the pair of smallest y_ij = 2 min(E_i^2, E_j^2)
+  // (1 - cos theta_ij) / s until one jet is left; the merge from n+1 to n
+  // jets records y_{n,n+1}.
+  double yres[4] = {-1.0, -1.0, -1.0, -1.0};
+  int m = n;
+  while (m > 1) {
+    double ymin = 0.0;
+    int bi = -1, bj = -1;
+    for (int i = 0; i < m; ++i) {
+      const double ai = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+      for (int j = i + 1; j < m; ++j) {
+        const double aj = sqrt(jx[j] * jx[j] + jy[j] * jy[j] + jz[j] * jz[j]);
+        const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ai * aj);
+        const double e2 = fmin(je[i] * je[i], je[j] * je[j]);
+        const double y = 2.0 * e2 * (1.0 - cosij) / s;
+        if (bi < 0 || y < ymin) {
+          ymin = y;
+          bi = i;
+          bj = j;
+        }
+      }
+    }
+    const int idx = m - 3;
+    if (idx >= 0 && idx < 4) yres[idx] = ymin;
+    je[bi] += je[bj];
+    jx[bi] += jx[bj];
+    jy[bi] += jy[bj];
+    jz[bi] += jz[bj];
+    je[bj] = je[m - 1];
+    jx[bj] = jx[m - 1];
+    jy[bj] = jy[m - 1];
+    jz[bj] = jz[m - 1];
+    --m;
+  }
+  for (int h = 0; h < 4; ++h) obs[h * N + ev] = yres[h];
+}
+
+// ---------------------------------------------------------- histograms
+// Block-private histograms in shared memory, then one atomic merge per bin.
+__global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
+  __shared__ double sh[GAPS_HIST_DOUBLES];
+  for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x) sh[i] = 0.0;
+  __syncthreads();
+  const int64_t N = E.n;
+  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < N;
+       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
+    const double w = E.weight[ev];
+    for (int h = 0; h < GAPS_N_OBS; ++h) {
+      const double o = E.obs[h * N + ev];
+      double x, lo, hi;
+      if (h < 4) {
+        if (!(o > 0.0)) continue;
+        x = log10(o);
+        lo = -4.3;
+        hi = -0.3;
+      } else {
+        x = o;
+        lo = 0.0;
+        hi = 0.5;
+      }
+      const double f = (x - lo) / (hi - lo) * GAPS_N_BINS;
+      const int bin = f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
+      double* cell = sh + (h * GAPS_HIST_ROW + bin) * 3;
+      atomicAdd(cell + 0, w);
+      atomicAdd(cell + 1, w * w);
+      atomicAdd(cell + 2, 1.0);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x)
+    if (sh[i] != 0.0) atomicAdd(hist + i, sh[i]);
+}
+
+// -------------------------------------------------------------- stats
+__global__ void __launch_bounds__(256) k_stats(Events E, gaps_stats* st) {
+  long long done = 0, over = 0, lim = 0, inval = 0, steps = 0, mx = 0, trials = 0, wins = 0, ems = 0,
+            parts = 0, dips = 0;
+  double sw = 0.0, sw2 = 0.0;
+  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < E.n;
+       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int stt = E.status[ev];
+    done += stt == GAPS_DONE;
+    over += stt == GAPS_OVERFLOW;
+    lim += stt == GAPS_STEP_LIMIT;
+    inval += E.valid[ev] != 0;
+    const int ns = E.n_steps[ev];
+    steps += ns;
+    mx = ns > mx ? ns : mx;
+    trials += E.n_trials[ev];
+    wins += E.n_winners[ev];
+    ems += E.n_emissions[ev];
+    parts += E.n_partons[ev];
+    dips += E.n_dipoles[ev];
+    const double w = E.weight[ev];
+    sw += w;
+    sw2 += w * w;
+  }
+  // warp reduction, then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    done += __shfl_down_sync(0xffffffffu, done, o);
+    over += __shfl_down_sync(0xffffffffu, over, o);
+    lim += __shfl_down_sync(0xffffffffu, lim, o);
+    inval += __shfl_down_sync(0xffffffffu, inval, o);
+    steps += __shfl_down_sync(0xffffffffu, steps, o);
+    const long long om = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = om > mx ? om : mx;
+    trials += __shfl_down_sync(0xffffffffu, trials, o);
+    wins += __shfl_down_sync(0xffffffffu, wins, o);
+    ems += __shfl_down_sync(0xffffffffu, ems, o);
+    parts += __shfl_down_sync(0xffffffffu, parts, o);
+    dips += __shfl_down_sync(0xffffffffu, dips, o);
+    sw += __shfl_down_sync(0xffffffffu, sw, o);
+    sw2 += __shfl_down_sync(0xffffffffu, sw2, o);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st->n_events), static_cast<unsigned long long>(E.n));
+  if ((threadIdx.x & 31) == 0) {
+    auto add = [](int64_t* p, long long v) {
+      if (v) atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+    };
+    add(&st->n_done, done);
+    add(&st->n_overflow, over);
+    add(&st->n_step_limit, lim);
+    add(&st->n_invalid, inval);
+    add(&st->sum_steps, steps);
+    atomicMax(reinterpret_cast<unsigned long long*>(&st->max_steps), static_cast<unsigned long long>(mx));
+    add(&st->sum_trials, trials);
+    add(&st->sum_winners, wins);
+    add(&st->sum_emissions, ems);
+    add(&st->sum_partons, parts);
+    add(&st->sum_dipoles, dips);
+    atomicAdd(&st->sum_weight, sw);
+    atomicAdd(&st->sum_weight2, sw2);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
+  k_validate<<<blocks, 128, 0, s>>>(P, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const DevParams& P, const Events& E, cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
+  if (E.cap <= 32) k_observables<32><<<blocks, 128, 0, s>>>(P, E);
+  else if (E.cap <= 64) k_observables<64><<<blocks, 128, 0, s>>>(P, E);
+  else if (E.cap <= 128) k_observables<128><<<blocks, 128, 0, s>>>(P, E);
+  else k_observables<256><<<blocks, 128, 0, s>>>(P, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (E.n + 255) / 256;
+  const unsigned blocks = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
+  k_histograms<<<blocks, 256, 0, s>>>(E, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (E.n + 255) / 256;
+  const unsigned blocks = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
+  k_stats<<<blocks, 256, 0, s>>>(E, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace gaps

@@ -1,0 +1,245 @@
+"""Python binding of the C ABI in include/gaps.h (ctypes, argument marshalling
+only).  Every step of the hot path runs in the CUDA library; PyTorch supplies
+the device workspace and the stream.  There is no CPU fallback: loading the
+library fails loudly if it has not been built or no GPU is present.
+"""
+import ctypes as C
+import os
+
+from . import build as _build
+
+GAPS_OK, GAPS_ERR_INVALID, GAPS_ERR_CUDA, GAPS_ERR_STEP_LIMIT, GAPS_ERR_NO_DEVICE = 0, -1, -2, -3, -4
+ACTIVE, DONE, OVERFLOW, STEP_LIMIT = 0, 1, 2, 3
+SHOWER_PLAIN = 0
+N_OBS, N_BINS, HIST_ROW = 6, 100, 102
+HIST_DOUBLES = N_OBS * HIST_ROW * 3
+
+
+class Params(C.Structure):
+    _fields_ = [("sqrt_s", C.c_double), ("alphas_mz", C.c_double), ("t_cutoff", C.c_double),
+                ("seed", C.c_uint64), ("n_flavours", C.c_int32), ("fixed_alphas", C.c_int32),
+                ("max_steps", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("workspace", C.c_void_p), ("n_events", C.c_int64), ("capacity", C.c_int32),
+                ("first_event", C.c_uint32)]
+
+
+_LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "t", "weight", "hash",
+                  "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
+                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "counters", "hist", "stats", "total_bytes"]
+
+
+class Layout(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in _LAYOUT_FIELDS]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_events", C.c_int64), ("n_done", C.c_int64), ("n_overflow", C.c_int64),
+                ("n_step_limit", C.c_int64), ("n_invalid", C.c_int64), ("sum_steps", C.c_int64),
+                ("max_steps", C.c_int64), ("sum_trials", C.c_int64), ("sum_winners", C.c_int64),
+                ("sum_emissions", C.c_int64), ("sum_partons", C.c_int64), ("sum_dipoles", C.c_int64),
+                ("launches", C.c_int64),
+                ("sum_weight", C.c_double), ("sum_weight2", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol include/gaps.h declares, with its ctypes signature.
+_P = C.POINTER
+SIGNATURES = {
+    "gaps_workspace_bytes": (C.c_size_t, [C.c_int64, C.c_int32]),
+    "gaps_workspace_layout": (C.c_int, [C.c_int64, C.c_int32, _P(Layout)]),
+    "gaps_check_params": (C.c_int, [_P(Params)]),
+    "gaps_generate_me": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
+    "gaps_shower": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), C.c_void_p]),
+    "gaps_shower_timed": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), _P(C.c_double),
+                                    C.c_void_p]),
+    "gaps_shower_step": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
+    "gaps_validate": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
+    "gaps_observables": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
+    "gaps_histograms": (C.c_int, [_P(Params), _P(Batch), C.c_void_p, C.c_void_p]),
+    "gaps_reduce_stats": (C.c_int, [_P(Batch), C.c_void_p, C.c_void_p]),
+    "gaps_run": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_double), _P(Stats), C.c_void_p]),
+    "gaps_strerror": (C.c_char_p, [C.c_int]),
+    "gaps_last_cuda_error": (C.c_char_p, []),
+    "gaps_version": (C.c_int, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgaps.so (building it first if needed) and bind every symbol."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with paper_2403_08692_gb300.build")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GapsError(RuntimeError):
+    def __init__(self, code, where):
+        L = load()
+        msg = L.gaps_strerror(code).decode()
+        if code == GAPS_ERR_CUDA:
+            msg += ": " + L.gaps_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def _check(code, where, allow=()):
+    if code != GAPS_OK and code not in allow:
+        raise GapsError(code, where)
+    return code
+
+
+def make_params(sqrt_s=91.2, alphas_mz=0.118, t_cutoff=1.0, seed=1, n_flavours=5, fixed_alphas=0,
+                max_steps=100000):
+    return Params(float(sqrt_s), float(alphas_mz), float(t_cutoff), int(seed), int(n_flavours),
+                  int(fixed_alphas), int(max_steps), 0)
+
+
+def workspace_bytes(n_events, capacity):
+    return int(load().gaps_workspace_bytes(int(n_events), int(capacity)))
+
+
+def layout(n_events, capacity) -> Layout:
+    L = Layout()
+    _check(load().gaps_workspace_layout(int(n_events), int(capacity), C.byref(L)), "gaps_workspace_layout")
+    return L
+
+
+def check_params(p: Params) -> int:
+    return load().gaps_check_params(C.byref(p))
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _batch(ws) -> Batch:
+    return Batch(C.c_void_p(ws.buffer.data_ptr()), ws.n_events, ws.capacity, ws.first_event)
+
+
+def generate_me(p, ws, stream=None):
+    _check(load().gaps_generate_me(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_generate_me")
+
+
+def shower(p, ws, mode=SHOWER_PLAIN, stream=None):
+    """Returns (status code, launches); GAPS_ERR_STEP_LIMIT is not raised."""
+    n = C.c_int64(0)
+    rc = _check(load().gaps_shower(C.byref(p), C.byref(_batch(ws)), int(mode), C.byref(n), _stream_handle(stream)),
+                "gaps_shower", allow=(GAPS_ERR_STEP_LIMIT,))
+    return rc, n.value
+
+
+def shower_timed(p, ws, mode=SHOWER_PLAIN, stream=None):
+    """gaps_shower_timed: returns (status code, launches, summed kernel ms)."""
+    n = C.c_int64(0)
+    ms = C.c_double(0.0)
+    rc = _check(load().gaps_shower_timed(C.byref(p), C.byref(_batch(ws)), int(mode), C.byref(n), C.byref(ms),
+                                         _stream_handle(stream)), "gaps_shower_timed", allow=(GAPS_ERR_STEP_LIMIT,))
+    return rc, n.value, ms.value
+
+
+def shower_step(p, ws, stream=None):
+    _check(load().gaps_shower_step(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_shower_step")
+
+
+def validate(p, ws, stream=None):
+    _check(load().gaps_validate(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_validate")
+
+
+def observables(p, ws, stream=None):
+    _check(load().gaps_observables(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_observables")
+
+
+def histograms(p, ws, hist_device, stream=None):
+    _check(load().gaps_histograms(C.byref(p), C.byref(_batch(ws)), C.c_void_p(hist_device.data_ptr()),
+                                  _stream_handle(stream)), "gaps_histograms")
+
+
+def reduce_stats(ws, stats_device, stream=None):
+    _check(load().gaps_reduce_stats(C.byref(_batch(ws)), C.c_void_p(stats_device.data_ptr()),
+                                    _stream_handle(stream)), "gaps_reduce_stats")
+
+
+def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):
+    """The whole pipeline through host buffers.  host_hist: a CPU float64
+    tensor/array of HIST_DOUBLES elements (pinned for asynchronous copies).
+    Returns (status code, Stats)."""
+    st = Stats()
+    ptr = host_hist.data_ptr() if hasattr(host_hist, "data_ptr") else host_hist.ctypes.data
+    rc = _check(load().gaps_run(C.byref(p), C.byref(_batch(ws)), int(mode), C.cast(ptr, C.POINTER(C.c_double)),
+                                C.byref(st), _stream_handle(stream)), "gaps_run", allow=(GAPS_ERR_STEP_LIMIT,))
+    return rc, st
+
+
+class Workspace:
+    """A device workspace for one batch, allocated by PyTorch, with typed
+    views of every array in the layout."""
+
+    def __init__(self, n_events, capacity=128, first_event=0, device="cuda"):
+        import torch
+        self.n_events = int(n_events)
+        self.capacity = int(capacity)
+        self.first_event = int(first_event)
+        nbytes = workspace_bytes(self.n_events, self.capacity)
+        if nbytes == 0:
+            raise ValueError("batch sizes out of range")
+        # 256 extra bytes so the base can be aligned to 256
+        self._raw = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self._raw.data_ptr()) % 256
+        self.buffer = self._raw[off:off + nbytes]
+        self.layout = layout(self.n_events, self.capacity)
+
+    def view(self, name, dtype, shape):
+        import torch
+        off = getattr(self.layout, name)
+        nbytes = 1
+        for d in shape:
+            nbytes *= d
+        nbytes *= torch.empty((), dtype=dtype).element_size()
+        return self.buffer[off:off + nbytes].view(dtype).view(*shape)
+
+    def momenta(self):
+        import torch
+        n, cap = self.n_events, self.capacity
+        return {c: self.view(c, torch.float64, (cap, n)) for c in ("e", "px", "py", "pz")}
+
+    def scalars(self):
+        import torch
+        n = self.n_events
+        out = {k: self.view(k, torch.int32, (n,)) for k in ("n_partons", "status", "n_steps", "n_emissions",
+                                                            "n_winners", "n_trials", "n_dipoles", "next_colour",
+                                                            "me_flavour", "valid")}
+        out["t"] = self.view("t", torch.float64, (n,))
+        out["weight"] = self.view("weight", torch.float64, (n,))
+        out["hash"] = self.view("hash", torch.int64, (n,))
+        return out
+
+    def obs(self):
+        import torch
+        return self.view("obs", torch.float64, (N_OBS, self.n_events))
+
+    def colours(self):
+        import torch
+        n, cap = self.n_events, self.capacity
+        return {"flav": self.view("flav", torch.int8, (cap, n)), "col": self.view("col", torch.int16, (cap, n)),
+                "acol": self.view("acol", torch.int16, (cap, n)), "link": self.view("link", torch.uint8, (2, cap, n))}

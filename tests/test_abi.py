@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every symbol include/gaps.h
+declares; host-only calls (sizing, layout, parameter checks) behave.  No GPU
+needed, no compute calls."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\**(gaps_[a-z0-9_]+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2403_08692_gb300 as g
+    g.load()
+    return g
+
+
+def test_every_declared_symbol_is_exported(g):
+    names = _declared_functions()
+    assert len(names) >= 14, names
+    lib = C.CDLL(g.gaps.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding knows every one of them, with the same names
+    assert set(names) <= set(g.gaps.SIGNATURES), set(names) - set(g.gaps.SIGNATURES)
+
+
+def test_header_constants_match_binding(g):
+    text = open(os.path.join(ROOT, "include", "gaps.h")).read()
+    assert "GAPS_N_OBS = 6, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102" in text
+    assert g.HIST_DOUBLES == 6 * 102 * 3
+    assert C.sizeof(g.gaps.Params) == 48
+    assert C.sizeof(g.gaps.Batch) == 24
+    assert C.sizeof(g.gaps.Stats) == 15 * 8
+
+
+def test_workspace_layout(g):
+    for n, cap in ((0, 4), (1, 128), (10000, 128), (12345, 50), (1000000, 255)):
+        L = g.layout(n, cap)
+        total = g.workspace_bytes(n, cap)
+        assert total == L.total_bytes
+        offs = [getattr(L, f) for f, _ in L._fields_ if f != "total_bytes"]
+        assert all(o % 256 == 0 for o in offs)
+        assert offs == sorted(offs)
+        if n > 0:
+            assert len(set(offs)) == len(offs)
+        assert L.py - L.px >= 8 * n * cap and L.flav - L.e >= 8 * n * cap
+        assert L.obs + 48 * n <= L.counters
+    assert g.workspace_bytes(10, 3) == 0
+    assert g.workspace_bytes(10, 256) == 0
+    assert g.workspace_bytes(-1, 128) == 0
+    with pytest.raises(g.GapsError):
+        g.layout(10, 300)
+
+
+def test_param_checks(g):
+    assert g.check_params(g.make_params()) == 0
+    assert g.check_params(g.make_params(t_cutoff=0.0)) == -1
+    assert g.check_params(g.make_params(t_cutoff=91.2 ** 2 / 4)) == -1
+    assert g.check_params(g.make_params(n_flavours=6)) == -1
+    assert g.check_params(g.make_params(max_steps=0)) == -1
+    assert g.check_params(g.make_params(t_cutoff=1e-4)) == -1
+    p = g.make_params()
+    p.reserved = 1
+    assert g.check_params(p) == -1
+
+
+def test_status_strings(g):
+    L = g.load()
+    assert L.gaps_strerror(0) == b"ok"
+    assert b"invalid" in L.gaps_strerror(-1)
+    assert L.gaps_version() >= 100
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2403_08692_gb300 import gaps as G
+    monkeypatch.setattr(G, "_lib", None)
+    monkeypatch.setattr(G._build, "LIB", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError):
+        G.load(build_if_missing=False)

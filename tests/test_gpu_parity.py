@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, event by
+event, on the same seeded inputs.  Requires a GB300."""
+import numpy as np
+import pytest
+
+from tests import gpu_harness as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_08692_gb300 as g
+    g.load()
+    return g
+
+
+def _both(g, O, n, capacity=128, first_event=0, **kw):
+    gp = g.make_params(**kw)
+    op = H.oracle_params(O, capacity, **kw)
+    gpu = H.run_gpu(g, gp, n, capacity, first_event)
+    orc = O.run(op, first_event, n, threads=O.threads_available(), want_momenta=True)
+    return gpu, orc
+
+
+def test_config1_small_plain(g, oracle_mod):
+    """10^4 LEP events, seed 1 (78 full blocks of 128 and a ragged tail of 16):
+    >= 99.9 % identical decision sequences, momenta to 1e-9, identical
+    flavours and colours, observables to 1e-9, validation clean."""
+    gpu, orc = _both(g, oracle_mod, 10000, seed=1)
+    res = H.compare_events(gpu, orc)
+    assert res["agree"] >= H.AGREE_MIN, res
+    sc = gpu["scalars"]
+    assert np.all(sc["status"] == g.DONE)
+    assert np.all(sc["valid"] == 0)
+    assert gpu["launches"] == sc["n_steps"].max() + 0  # the last launch finishes the last event
+    print("agreement", res)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(sqrt_s=133.0, t_cutoff=0.5, seed=41),
+    dict(sqrt_s=200.0, t_cutoff=2.0, seed=42),
+    dict(sqrt_s=91.2, t_cutoff=1.0, seed=43, n_flavours=3),
+    dict(sqrt_s=91.2, t_cutoff=1.0, seed=44, fixed_alphas=1),
+    dict(sqrt_s=91.2, t_cutoff=1.0, seed=0xFFFFFFFF00000001),
+])
+def test_parameter_variants(g, oracle_mod, kw):
+    gpu, orc = _both(g, oracle_mod, 3000, **kw)
+    res = H.compare_events(gpu, orc)
+    assert res["agree"] >= H.AGREE_MIN, res
+
+
+def test_first_event_offset_and_single_event(g, oracle_mod):
+    """Event ids start anywhere in the 32-bit range; a one-event batch is
+    the same event as inside a big batch."""
+    gpu, orc = _both(g, oracle_mod, 777, first_event=0xFFFFF000, seed=5)
+    assert H.compare_events(gpu, orc)["agree"] >= H.AGREE_MIN
+    one, orc1 = _both(g, oracle_mod, 1, first_event=0xFFFFF000 + 123, seed=5)
+    assert one["scalars"]["hash"][0] == gpu["scalars"]["hash"][123]
+    k = one["scalars"]["n_partons"][0]
+    assert k == gpu["scalars"]["n_partons"][123]
+    assert np.array_equal(one["mom"][0, :k], gpu["mom"][123, :k])
+    assert H.compare_events(one, orc1)["agree"] == 1.0
+
+
+def test_overflow_matches_oracle(g, oracle_mod):
+    """Capacity 4: events that fill their record stop with the overflow
+    status exactly where the oracle's do."""
+    gpu, orc = _both(g, oracle_mod, 2000, capacity=4, seed=3)
+    sc = gpu["scalars"]
+    assert np.sum(sc["status"] == g.OVERFLOW) > 200
+    assert np.array_equal(sc["status"], orc["events"]["status"])
+    res = H.compare_events(gpu, orc)
+    assert res["agree"] >= H.AGREE_MIN
+    # overflowed events get no observables
+    assert np.all(gpu["obs"][sc["status"] == g.OVERFLOW] == -1.0)
+
+
+def test_step_limit(g, oracle_mod):
+    gpu, orc = _both(g, oracle_mod, 1000, seed=3, max_steps=6)
+    assert gpu["rc"] == -3  # GAPS_ERR_STEP_LIMIT
+    sc = gpu["scalars"]
+    assert np.array_equal(sc["status"], orc["events"]["status"])
+    assert np.any(sc["status"] == g.STEP_LIMIT)
+    assert gpu["launches"] == 7
+
+
+def test_empty_batch_is_a_no_op(g):
+    ws = g.Workspace(0, 128)
+    p = g.make_params()
+    g.generate_me(p, ws)
+    rc, launches = g.shower(p, ws)
+    g.validate(p, ws)
+    g.observables(p, ws)
+    assert rc == 0 and launches == 0
+
+
+def test_invalid_arguments_are_rejected(g):
+    ws = g.Workspace(10, 128)
+    for bad in (dict(t_cutoff=0.0), dict(t_cutoff=91.2 ** 2), dict(n_flavours=0), dict(sqrt_s=-5.0),
+                dict(max_steps=0), dict(t_cutoff=1e-4)):
+        with pytest.raises(g.GapsError) as e:
+            g.generate_me(g.make_params(**bad), ws)
+        assert e.value.code == -1
+
+
+def test_histograms_and_pipeline(g, oracle_mod):
+    """gaps_histograms bins exactly the per-event observables it is given;
+    gaps_run (host buffers) reproduces the stage-by-stage pipeline; the
+    oracle's histogram of the same events agrees."""
+    import torch
+    n = 5000
+    p = g.make_params(seed=7)
+    ws = g.Workspace(n, 128)
+    host = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64).pin_memory()
+    rc, st = g.run(p, ws, host)
+    assert rc == 0
+    assert st.n_events == n and st.n_done == n and st.n_invalid == 0
+    hist = host.numpy().reshape(6, 102, 3).copy()
+    # stage-by-stage on a fresh workspace
+    gpu = H.run_gpu(g, p, n, 128)
+    hd = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
+    g.histograms(p, gpu["ws"], hd)
+    h2 = hd.cpu().numpy().reshape(6, 102, 3)
+    np.testing.assert_allclose(hist, h2, rtol=1e-12, atol=1e-9)
+    # re-bin the GPU observables on the host
+    sc, obs = gpu["scalars"], gpu["obs"]
+    w = sc["weight"]
+    for h in range(6):
+        x = obs[:, h]
+        ok = sc["status"] == g.DONE
+        if h < 4:
+            ok &= x > 0
+            v, lo, hi = np.log10(np.where(ok, x, 1.0)), -4.3, -0.3
+        else:
+            v, lo, hi = x, 0.0, 0.5
+        f = (v - lo) / (hi - lo) * 100
+        b = np.where(f < 0, 0, np.where(f >= 100, 101, 1 + np.floor(np.clip(f, 0, 99.999999)).astype(int)))
+        np.testing.assert_allclose(h2[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=102), rtol=1e-12)
+        assert np.array_equal(h2[h, :, 2], np.bincount(b[ok], minlength=102).astype(float))
+    # against the oracle's own histogram of the same events
+    orc = oracle_mod.run(H.oracle_params(oracle_mod, 128, seed=7), 0, n, threads=oracle_mod.threads_available())
+    chi2, ndf = H.hist_chi2(hist, orc["hist"])
+    assert chi2 < 1.5 and ndf > 100
+    # statistics agree with the per-event arrays
+    assert st.sum_steps == int(sc["n_steps"].sum())
+    assert st.sum_emissions == int(sc["n_emissions"].sum())
+    assert st.max_steps == int(sc["n_steps"].max())
+    assert st.launches == st.max_steps
+    np.testing.assert_allclose(st.sum_weight, w.sum(), rtol=1e-12)
+
+
+def test_rerun_is_bitwise_deterministic(g):
+    p = g.make_params(seed=12)
+    a = H.run_gpu(g, p, 4000)
+    b = H.run_gpu(g, p, 4000)
+    assert np.array_equal(a["scalars"]["n_partons"], b["scalars"]["n_partons"])
+    for j in range(4000):
+        k = a["scalars"]["n_partons"][j]
+        assert np.array_equal(a["mom"][j, :k], b["mom"][j, :k])
+    assert np.array_equal(a["obs"], b["obs"])
+    assert np.array_equal(a["scalars"]["hash"], b["scalars"]["hash"])
+
+
+def test_paper_scale_config2(g, oracle_mod):
+    """10^6 LEP events, seed 2, plain form as benchmarked: 3000 sampled events
+    against the oracle one by one, and all histograms against the oracle's
+    10^6-event histograms (chi^2/ndf < 1.5)."""
+    import torch
+    n = 1_000_000
+    p = g.make_params(seed=2)
+    ws = g.Workspace(n, 128)
+    host = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64).pin_memory()
+    rc, st = g.run(p, ws, host)
+    assert rc == 0 and st.n_done == n and st.n_invalid == 0
+    sc = {k: v.cpu().numpy() for k, v in ws.scalars().items()}
+    sc["hash"] = sc["hash"].view(np.uint64)
+    rng = np.random.default_rng(2024)
+    ids = np.sort(rng.choice(n, size=3000, replace=False))
+    op = H.oracle_params(oracle_mod, 128, seed=2)
+    same = 0
+    mom = ws.momenta()
+    e = mom["e"].cpu().numpy()
+    for j in ids:
+        one = oracle_mod.run(op, int(j), 1, want_momenta=True)
+        ev = one["events"][0]
+        if ev["hash"] == sc["hash"][j] and ev["n_partons"] == sc["n_partons"][j]:
+            same += 1
+            k = ev["n_partons"]
+            assert np.all(np.abs(e[:k, j] - one["mom"][0, :k, 0]) <= H.MOM_REL * one["mom"][0, :k, 0] + H.MOM_ABS)
+    assert same / len(ids) >= H.AGREE_MIN
+    orc = oracle_mod.run(op, 0, n, threads=oracle_mod.threads_available(), want_obs=False)
+    hist = host.numpy().reshape(6, 102, 3)
+    chi2, ndf = H.hist_chi2(hist, orc["hist"])
+    assert chi2 < 1.5, (chi2, ndf)
+    print("config2 launches", st.launches, "max steps", st.max_steps, "chi2/ndf", chi2)
