@@ -236,6 +236,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
 
+    # FP32-screen fallbacks of the last pass (cycles redone in FP64, vetoes
+    # decided in FP64)
+    counters = ws.view("counters", torch.int64, (16,)).cpu().numpy()
     # per-event work units of one pass (identical every step)
     g.reduce_stats(ws, stats_dev, stream)
     st = g.Stats.from_buffer_copy(stats_dev.cpu().numpy().tobytes()[:len(bytes(g.Stats()))])
@@ -295,7 +298,8 @@ def main():
         "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,
                                       "winners": st.sum_winners, "emissions": st.sum_emissions},
-                   "max_steps": st.max_steps, "mean_partons": st.sum_partons / max(1, st.n_events)},
+                   "max_steps": st.max_steps, "mean_partons": st.sum_partons / max(1, st.n_events),
+                   "fp64_fallback_cycles": int(counters[2]), "fp64_vetoes": int(counters[3])},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu

@@ -82,7 +82,13 @@ typedef struct gaps_layout {
   int64_t col, acol;      /* int16  [capacity][n_events]: colour / anticolour line, 0 = none */
   int64_t link;           /* uint8  [2][capacity][n_events]: colour partner slot on side 0
                              (colour line) and side 1 (anticolour line), 255 = none */
-  int64_t t;              /* double [n_events]: evolution scale t (GeV^2) */
+  int64_t dip;            /* float2 [2][capacity][n_events]: per-dipole cache of the trial
+                             densities (library-internal contents) */
+  int64_t dq2, dzp, dinv; /* double [2][capacity][n_events]: FP64 part of the dipole cache
+                             (Q^2, z+, 1/ln(z+/z-); library-internal contents) */
+  int64_t t;              /* double [n_events]: evolution scale t (GeV^2) at which the event
+                             finished: t_C at the cutoff, the last winner's scale otherwise */
+  int64_t lnt;            /* double [n_events]: ln t while the event is showering */
   int64_t weight;         /* double [n_events]: matrix-element weight (pb) */
   int64_t hash;           /* uint64 [n_events]: FNV-1a of the veto decisions */
   int64_t n_partons;      /* int32  [n_events] */
@@ -96,7 +102,8 @@ typedef struct gaps_layout {
   int64_t me_flavour;     /* int32  [n_events] */
   int64_t valid;          /* int32  [n_events]: validation bits, 0 = valid */
   int64_t obs;            /* double [6][n_events]: y23, y34, y45, y56, 1-T, rho_H (-1 = undefined) */
-  int64_t counters;       /* uint64 [16]: device counters (word 0 = finished events) */
+  int64_t counters;       /* uint64 [16]: device counters of the last shower call: 0 finished events,
+                             1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64 */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t total_bytes;

@@ -40,7 +40,12 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->col = take(2 * pc);
   L->acol = take(2 * pc);
   L->link = take(2 * pc);
+  L->dip = take(16 * pc);
+  L->dq2 = take(16 * pc);
+  L->dzp = take(16 * pc);
+  L->dinv = take(16 * pc);
   L->t = take(8 * n);
+  L->lnt = take(8 * n);
   L->weight = take(8 * n);
   L->hash = take(8 * n);
   L->n_partons = take(4 * n);
@@ -82,6 +87,15 @@ DevParams make_dev_params(const gaps_params& p) {
   d.b0 = (33.0 - 2.0 * p.n_flavours) / (12.0 * kPi);
   d.as_over = d.fixed ? p.alphas_mz
                       : p.alphas_mz / (1.0 + p.alphas_mz * d.b0 * std::log(p.t_cutoff / (kMZ * kMZ)));
+  d.ln_tc = std::log(p.t_cutoff);
+  d.inv_as2pi_2cf = 1.0 / ((d.as_over / (2.0 * kPi)) * (2.0 * kCF));
+  d.inv_as2pi_ca = 1.0 / ((d.as_over / (2.0 * kPi)) * kCA);
+  d.tcf = static_cast<float>(p.t_cutoff);
+  d.as2pi_f = static_cast<float>(d.as_over / (2.0 * kPi));
+  d.lg2_tc_f = static_cast<float>(std::log2(p.t_cutoff));
+  d.as_mz_over_f = static_cast<float>(p.alphas_mz / d.as_over);
+  d.as_b0_f = static_cast<float>(p.alphas_mz * d.b0);
+  d.ln_mz2_f = static_cast<float>(std::log(kMZ * kMZ));
   d.seed_lo = static_cast<uint32_t>(p.seed);
   d.seed_hi = static_cast<uint32_t>(p.seed >> 32);
   return d;
@@ -100,6 +114,11 @@ Events make_events(const gaps_batch& b) {
   E.col = reinterpret_cast<int16_t*>(base + L.col);
   E.acol = reinterpret_cast<int16_t*>(base + L.acol);
   E.link = reinterpret_cast<uint8_t*>(base + L.link);
+  E.dip = reinterpret_cast<float2*>(base + L.dip);
+  E.dq2 = reinterpret_cast<double*>(base + L.dq2);
+  E.dzp = reinterpret_cast<double*>(base + L.dzp);
+  E.dinv = reinterpret_cast<double*>(base + L.dinv);
+  E.lnt = reinterpret_cast<double*>(base + L.lnt);
   E.t = reinterpret_cast<double*>(base + L.t);
   E.weight = reinterpret_cast<double*>(base + L.weight);
   E.hash = reinterpret_cast<unsigned long long*>(base + L.hash);
@@ -196,7 +215,7 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
       if (b) cudaEventDestroy(b);
     }
   } guard{ev0, ev1};
-  e = cudaMemsetAsync(E.counters, 0, 2 * sizeof(unsigned long long), s);
+  e = cudaMemsetAsync(E.counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e);
   // The host loop of App. C: one cycle for every event per launch, then the
   // finished-event counter is read back; an event stops after max_steps

@@ -35,6 +35,10 @@ struct DevParams {
   double b0;                  // one-loop beta_0 = (33 - 2 n_f) / (12 pi)
   uint32_t seed_lo, seed_hi;
   int nf, fixed, max_steps;
+  double ln_tc;                       // ln t_C
+  double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
+  // FP32 copies used by the screens
+  float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;
 };
 
 // Pointers into the workspace (gaps_layout) for one batch.
@@ -43,6 +47,9 @@ struct Events {
   int8_t* flav;
   int16_t *col, *acol;
   uint8_t* link;  // [2][cap][n]
+  float2* dip;    // [2][cap][n] dipole cache (see shower_cycle.cuh)
+  double *dq2, *dzp, *dinv;  // [2][cap][n] FP64 part of the dipole cache
+  double* lnt;               // [n] ln t of the active events
   double *t, *weight;
   unsigned long long* hash;
   int32_t *n_partons, *status, *n_steps, *n_emissions, *n_winners, *n_trials, *n_dipoles, *next_colour,

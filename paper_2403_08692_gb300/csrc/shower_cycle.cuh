@@ -1,0 +1,428 @@
+// One veto cycle of one event (Sec. 2, App. A, App. C), split in two phases
+// and shared by every shower form:
+//   cycle_select_veto  SelectWinnerEmission + CheckCutoff + AcceptOrVeto
+//   cycle_emit         GenerateEmission for an accepted winner
+// The caller runs the first phase for a dense set of active events, queues
+// the accepted ones (about one in ten) and runs the second phase on the
+// queue, so the FP64-heavy splitting never executes in a warp whose other
+// lanes idle.
+//
+// GB300 runs FP64 at about 1/74 of its FP32 rate, so the cycle spends FP64
+// only where the result must be FP64:
+//  * Trial screening.  Every trial's scale is ranked by its key
+//    log2(t'/t) = log2(r) / c in FP32, from a per-dipole cache of 1/c; each
+//    key carries a bound on its FP32 error.  When one trial's key beats every
+//    other trial's and the cutoff by more than the bounds, it is the winner
+//    the exact FP64 comparison would pick, and only its scale is evaluated in
+//    FP64.  Otherwise (about 1e-4 of cycles) the whole cycle is redone with
+//    every trial in FP64, exactly as the oracle does it.
+//  * Log-space evolution.  The event carries L = ln t; a winner moves it to
+//    L + ln(r)/c (Eq. A.6 in logarithms), so a cycle needs one FP64 log and
+//    no exp; t itself is formed only for an accepted emission.
+//  * Veto.  z, y and the acceptance ratio are formed in FP32 with an error
+//    bound; only a veto number within the bound of the ratio is decided in
+//    FP64.  z and y are recomputed in FP64 for the accepted emissions.
+//  * Dipole cache.  A dipole's trial density depends only on its invariant
+//    mass, which changes only when an emission moves one of its partons, so
+//    Q^2, z+ and 1/ln(z+/z-) (FP64) and 1/c (FP32) are stored per dipole and
+//    recomputed once per dipole an emission touches.
+#pragma once
+#include "gaps_device.cuh"
+
+namespace gaps {
+
+// Error allowances of the FP32 screens: several times the worst-case error of
+// the FP32 operations involved (derivation in the design notes).
+constexpr float kKeyRelInvc = 4e-6f;
+constexpr float kKeyRelKey = 1.6e-5f;
+constexpr float kVetoRel = 5e-5f;
+constexpr float kVetoAbs = 2e-5f;
+
+__device__ __forceinline__ V4 load_p(const Events& E, int slot, int64_t ev) {
+  const size_t a = E.at(slot, ev);
+  return V4{E.e[a], E.px[a], E.py[a], E.pz[a]};
+}
+__device__ __forceinline__ void store_p(const Events& E, int slot, int64_t ev, const V4& p) {
+  const size_t a = E.at(slot, ev);
+  E.e[a] = p.e;
+  E.px[a] = p.x;
+  E.py[a] = p.y;
+  E.pz[a] = p.z;
+}
+
+__device__ __forceinline__ size_t dip_at(const Events& E, int side, int slot, int64_t ev) {
+  return E.link_at(side, slot, ev);
+}
+
+// Cache entry of a dipole of invariant mass q2: FP64 Q^2, z+ = (1 +
+// sqrt(1 - 4 t_C/Q^2))/2 and 1/ln(z+/z-) with z- = 1 - z+ (the oracle's
+// formulas), and the FP32 screen entry x = 1/(a ln(z+/z-)), y = 1/(a T_R/2
+// (z+ - z-)), a = alpha_s^over/(2 pi).  x = -1 marks a dipole without phase
+// space (Q^2 < 4 t_C, the oracle's FP64 test).
+struct DipoleEntry {
+  double q2, zp, inv_ls;
+  float2 screen;
+};
+
+__device__ __forceinline__ DipoleEntry make_dipole(const DevParams& P, double q2) {
+  DipoleEntry d;
+  d.q2 = q2;
+  if (q2 < 4.0 * P.tc) {
+    d.zp = d.inv_ls = 0.0;
+    d.screen = make_float2(-1.0f, -1.0f);
+    return d;
+  }
+  d.zp = 0.5 * (1.0 + sqrt(1.0 - 4.0 * P.tc / q2));
+  const double ls = log(d.zp / (1.0 - d.zp));
+  d.inv_ls = 1.0 / ls;
+  d.screen = make_float2(1.0f / (P.as2pi_f * static_cast<float>(ls)),
+                         1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * static_cast<float>(2.0 * d.zp - 1.0)));
+  return d;
+}
+
+__device__ __forceinline__ void store_dipole(const Events& E, int64_t ev, int slot, int side, const DipoleEntry& d) {
+  const size_t a = dip_at(E, side, slot, ev);
+  E.dip[a] = d.screen;
+  if (d.screen.x < 0.0f) return;
+  E.dq2[a] = d.q2;
+  E.dzp[a] = d.zp;
+  E.dinv[a] = d.inv_ls;
+}
+
+// 32-bit float close to the 52-bit uniform built from (hi, lo): relative
+// error below 2^-22 for every value.
+__device__ __forceinline__ float unit_float(uint32_t hi, uint32_t lo) {
+  const float a = __uint2float_rn(hi >> 6);
+  const float b = __uint2float_rn(lo >> 6);
+  return fmaf(a, 0x1p-26f, fmaf(b, 0x1p-52f, 0x1p-53f));
+}
+
+// Everything GenerateEmission needs about an accepted winner.
+struct EmitTask {
+  int64_t ev;
+  double lnt, q2, zp, inv_ls;
+  uint32_t rz_hi, rz_lo;
+  int i, k, side, kappa, kind, n, step, pad;
+};
+
+// 1/c of a kernel for a dipole, c = alpha_s^over/(2 pi) * integral of
+// P^over over [z-, z+].
+__device__ __forceinline__ double inv_c_fp64(const DevParams& P, int kind, double zp, double inv_ls) {
+  if (kind == kGtoQQ) return 1.0 / ((P.as_over / (2.0 * kPi)) * (0.5 * kTR) * (zp - (1.0 - zp)));
+  return inv_ls * (kind == kQtoQG ? P.inv_as2pi_2cf : P.inv_as2pi_ca);
+}
+
+// The full FP64 SelectWinnerEmission (every trial exact, recomputed from the
+// momenta); the fallback of the FP32 screen.  The log-space scale of trial
+// j is L + ln(r_j)/c_j; the highest above ln t_C wins, the first on ties.
+// Returns false if no trial is above t_C.
+__device__ bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+                                   double lnt, EmitTask& w) {
+  double best = P.ln_tc;
+  bool found = false;
+  for (int i = 0; i < n; ++i) {
+    const bool gluon = E.flav[E.at(i, ev)] == kGluon;
+    const int nk = gluon ? 1 + P.nf : 1;
+    const V4 pi = load_p(E, i, ev);
+    for (int side = 0; side < 2; ++side) {
+      const int k = E.link[E.link_at(side, i, ev)];
+      if (k == kNoLink) continue;
+      const DipoleEntry d = make_dipole(P, 2.0 * mdot(pi, load_p(E, k, ev)));
+      if (d.screen.x < 0.0f) continue;
+      for (int kp = 0; kp < nk; kp += 2) {
+        const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
+                              kDrawTrial, P.seed_lo, P.seed_hi);
+        for (int h = 0; h < 2 && kp + h < nk; ++h) {
+          const int kappa = kp + h;
+          const int kind = gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG;
+          const double u = h ? to_unit(r.z, r.w) : to_unit(r.x, r.y);
+          const double lt = lnt + log(u) * inv_c_fp64(P, kind, d.zp, d.inv_ls);
+          if (lt > best) {
+            best = lt;
+            found = true;
+            w.lnt = lt;
+            w.q2 = d.q2;
+            w.zp = d.zp;
+            w.inv_ls = d.inv_ls;
+            w.i = i;
+            w.k = k;
+            w.side = side;
+            w.kappa = kappa;
+            w.kind = kind;
+          }
+        }
+      }
+    }
+  }
+  return found;
+}
+
+// Exact FP64 acceptance ratio of Eq. (A.9) with the (1 - y) factor, for a
+// given z.  Returns -1 when y >= 1.
+__device__ __forceinline__ double veto_ratio_fp64(const DevParams& P, int kind, double t, double q2, double z) {
+  const double y = t / (q2 * z * (1.0 - z));
+  if (!(y < 1.0)) return -1.0;
+  const double f = (1.0 - y) * alpha_s(P, t) * kernel_p(kind, z, y);
+  const double g = P.as_over * kernel_over(kind, z);
+  return f / g;
+}
+
+// z from Eq. (A.8) in FP64, in a cancellation-free form: for the 1/(1-z)
+// kernels 1 - z = z+ (z-/z+)^r, i.e. z = z- - z+ expm1(-r ln(z+/z-)).
+__device__ __forceinline__ double z_fp64(int kind, double zp, double lsoft, double r) {
+  const double zm = 1.0 - zp;
+  if (kind == kGtoQQ) return zm + (zp - zm) * r;
+  return zm - zp * expm1(-r * lsoft);
+}
+
+enum : int { kCycleVetoed = 0, kCycleFinished = 1, kCycleAccepted = 2 };
+
+// Leave the active state with `status`, recording the final scale.
+__device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int status, double t) {
+  E.status[ev] = status;
+  E.t[ev] = t;
+}
+
+// Phase 1 of a cycle for active event ev.  Returns kCycleFinished when the
+// event left the active state (status written), kCycleAccepted with `task`
+// filled when an emission must be generated, kCycleVetoed otherwise.
+__device__ int cycle_select_veto(const DevParams& P, const Events& E, int64_t ev, EmitTask& task) {
+  const uint32_t id = E.first + static_cast<uint32_t>(ev);
+  const int n = E.n_partons[ev];
+  const int step = E.n_steps[ev];
+  const double lnt = E.lnt[ev];
+  if (step >= P.max_steps) {
+    finish_event(E, ev, GAPS_STEP_LIMIT, exp(lnt));
+    return kCycleFinished;
+  }
+
+  // ---- SelectWinnerEmission, FP32 screen over every trial.
+  float best_key = -INFINITY, best_m = 0.0f, others_hi = -INFINITY;
+  int best_code = -1;  // (2 i + side) * 8 + kappa
+  uint32_t best_hi = 0, best_lo = 0;
+  int trials = 0, dipoles = 0;
+  constexpr float kInvCF2 = static_cast<float>(1.0 / (2.0 * kCF));
+  constexpr float kInvCA = static_cast<float>(1.0 / kCA);
+  for (int i = 0; i < n; ++i) {
+    const bool gluon = E.flav[E.at(i, ev)] == kGluon;
+    const int nk = gluon ? 1 + P.nf : 1;
+    for (int side = 0; side < 2; ++side) {
+      if (E.link[E.link_at(side, i, ev)] == kNoLink) continue;
+      const float2 d = E.dip[dip_at(E, side, i, ev)];
+      if (d.x < 0.0f) continue;
+      ++dipoles;
+      for (int kp = 0; kp < nk; kp += 2) {
+        const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
+                              kDrawTrial, P.seed_lo, P.seed_hi);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kappa = kp + h;
+          if (kappa >= nk) break;
+          const uint32_t whi = h ? r.z : r.x, wlo = h ? r.w : r.y;
+          const float lg2u = __log2f(unit_float(whi, wlo));
+          const float invc = !gluon ? d.x * kInvCF2 : (kappa == 0 ? d.x * kInvCA : d.y);
+          const float key = lg2u * invc;
+          const float m = kKeyRelInvc * invc + kKeyRelKey * fabsf(key);
+          ++trials;
+          if (key > best_key) {
+            others_hi = fmaxf(others_hi, best_key + best_m);
+            best_key = key;
+            best_m = m;
+            best_code = (2 * i + side) * 8 + kappa;
+            best_hi = whi;
+            best_lo = wlo;
+          } else {
+            others_hi = fmaxf(others_hi, key + m);
+          }
+        }
+      }
+    }
+  }
+  E.n_steps[ev] = step + 1;
+  E.n_trials[ev] += trials;
+  E.n_dipoles[ev] += dipoles;
+
+  // Cutoff threshold in key units: t' > t_C  <=>  key > log2(t_C / t).
+  const float lt2 = static_cast<float>(lnt) * 1.44269504f;
+  const float thr = P.lg2_tc_f - lt2;
+  const float thr_m = 2e-6f * (1.0f + fabsf(lt2) + fabsf(P.lg2_tc_f));
+
+  bool have = false, decided = false;
+  if (best_code < 0 || fmaxf(best_key + best_m, others_hi) < thr - thr_m) {
+    decided = true;  // certainly no trial above the cutoff
+  } else if (best_key - best_m > thr + thr_m && others_hi < best_key - best_m) {
+    // Certain winner: its scale exactly, from the FP64 cache.
+    const int dcode = best_code >> 3, kappa = best_code & 7;
+    const int i = dcode >> 1, side = dcode & 1;
+    const size_t a = dip_at(E, side, i, ev);
+    const bool gluon = E.flav[E.at(i, ev)] == kGluon;
+    const int kind = gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG;
+    const double zp = E.dzp[a], inv_ls = E.dinv[a];
+    const double lt = lnt + log(to_unit(best_hi, best_lo)) * inv_c_fp64(P, kind, zp, inv_ls);
+    if (lt > P.ln_tc) {
+      task.lnt = lt;
+      task.q2 = E.dq2[a];
+      task.zp = zp;
+      task.inv_ls = inv_ls;
+      task.i = i;
+      task.k = E.link[E.link_at(side, i, ev)];
+      task.side = side;
+      task.kappa = kappa;
+      task.kind = kind;
+      have = decided = true;
+    }
+  }
+  if (!decided) {
+    atomicAdd(&E.counters[2], 1ull);  // screen undecided: full FP64 cycle
+    have = select_winner_fp64(P, E, ev, id, step, n, lnt, task);
+  }
+
+  // ---- CheckCutoff.
+  if (!have) {
+    finish_event(E, ev, GAPS_DONE, P.tc);
+    return kCycleFinished;
+  }
+  E.lnt[ev] = task.lnt;
+  E.n_winners[ev] += 1;
+
+  // ---- AcceptOrVeto: FP32 screen of Eq. (A.8)-(A.9), FP64 near the edge.
+  const U4 rw = philox10(id, static_cast<uint32_t>(step), 0u, kDrawWinner, P.seed_lo, P.seed_hi);
+  bool accept;
+  {
+    const float zpf = static_cast<float>(task.zp);
+    const float zmf = static_cast<float>(1.0 - task.zp);
+    const float lf = 1.0f / static_cast<float>(task.inv_ls);
+    const float rzf = unit_float(rw.x, rw.y);
+    float z, e;  // z and 1 - z
+    if (task.kind == kGtoQQ) {
+      z = fmaf(zpf - zmf, rzf, zmf);
+      e = fmaf(-(zpf - zmf), rzf, zpf);
+    } else {
+      z = zmf - zpf * expm1f(-rzf * lf);
+      e = zpf * __expf(-rzf * lf);
+    }
+    const float lnt_f = static_cast<float>(task.lnt);
+    const float y = __expf(lnt_f) / (static_cast<float>(task.q2) * z * e);
+    const float as_ratio = P.fixed ? 1.0f : P.as_mz_over_f / (1.0f + P.as_b0_f * (lnt_f - P.ln_mz2_f));
+    float pr;  // P(z, y) / P^over(z)
+    if (task.kind == kQtoQG) {
+      pr = e / (e + z * y) - 0.5f * (1.0f + z) * e;
+    } else if (task.kind == kGtoGG) {
+      pr = e / (e + z * y) - e + 0.5f * z * e * e;
+    } else {
+      pr = 1.0f - 2.0f * z * e;
+    }
+    const float ratio = (1.0f - y) * as_ratio * pr;
+    const float rvf = unit_float(rw.z, rw.w);
+    const float margin = kVetoRel * (fabsf(ratio) + rvf) + kVetoAbs;
+    if (fabsf(y - 1.0f) <= 1e-4f || fabsf(rvf - ratio) <= margin) {
+      atomicAdd(&E.counters[3], 1ull);  // veto decided in FP64
+      const double zz = z_fp64(task.kind, task.zp, 1.0 / task.inv_ls, to_unit(rw.x, rw.y));
+      const double ratio64 = veto_ratio_fp64(P, task.kind, exp(task.lnt), task.q2, zz);
+      accept = ratio64 >= 0.0 && to_unit(rw.z, rw.w) < ratio64;
+    } else {
+      accept = y < 1.0f && rvf < ratio;
+    }
+  }
+  const unsigned long long word = static_cast<unsigned long long>(step) |
+                                  (static_cast<unsigned long long>(task.i) << 32) |
+                                  (static_cast<unsigned long long>(task.side) << 40) |
+                                  (static_cast<unsigned long long>(task.kappa) << 48) |
+                                  (static_cast<unsigned long long>(accept ? 1 : 0) << 56);
+  E.hash[ev] = fnv1a64(E.hash[ev], word);
+  if (!accept) return kCycleVetoed;
+  if (n >= E.cap) {
+    finish_event(E, ev, GAPS_OVERFLOW, exp(task.lnt));
+    return kCycleFinished;
+  }
+  task.ev = ev;
+  task.rz_hi = rw.x;
+  task.rz_lo = rw.y;
+  task.n = n;
+  task.step = step;
+  return kCycleAccepted;
+}
+
+// Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours,
+// the new parton in slot n, and the dipoles whose invariant mass moved.
+__device__ void cycle_emit(const DevParams& P, const Events& E, const EmitTask& w) {
+  const int64_t ev = w.ev;
+  const uint32_t id = E.first + static_cast<uint32_t>(ev);
+  const double t = exp(w.lnt);
+  const double z = z_fp64(w.kind, w.zp, 1.0 / w.inv_ls, to_unit(w.rz_hi, w.rz_lo));
+  const double y = t / (w.q2 * z * (1.0 - z));
+  const U4 rphi = philox10(id, static_cast<uint32_t>(w.step), 1u, kDrawWinner, P.seed_lo, P.seed_hi);
+  double sphi, cphi;
+  sincospi(2.0 * to_unit(rphi.x, rphi.y), &sphi, &cphi);
+  const V4 a = load_p(E, w.i, ev);
+  const V4 b = load_p(E, w.k, ev);
+  V4 pi, pj, pb;
+  dipole_map(a, b, z, y, cphi, sphi, pi, pj, pb);
+  const int j = w.n;
+  store_p(E, w.i, ev, pi);
+  store_p(E, j, ev, pj);
+  store_p(E, w.k, ev, pb);
+  const size_t ai = E.at(w.i, ev), aj = E.at(j, ev);
+  if (w.kind == kGtoQQ) {
+    // g(c, a) -> q(c, 0) + qbar(0, a); the parton holding colour a now
+    // connects to the antiquark.
+    const int q = E.link[E.link_at(1, w.i, ev)];
+    E.flav[ai] = static_cast<int8_t>(w.kappa);
+    E.flav[aj] = static_cast<int8_t>(-w.kappa);
+    E.col[aj] = 0;
+    E.acol[aj] = E.acol[ai];
+    E.acol[ai] = 0;
+    E.link[E.link_at(1, w.i, ev)] = kNoLink;
+    E.link[E.link_at(0, j, ev)] = kNoLink;
+    E.link[E.link_at(1, j, ev)] = static_cast<uint8_t>(q);
+    E.link[E.link_at(0, q, ev)] = static_cast<uint8_t>(j);
+  } else {
+    // A gluon enters the shared colour line between splitter and spectator;
+    // the splitter takes the new line m.
+    const int m = E.next_colour[ev];
+    E.next_colour[ev] = m + 1;
+    E.flav[aj] = static_cast<int8_t>(kGluon);
+    if (w.side == 0) {
+      E.col[aj] = E.col[ai];
+      E.acol[aj] = static_cast<int16_t>(m);
+      E.col[ai] = static_cast<int16_t>(m);
+      E.link[E.link_at(0, w.i, ev)] = static_cast<uint8_t>(j);
+      E.link[E.link_at(0, j, ev)] = static_cast<uint8_t>(w.k);
+      E.link[E.link_at(1, j, ev)] = static_cast<uint8_t>(w.i);
+      E.link[E.link_at(1, w.k, ev)] = static_cast<uint8_t>(j);
+    } else {
+      E.col[aj] = static_cast<int16_t>(m);
+      E.acol[aj] = E.acol[ai];
+      E.acol[ai] = static_cast<int16_t>(m);
+      E.link[E.link_at(1, w.i, ev)] = static_cast<uint8_t>(j);
+      E.link[E.link_at(1, j, ev)] = static_cast<uint8_t>(w.k);
+      E.link[E.link_at(0, j, ev)] = static_cast<uint8_t>(w.i);
+      E.link[E.link_at(0, w.k, ev)] = static_cast<uint8_t>(j);
+    }
+  }
+  // Recompute every dipole with a moved parton once: dipole (x, side) and
+  // its partner's opposite side share Q^2; a pair whose partner is a moved
+  // parton listed earlier was already done from that side.
+  const int moved[3] = {w.i, j, w.k};
+  const V4 mp[3] = {pi, pj, pb};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int x = moved[m];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int k = E.link[E.link_at(side, x, ev)];
+      if (k == kNoLink) continue;
+      bool seen = false;
+#pragma unroll
+      for (int m2 = 0; m2 < m; ++m2) seen |= (k == moved[m2]);
+      if (seen) continue;
+      const DipoleEntry d = make_dipole(P, 2.0 * mdot(mp[m], load_p(E, k, ev)));
+      store_dipole(E, ev, x, side, d);
+      store_dipole(E, ev, k, 1 - side, d);
+    }
+  }
+  E.n_partons[ev] = j + 1;
+  E.n_emissions[ev] += 1;
+}
+
+}  // namespace gaps

@@ -26,7 +26,8 @@ class Batch(C.Structure):
                 ("first_event", C.c_uint32)]
 
 
-_LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "t", "weight", "hash",
+_LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "dq2", "dzp", "dinv", "t", "lnt",
+                  "weight", "hash",
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
                   "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "counters", "hist", "stats", "total_bytes"]
 
