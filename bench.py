@@ -39,6 +39,14 @@ OPS_PER_EMISSION = 206.0  # azimuth, transverse frame, dipole map
 FP64_PEAK_DFMA_PER_S = 5.03e11  # measured DFMA throughput of this GB300 (pipe probe)
 
 
+def kernels_outside_shower(capacity):
+    """Library kernels per pass besides the shower cycles: matrix element,
+    validation, the three bucketing kernels and one event-shape kernel per
+    multiplicity class (16, 32, 64, 128, 256 slots), histograms."""
+    classes = sum(1 for lo in (0, 16, 32, 64, 128) if capacity > lo)
+    return 1 + 1 + 3 + classes + 1
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,7 +292,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48,
                 "d2h_bytes_per_step": 8 * g.HIST_DOUBLES + len(bytes(g.Stats())),
                 "api": "gaps_run (parameters from host, histograms and statistics back to host)"},
-        "gpu_launches": int(args.steps * 4 + launches_total),
+        "gpu_launches": int(args.steps * kernels_outside_shower(args.capacity) + launches_total),
         "roofline": {"bound": "alu", "kernel": "k_step_plain (fused veto cycle)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak_tflops, "traffic": None,
@@ -299,7 +307,8 @@ def main():
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,
                                       "winners": st.sum_winners, "emissions": st.sum_emissions},
                    "max_steps": st.max_steps, "mean_partons": st.sum_partons / max(1, st.n_events),
-                   "fp64_fallback_cycles": int(counters[2]), "fp64_vetoes": int(counters[3])},
+                   "fp64_fallback_cycles": int(counters[2]), "fp64_vetoes": int(counters[3]),
+                   "fp64_thrust_searches": int(counters[4]), "durham_multi_candidate_merges": int(counters[5])},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu

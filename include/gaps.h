@@ -102,8 +102,12 @@ typedef struct gaps_layout {
   int64_t me_flavour;     /* int32  [n_events] */
   int64_t valid;          /* int32  [n_events]: validation bits, 0 = valid */
   int64_t obs;            /* double [6][n_events]: y23, y34, y45, y56, 1-T, rho_H (-1 = undefined) */
+  int64_t buckets;        /* int32 [769]: scratch of gaps_observables (multiplicity buckets) */
+  int64_t order;          /* int32 [n_events]: scratch of gaps_observables (events by multiplicity) */
   int64_t counters;       /* uint64 [16]: device counters of the last shower call: 0 finished events,
-                             1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64 */
+                             1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
+                             of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
+                             merges with several FP64 candidates */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t total_bytes;

@@ -59,6 +59,8 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->me_flavour = take(4 * n);
   L->valid = take(4 * n);
   L->obs = take(8 * 6 * n);
+  L->buckets = take(4 * 769);
+  L->order = take(4 * n);
   L->counters = take(8 * 16);
   L->hist = take(8 * GAPS_HIST_DOUBLES);
   L->stats = take(sizeof(gaps_stats));
@@ -133,6 +135,8 @@ Events make_events(const gaps_batch& b) {
   E.me_flavour = reinterpret_cast<int32_t*>(base + L.me_flavour);
   E.valid = reinterpret_cast<int32_t*>(base + L.valid);
   E.obs = reinterpret_cast<double*>(base + L.obs);
+  E.buckets = reinterpret_cast<int*>(base + L.buckets);
+  E.order = reinterpret_cast<int*>(base + L.order);
   E.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
   E.hist = reinterpret_cast<double*>(base + L.hist);
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
@@ -267,7 +271,8 @@ int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stre
 int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* stream) {
   if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
   const cudaError_t e =
-      launch_observables(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+      launch_observables(make_dev_params(*params), make_events(*batch), make_events(*batch).buckets,
+                         make_events(*batch).order, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 

@@ -1,0 +1,367 @@
+// Observables of the finished events (Sec. 3.1): exact thrust and the
+// heavy-jet mass, and the Durham jet resolutions y23..y56.
+//
+// Layout of the work.  The finished events are first bucketed by parton
+// multiplicity (count, scan, scatter into an index list), so the threads of
+// a warp handle events of the same size: the O(n^3) loops of thrust and
+// Durham then run with no lane waiting on a larger neighbour.  One thread
+// handles one event, with per-thread arrays sized by the bucket (16, 32, 64,
+// 128 or 256 partons).
+//
+// Precision.  As in the shower, the searches run in FP32 and the answers in
+// FP64:
+//  * Thrust.  Every candidate partition P = sum s_i p_i of the exact
+//    algorithm (planes through every pair, both signs of the pair) is scored
+//    |P|^2 in FP32 and identified by its bitmask; the two best distinct
+//    partitions are tracked.  When the best beats the runner-up by more than
+//    the FP32 error bound, its |P| and axis are recomputed in FP64; otherwise
+//    (or for more than 64 partons) the whole search runs in FP64.
+//  * Durham.  Pair distances min(E_i^2, E_j^2) |u_i - u_j|^2 (u = unit
+//    momentum, free of the 1 - cos cancellation) are compared in FP32 with a
+//    per-pair error bound; every pair that could be the minimum is evaluated
+//    with the FP64 formula 2 min(E_i^2, E_j^2)(1 - cos theta_ij)/s, and the
+//    smallest of those is merged, ties to the first pair as in the oracle.
+#include "gaps_launch.hpp"
+
+namespace gaps {
+
+namespace {
+
+constexpr int kShapeThreads = 128;
+constexpr int kMaskMax = 64;
+
+// Exact FP64 thrust search (the fallback): planes through every pair with a
+// non-zero cross product, other momenta signed by their side, the pair tried
+// with both signs; the longest P is the thrust axis.
+template <int MAXJ>
+__device__ double thrust_fp64(int n, const double* jx, const double* jy, const double* jz, double sum_abs,
+                              double& ax, double& ay, double& az) {
+  double best2 = -1.0, bx = 0.0, by = 0.0, bz = 0.0;
+  for (int j = 0; j < n; ++j) {
+    for (int k = j + 1; k < n; ++k) {
+      const double nx = jy[j] * jz[k] - jz[j] * jy[k];
+      const double ny = jz[j] * jx[k] - jx[j] * jz[k];
+      const double nz = jx[j] * jy[k] - jy[j] * jx[k];
+      if (nx == 0.0 && ny == 0.0 && nz == 0.0) continue;
+      double px = 0.0, py = 0.0, pz = 0.0;
+      for (int i = 0; i < n; ++i) {
+        if (i == j || i == k) continue;
+        const double sg = (jx[i] * nx + jy[i] * ny + jz[i] * nz) >= 0.0 ? 1.0 : -1.0;
+        px += sg * jx[i];
+        py += sg * jy[i];
+        pz += sg * jz[i];
+      }
+      for (int c = 0; c < 4; ++c) {
+        const double fj = (c & 2) ? -1.0 : 1.0, fk = (c & 1) ? -1.0 : 1.0;
+        const double cx = px + fj * jx[j] + fk * jx[k];
+        const double cy = py + fj * jy[j] + fk * jy[k];
+        const double cz = pz + fj * jz[j] + fk * jz[k];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        if (c2 > best2) {
+          best2 = c2;
+          bx = cx;
+          by = cy;
+          bz = cz;
+        }
+      }
+    }
+  }
+  if (best2 < 0.0) {  // collinear: T = 1 along the first momentum
+    const double l = sqrt(jx[0] * jx[0] + jy[0] * jy[0] + jz[0] * jz[0]);
+    ax = jx[0] / l;
+    ay = jy[0] / l;
+    az = jz[0] / l;
+    return 1.0;
+  }
+  const double l = sqrt(best2);
+  ax = bx / l;
+  ay = by / l;
+  az = bz / l;
+  return l / sum_abs;
+}
+
+// Top two distinct partitions by score.
+struct Top2 {
+  float s1 = -1.0f, s2 = -1.0f;
+  unsigned long long m1 = 0ull, m2 = ~0ull;
+  __device__ __forceinline__ void add(float s, unsigned long long m) {
+    if (m == m1) {
+      s1 = fmaxf(s1, s);
+    } else if (s > s1) {
+      s2 = s1;
+      m2 = m1;
+      s1 = s;
+      m1 = m;
+    } else if (m == m2) {
+      s2 = fmaxf(s2, s);
+    } else if (s > s2) {
+      s2 = s;
+      m2 = m;
+    }
+  }
+};
+
+template <int MAXJ>
+__device__ void event_shapes(const DevParams& P, const Events& E, int64_t ev, int n) {
+  const int64_t N = E.n;
+  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
+  float fx[MAXJ], fy[MAXJ], fz[MAXJ];
+  double sum_abs = 0.0;
+  float sum_absf = 0.0f;
+  for (int i = 0; i < n; ++i) {
+    const size_t a = E.at(i, ev);
+    je[i] = E.e[a];
+    jx[i] = E.px[a];
+    jy[i] = E.py[a];
+    jz[i] = E.pz[a];
+    fx[i] = static_cast<float>(jx[i]);
+    fy[i] = static_cast<float>(jy[i]);
+    fz[i] = static_cast<float>(jz[i]);
+    sum_abs += sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+  }
+  sum_absf = static_cast<float>(sum_abs);
+
+  // ---- thrust
+  double thrust = 1.0, ax = 0.0, ay = 0.0, az = 0.0;
+  bool decided = false;
+  if (n == 2) {
+    // no emission: the pair is back to back, T = 1 along the quark
+    const double l = sqrt(jx[0] * jx[0] + jy[0] * jy[0] + jz[0] * jz[0]);
+    ax = jx[0] / l;
+    ay = jy[0] / l;
+    az = jz[0] / l;
+    decided = true;
+  } else if (n <= kMaskMax) {
+    Top2 top;
+    const unsigned long long full = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+    for (int j = 0; j < n; ++j) {
+      for (int k = j + 1; k < n; ++k) {
+        const float nx = fy[j] * fz[k] - fz[j] * fy[k];
+        const float ny = fz[j] * fx[k] - fx[j] * fz[k];
+        const float nz = fx[j] * fy[k] - fy[j] * fx[k];
+        if (nx == 0.0f && ny == 0.0f && nz == 0.0f) continue;
+        float px = 0.0f, py = 0.0f, pz = 0.0f;
+        unsigned long long mask = 0ull;
+        for (int i = 0; i < n; ++i) {
+          if (i == j || i == k) continue;
+          if (fx[i] * nx + fy[i] * ny + fz[i] * nz >= 0.0f) {
+            px += fx[i];
+            py += fy[i];
+            pz += fz[i];
+            mask |= 1ull << i;
+          } else {
+            px -= fx[i];
+            py -= fy[i];
+            pz -= fz[i];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const bool pj = !(c & 2), pk = !(c & 1);
+          const float cx = px + (pj ? fx[j] : -fx[j]) + (pk ? fx[k] : -fx[k]);
+          const float cy = py + (pj ? fy[j] : -fy[j]) + (pk ? fy[k] : -fy[k]);
+          const float cz = pz + (pj ? fz[j] : -fz[j]) + (pk ? fz[k] : -fz[k]);
+          unsigned long long m = mask | (pj ? 1ull << j : 0ull) | (pk ? 1ull << k : 0ull);
+          if (m & 1ull) m = ~m & full;  // a partition and its complement are one candidate
+          top.add(cx * cx + cy * cy + cz * cz, m);
+        }
+      }
+    }
+    // FP32 error of |P|^2: n rounded terms of size <= sum |p| per component.
+    const float margin = 8.0f * static_cast<float>(n + 2) * 6.0e-8f * sum_absf * sum_absf;
+    if (top.s1 < 0.0f) {
+      decided = false;  // no pair spans a plane: let the exact search decide
+    } else if (top.s2 < top.s1 - margin) {
+      double px = 0.0, py = 0.0, pz = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double sg = ((top.m1 >> i) & 1ull) ? 1.0 : -1.0;
+        px += sg * jx[i];
+        py += sg * jy[i];
+        pz += sg * jz[i];
+      }
+      const double l = sqrt(px * px + py * py + pz * pz);
+      thrust = l / sum_abs;
+      ax = px / l;
+      ay = py / l;
+      az = pz / l;
+      decided = true;
+    }
+  }
+  if (!decided) {
+    atomicAdd(&E.counters[4], 1ull);  // thrust decided by the exact FP64 search
+    thrust = thrust_fp64<MAXJ>(n, jx, jy, jz, sum_abs, ax, ay, az);
+  }
+  // Heavy-jet mass: hemispheres by the sign of p . n_T.
+  double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    double* h = (jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0) ? hp : hm;
+    h[0] += je[i];
+    h[1] += jx[i];
+    h[2] += jy[i];
+    h[3] += jz[i];
+  }
+  const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
+  const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
+  E.obs[4 * N + ev] = 1.0 - thrust;
+  E.obs[5 * N + ev] = fmax(mp, mm) / P.s;
+
+  // ---- Durham (E-scheme)
+  float fe2[MAXJ];
+  for (int i = 0; i < n; ++i) {
+    const float e = static_cast<float>(je[i]);
+    fe2[i] = e * e;
+    const float r = rsqrtf(fx[i] * fx[i] + fy[i] * fy[i] + fz[i] * fz[i]);
+    fx[i] *= r;  // from here on fx, fy, fz hold unit directions
+    fy[i] *= r;
+    fz[i] *= r;
+  }
+  double yres[4] = {-1.0, -1.0, -1.0, -1.0};
+  for (int m = n; m > 1; --m) {
+    // pass 1: the smallest upper bound of the FP32 distances
+    float ubest = INFINITY;
+    for (int i = 0; i < m; ++i) {
+      for (int j = i + 1; j < m; ++j) {
+        const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
+        const float d = dx * dx + dy * dy + dz * dz;
+        const float y = fminf(fe2[i], fe2[j]) * d;
+        const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
+        ubest = fminf(ubest, y * (1.0f + rel) + 1e-30f);
+      }
+    }
+    // pass 2: every pair whose lower bound reaches it, in FP64
+    double ymin = 0.0;
+    int bi = -1, bj = -1, n_exact = 0;
+    for (int i = 0; i < m; ++i) {
+      for (int j = i + 1; j < m; ++j) {
+        const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
+        const float d = dx * dx + dy * dy + dz * dz;
+        const float y = fminf(fe2[i], fe2[j]) * d;
+        const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
+        if (y * (1.0f - rel) > ubest) continue;
+        ++n_exact;
+        const double ai = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+        const double aj = sqrt(jx[j] * jx[j] + jy[j] * jy[j] + jz[j] * jz[j]);
+        const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ai * aj);
+        const double yy = 2.0 * fmin(je[i] * je[i], je[j] * je[j]) * (1.0 - cosij) / P.s;
+        if (bi < 0 || yy < ymin) {
+          ymin = yy;
+          bi = i;
+          bj = j;
+        }
+      }
+    }
+    if (n_exact > 1) atomicAdd(&E.counters[5], 1ull);  // merges with several FP64 candidates
+    const int idx = m - 3;
+    if (idx >= 0 && idx < 4) yres[idx] = ymin;
+    je[bi] += je[bj];
+    jx[bi] += jx[bj];
+    jy[bi] += jy[bj];
+    jz[bi] += jz[bj];
+    je[bj] = je[m - 1];
+    jx[bj] = jx[m - 1];
+    jy[bj] = jy[m - 1];
+    jz[bj] = jz[m - 1];
+    fe2[bj] = fe2[m - 1];
+    fx[bj] = fx[m - 1];
+    fy[bj] = fy[m - 1];
+    fz[bj] = fz[m - 1];
+    {
+      const float e = static_cast<float>(je[bi]);
+      fe2[bi] = e * e;
+      const float x = static_cast<float>(jx[bi]), y = static_cast<float>(jy[bi]), z = static_cast<float>(jz[bi]);
+      const float r = rsqrtf(x * x + y * y + z * z);
+      fx[bi] = x * r;
+      fy[bi] = y * r;
+      fz[bi] = z * r;
+    }
+  }
+  for (int h = 0; h < 4; ++h) E.obs[h * N + ev] = yres[h];
+}
+
+// ------------------------------------------------------------- buckets
+// counts[n] = finished events with n partons (n <= 255).
+__global__ void __launch_bounds__(256) k_bucket_count(Events E, int* counts) {
+  __shared__ int sh[256];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < E.n;
+       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (E.status[ev] == GAPS_DONE) atomicAdd(&sh[E.n_partons[ev]], 1);
+  }
+  __syncthreads();
+  if (sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
+}
+
+// offsets[n] = first position of bucket n; cursor[n] = offsets[n];
+// offsets[256] = number of finished events.
+__global__ void __launch_bounds__(256) k_bucket_scan(const int* counts, int* offsets, int* cursor) {
+  __shared__ int sh[256];
+  const int t = threadIdx.x;
+  sh[t] = counts[t];
+  __syncthreads();
+  for (int d = 1; d < 256; d <<= 1) {
+    const int v = t >= d ? sh[t - d] : 0;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  const int excl = t ? sh[t - 1] : 0;
+  offsets[t] = excl;
+  cursor[t] = excl;
+  if (t == 255) offsets[256] = sh[255];
+}
+
+// Finished events go to their bucket; the others get undefined observables.
+__global__ void __launch_bounds__(256) k_bucket_scatter(Events E, int* cursor, int* order) {
+  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (ev >= E.n) return;
+  if (E.status[ev] == GAPS_DONE) {
+    order[atomicAdd(&cursor[E.n_partons[ev]], 1)] = static_cast<int>(ev);
+  } else {
+    for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.n + ev] = -1.0;
+  }
+}
+
+// Events of buckets n_lo..n_hi (all with n <= MAXJ).
+template <int MAXJ>
+__global__ void __launch_bounds__(kShapeThreads) k_event_shapes(DevParams P, Events E, const int* order,
+                                                                const int* offsets, int n_lo, int n_hi) {
+  const int begin = offsets[n_lo], end = offsets[n_hi + 1 > 256 ? 256 : n_hi + 1];
+  for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end; k += gridDim.x * blockDim.x) {
+    const int64_t ev = order[k];
+    event_shapes<MAXJ>(P, E, ev, E.n_partons[ev]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int* counts = buckets;
+  int* offsets = buckets + 256;
+  int* cursor = buckets + 256 + 257;
+  cudaError_t e = cudaMemsetAsync(counts, 0, 256 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(E.counters + 4, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (E.n + 255) / 256;
+  const unsigned grid_count = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
+  k_bucket_count<<<grid_count, 256, 0, s>>>(E, counts);
+  k_bucket_scan<<<1, 256, 0, s>>>(counts, offsets, cursor);
+  k_bucket_scatter<<<static_cast<unsigned>(want), 256, 0, s>>>(E, cursor, order);
+  // One launch per multiplicity class; grids cover the largest possible
+  // class and stride over the actual one.
+  const int64_t all = (E.n + kShapeThreads - 1) / kShapeThreads;
+  const unsigned big = static_cast<unsigned>(all < 16 * sms ? all : 16 * sms);
+  const unsigned small = static_cast<unsigned>(all < 2 * sms ? all : 2 * sms);
+  k_event_shapes<16><<<big, kShapeThreads, 0, s>>>(P, E, order, offsets, 0, 16);
+  if (E.cap > 16) k_event_shapes<32><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 17, 32);
+  if (E.cap > 32) k_event_shapes<64><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 33, 64);
+  if (E.cap > 64) k_event_shapes<128><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 65, 128);
+  if (E.cap > 128) k_event_shapes<256><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 129, 255);
+  return cudaGetLastError();
+}
+
+}  // namespace gaps

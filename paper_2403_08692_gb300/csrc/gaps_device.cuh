@@ -55,6 +55,8 @@ struct Events {
   int32_t *n_partons, *status, *n_steps, *n_emissions, *n_winners, *n_trials, *n_dipoles, *next_colour,
       *me_flavour, *valid;
   double* obs;  // [6][n]
+  int* buckets;  // [769] scratch of the observables' multiplicity buckets
+  int* order;    // [n] scratch: finished events ordered by multiplicity
   unsigned long long* counters;
   double* hist;
   gaps_stats* stats;

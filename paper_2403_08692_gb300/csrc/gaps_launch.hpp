@@ -12,7 +12,9 @@ Events make_events(const gaps_batch& b);
 cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);
 cudaError_t launch_step_plain(const DevParams& P, const Events& E, cudaStream_t s);
 cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s);
-cudaError_t launch_observables(const DevParams& P, const Events& E, cudaStream_t s);
+// buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
+// scratch [n_events].
+cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s);
 cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s);
 cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s);
 

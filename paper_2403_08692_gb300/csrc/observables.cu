@@ -1,5 +1,5 @@
-// Event validation, observables (Sec. 3.1: Durham jet resolutions, thrust,
-// heavy-jet mass), atomic histogramming (Sec. 3.2) and batch statistics.
+// Event validation, atomic histogramming of the observables (Sec. 3.2) and
+// batch statistics.
 #include "gaps_launch.hpp"
 
 namespace gaps {
@@ -89,131 +89,6 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P, Events E) {
     if (fsum[f] != 0) bits |= 16;
   (void)n_quarks;
   E.valid[ev] = bits;
-}
-
-// ----------------------------------------------------------- observables
-// One thread per event; the event's momenta are copied into a per-thread
-// array of MAXJ entries (MAXJ >= capacity).
-template <int MAXJ>
-__global__ void __launch_bounds__(128) k_observables(DevParams P, Events E) {
-  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (ev >= E.n) return;
-  double* obs = E.obs;
-  const int64_t N = E.n;
-  if (E.status[ev] != GAPS_DONE) {
-    for (int h = 0; h < 6; ++h) obs[h * N + ev] = -1.0;
-    return;
-  }
-  const int n = E.n_partons[ev];
-  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
-  for (int i = 0; i < n; ++i) {
-    const size_t a = E.at(i, ev);
-    je[i] = E.e[a];
-    jx[i] = E.px[a];
-    jy[i] = E.py[a];
-    jz[i] = E.pz[a];
-  }
-  const double s = P.s;
-
-  // Thrust (exact): planes through every pair (j, k) with p_j x p_k != 0,
-  // the other momenta signed by their side, the pair tried with both signs.
-  double sum_abs = 0.0;
-  for (int i = 0; i < n; ++i) sum_abs += sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
-  double best2 = -1.0, bx = 0.0, by = 0.0, bz = 0.0;
-  for (int j = 0; j < n; ++j) {
-    for (int k = j + 1; k < n; ++k) {
-      const double nx = jy[j] * jz[k] - jz[j] * jy[k];
-      const double ny = jz[j] * jx[k] - jx[j] * jz[k];
-      const double nz = jx[j] * jy[k] - jy[j] * jx[k];
-      if (nx == 0.0 && ny == 0.0 && nz == 0.0) continue;
-      double px = 0.0, py = 0.0, pz = 0.0;
-      for (int i = 0; i < n; ++i) {
-        if (i == j || i == k) continue;
-        const double d = jx[i] * nx + jy[i] * ny + jz[i] * nz;
-        const double sg = d >= 0.0 ? 1.0 : -1.0;
-        px += sg * jx[i];
-        py += sg * jy[i];
-        pz += sg * jz[i];
-      }
-      for (int c = 0; c < 4; ++c) {
-        const double fj = (c & 2) ? -1.0 : 1.0;
-        const double fk = (c & 1) ? -1.0 : 1.0;
-        const double cx = px + fj * jx[j] + fk * jx[k];
-        const double cy = py + fj * jy[j] + fk * jy[k];
-        const double cz = pz + fj * jz[j] + fk * jz[k];
-        const double c2 = cx * cx + cy * cy + cz * cz;
-        if (c2 > best2) {
-          best2 = c2;
-          bx = cx;
-          by = cy;
-          bz = cz;
-        }
-      }
-    }
-  }
-  double thrust, ax, ay, az;
-  if (best2 < 0.0) {
-    const double l = sqrt(jx[0] * jx[0] + jy[0] * jy[0] + jz[0] * jz[0]);
-    thrust = 1.0;
-    ax = jx[0] / l;
-    ay = jy[0] / l;
-    az = jz[0] / l;
-  } else {
-    const double l = sqrt(best2);
-    thrust = l / sum_abs;
-    ax = bx / l;
-    ay = by / l;
-    az = bz / l;
-  }
-  // Heavy-jet mass: hemispheres by the sign of p . n_T.
-  double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
-  for (int i = 0; i < n; ++i) {
-    double* h = (jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0) ? hp : hm;
-    h[0] += je[i];
-    h[1] += jx[i];
-    h[2] += jy[i];
-    h[3] += jz[i];
-  }
-  const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
-  const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
-  obs[4 * N + ev] = 1.0 - thrust;
-  obs[5 * N + ev] = fmax(mp, mm) / s;
-
-  // Durham (E-scheme): merge the pair of smallest y_ij = 2 min(E_i^2, E_j^2)
-  // (1 - cos theta_ij) / s until one jet is left; the merge from n+1 to n
-  // jets records y_{n,n+1}.
-  double yres[4] = {-1.0, -1.0, -1.0, -1.0};
-  int m = n;
-  while (m > 1) {
-    double ymin = 0.0;
-    int bi = -1, bj = -1;
-    for (int i = 0; i < m; ++i) {
-      const double ai = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
-      for (int j = i + 1; j < m; ++j) {
-        const double aj = sqrt(jx[j] * jx[j] + jy[j] * jy[j] + jz[j] * jz[j]);
-        const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ai * aj);
-        const double e2 = fmin(je[i] * je[i], je[j] * je[j]);
-        const double y = 2.0 * e2 * (1.0 - cosij) / s;
-        if (bi < 0 || y < ymin) {
-          ymin = y;
-          bi = i;
-          bj = j;
-        }
-      }
-    }
-    const int idx = m - 3;
-    if (idx >= 0 && idx < 4) yres[idx] = ymin;
-    je[bi] += je[bj];
-    jx[bi] += jx[bj];
-    jy[bi] += jy[bj];
-    jz[bi] += jz[bj];
-    je[bj] = je[m - 1];
-    jx[bj] = jx[m - 1];
-    jy[bj] = jy[m - 1];
-    jz[bj] = jz[m - 1];
-    --m;
-  }
-  for (int h = 0; h < 4; ++h) obs[h * N + ev] = yres[h];
 }
 
 // ---------------------------------------------------------- histograms
@@ -322,16 +197,6 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s)
   if (E.n == 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
   k_validate<<<blocks, 128, 0, s>>>(P, E);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_observables(const DevParams& P, const Events& E, cudaStream_t s) {
-  if (E.n == 0) return cudaSuccess;
-  const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
-  if (E.cap <= 32) k_observables<32><<<blocks, 128, 0, s>>>(P, E);
-  else if (E.cap <= 64) k_observables<64><<<blocks, 128, 0, s>>>(P, E);
-  else if (E.cap <= 128) k_observables<128><<<blocks, 128, 0, s>>>(P, E);
-  else k_observables<256><<<blocks, 128, 0, s>>>(P, E);
   return cudaGetLastError();
 }
 

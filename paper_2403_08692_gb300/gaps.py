@@ -29,7 +29,8 @@ class Batch(C.Structure):
 _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "dq2", "dzp", "dinv", "t", "lnt",
                   "weight", "hash",
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
-                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "counters", "hist", "stats", "total_bytes"]
+                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "counters", "hist",
+                  "stats", "total_bytes"]
 
 
 class Layout(C.Structure):
