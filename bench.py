@@ -27,16 +27,25 @@ if ROOT not in sys.path:
 METRIC = "showered events/sec on 1 GB300 (10^6 LEP events) vs plain GPU; p50/p99 job latency"
 UNIT = "events/s"
 
-# Algorithmic FP64 work of the veto algorithm as the oracle computes it, in
-# DFMA-equivalent operations per unit (+, -, x and a fused a*b+c count 1;
-# division, square root, log and exp count their measured cost on this GPU
-# relative to one DFMA: 6.6, 9.6, 31, 17).  Units are counted exactly by the
-# kernel: dipoles evaluated, trials, winners and accepted emissions.
-OPS_PER_DIPOLE = 65.0     # Q^2, z+-, ln(z+/z-)
-OPS_PER_TRIAL = 61.0      # c, t r^(1/c) via log and exp, comparison
-OPS_PER_WINNER = 168.0    # z inversion, y, alpha_s(t), P / P^over, veto
-OPS_PER_EMISSION = 206.0  # azimuth, transverse frame, dipole map
-FP64_PEAK_DFMA_PER_S = 5.03e11  # measured DFMA throughput of this GB300 (pipe probe)
+# Required FP64 work of the shower cycle: the FP64 arithmetic an
+# oracle-exact result cannot avoid, counted from the oracle's formulas.
+# Trial ranking and veto decisions give the same outcome in FP32 and are not
+# counted.  "simple" = +, -, x or a fused a*b+c; the other operations are
+# converted to DFMA-equivalents with their throughput measured on the device
+# in the same run (gaps_probe_fp64_rates).
+#   per winner:   ln r and the scaled update of ln t
+#   per emission: t = exp(ln t), z (expm1), y, the azimuth (sincospi), the
+#                 dipole map (transverse frame, k_perp, three momenta) and
+#                 four dipole-cache refreshes (Q^2, z+, ln(z+/z-), 1/ln)
+WORK_PER_WINNER = {"simple": 5, "log": 1}
+WORK_PER_EMISSION = {"simple": 164, "div": 18, "sqrt": 7, "log": 4, "exp": 2, "sincospi": 1}
+# FP64 units: two DFMA per SM per clock (the sm__sass_thread_inst_executed_op_dfma
+# peak ncu reports for this GB300), two flops per DFMA.
+DFMA_PER_SM_PER_CLOCK = 2
+
+
+def dfma_equivalents(counts, rates):
+    return sum(n * (1.0 if op == "simple" else rates["dfma"] / rates[op]) for op, n in counts.items())
 
 
 def kernels_outside_shower(capacity):
@@ -250,12 +259,16 @@ def main():
     # per-event work units of one pass (identical every step)
     g.reduce_stats(ws, stats_dev, stream)
     st = g.Stats.from_buffer_copy(stats_dev.cpu().numpy().tobytes()[:len(bytes(g.Stats()))])
-    ops_per_pass = (OPS_PER_DIPOLE * st.sum_dipoles + OPS_PER_TRIAL * st.sum_trials +
-                    OPS_PER_WINNER * st.sum_winners + OPS_PER_EMISSION * st.sum_emissions)
+    rates = g.probe_fp64_rates(stream)
+    dfma_per_winner = dfma_equivalents(WORK_PER_WINNER, rates)
+    dfma_per_emission = dfma_equivalents(WORK_PER_EMISSION, rates)
+    dfma_per_pass = dfma_per_winner * st.sum_winners + dfma_per_emission * st.sum_emissions
     launches_per_pass = launches_total / args.steps
     kernel_s_per_launch = kernel_ms_total / 1e3 / launches_total
-    achieved_tflops = 2.0 * ops_per_pass / (kernel_ms_total / 1e3 / args.steps) / 1e12
-    peak_tflops = 2.0 * FP64_PEAK_DFMA_PER_S / 1e12
+    achieved_tflops = 2.0 * dfma_per_pass / (kernel_ms_total / 1e3 / args.steps) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = 2.0 * DFMA_PER_SM_PER_CLOCK * sms * clock_mhz * 1e6 / 1e12
 
     # end to end through the C ABI with host buffers: params in, histograms and
     # statistics out, every step
@@ -296,12 +309,16 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_step_plain (fused veto cycle)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak_tflops, "traffic": None,
-                     "peak_source": "FP64 DFMA throughput measured on this GB300 by a pipe probe "
-                                    "(MEASURED_PEAKS.json has no FP64 entry)",
-                     "work_model": "FP64 DFMA-equivalent ops of the oracle's formulas per dipole, trial, "
-                                   "winner and emission, x2 flops",
+                     "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "
+                                    f"x {clock_mhz:.0f} MHz (median SM clock under load) x 2 flops; "
+                                    f"MEASURED_PEAKS.json has no FP64 entry",
+                     "work_model": f"required FP64 work: {dfma_per_winner:.1f} DFMA-equivalents per winner, "
+                                   f"{dfma_per_emission:.1f} per accepted emission (oracle formulas; "
+                                   f"transcendentals at their measured cost), x2 flops",
                      "launches_per_pass": launches_per_pass,
-                     "avg_launch_ms": kernel_s_per_launch * 1e3},
+                     "avg_launch_ms": kernel_s_per_launch * 1e3,
+                     "fp64_probe_per_s": {k: float(f"{v:.4g}") for k, v in rates.items()},
+                     "probe_dfma_tflops": 2.0 * rates["dfma"] / 1e12},
         "clocks": clocks,
         "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,

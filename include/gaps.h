@@ -207,6 +207,12 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
              gaps_stats* host_stats, void* stream);
 
 /* --------------------------------------------------------------- misc */
+
+/* Measurement helper (no counterpart in the paper): FP64 results per second
+ * of this GPU with every SM busy, for DFMA, log, exp, division, sqrt and
+ * sincospi, in host_rates[0..5].  device_sink: one device double, never
+ * written in practice.  Synchronous; about 50 ms. */
+int gaps_probe_fp64_rates(double* device_sink, double* host_rates, void* stream);
 const char* gaps_strerror(int status);
 const char* gaps_last_cuda_error(void);
 /* Library version as major * 10000 + minor * 100 + patch. */

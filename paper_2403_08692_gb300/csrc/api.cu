@@ -77,6 +77,8 @@ int check_batch(const gaps_batch* b) {
 
 }  // namespace
 
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 DevParams make_dev_params(const gaps_params& p) {
   DevParams d{};
   d.sqrt_s = p.sqrt_s;

@@ -7,6 +7,8 @@
 namespace gaps {
 
 DevParams make_dev_params(const gaps_params& p);
+// Remember a CUDA error for gaps_last_cuda_error() and return GAPS_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
 Events make_events(const gaps_batch& b);
 
 cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);

@@ -31,8 +31,14 @@
 
 namespace gaps {
 
-// Error allowances of the FP32 screens: several times the worst-case error of
-// the FP32 operations involved (derivation in the design notes).
+// Error allowances of the FP32 screens, several times the worst-case error of
+// the FP32 operations involved.  Trial key = log2(r) * (1/c): the 24-bit
+// uniform is within 2^-22 relative of r (3.4e-7 absolute in log2 r), MUFU
+// log2 adds at most 2e-6 (1 + |log2 r|), the cached 1/c is within 1e-6
+// relative, the product rounds once; so |key error| <= 2e-6/c + 7e-6 |key|,
+// allowed as 4e-6/c + 1.6e-5 |key|.  Veto ratio: z, 1 - z and y from MUFU
+// exp/log and ~20 FP32 operations carry <= 1e-5 relative error and (1 - y)
+// <= 5e-6 absolute, allowed as 5e-5 (ratio + r) + 2e-5.
 constexpr float kKeyRelInvc = 4e-6f;
 constexpr float kKeyRelKey = 1.6e-5f;
 constexpr float kVetoRel = 5e-5f;

@@ -65,6 +65,7 @@ SIGNATURES = {
     "gaps_histograms": (C.c_int, [_P(Params), _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_reduce_stats": (C.c_int, [_P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_run": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_double), _P(Stats), C.c_void_p]),
+    "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
     "gaps_last_cuda_error": (C.c_char_p, []),
     "gaps_version": (C.c_int, []),
@@ -180,6 +181,17 @@ def histograms(p, ws, hist_device, stream=None):
 def reduce_stats(ws, stats_device, stream=None):
     _check(load().gaps_reduce_stats(C.byref(_batch(ws)), C.c_void_p(stats_device.data_ptr()),
                                     _stream_handle(stream)), "gaps_reduce_stats")
+
+
+def probe_fp64_rates(stream=None):
+    """FP64 results per second of this GPU: dict of dfma, log, exp, div, sqrt,
+    sincospi."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rates = (C.c_double * 6)()
+    _check(load().gaps_probe_fp64_rates(C.c_void_p(sink.data_ptr()), rates, _stream_handle(stream)),
+           "gaps_probe_fp64_rates")
+    return dict(zip(("dfma", "log", "exp", "div", "sqrt", "sincospi"), list(rates)))
 
 
 def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):
