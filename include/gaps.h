@@ -206,6 +206,39 @@ int gaps_reduce_stats(const gaps_batch* batch, gaps_stats* stats_device, void* s
 int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, double* host_hist,
              gaps_stats* host_stats, void* stream);
 
+/* ------------------------------------------------- allocation-free entry */
+
+/* Largest batch gaps_event_shapes_noalloc accepts. */
+#define GAPS_NOALLOC_MAX_EVENTS (1 << 20)
+
+/* The observables stage of gaps_observables (Durham y23..y56, 1-T, rho_H)
+ * for callers that cannot allocate device memory -- code that must stay
+ * inside another framework's memory pool, plug-ins whose host forbids
+ * allocation calls, or processes that hand out all device memory up front.
+ * The paper has no counterpart; it is a deployment variant.  The caller
+ * passes only inputs and outputs: momenta px, py, pz, e as slot-major
+ * [capacity][n_events] doubles (the workspace layout), n_partons and status
+ * (int32 [n_events]), and obs (double [6][n_events], written: -1 for events
+ * whose status is not GAPS_DONE and for undefined y values).  The working
+ * arrays live in one fixed device array inside the library (about 4.2 MB,
+ * held by every GPU that loads the library until the process exits), so the
+ * call allocates nothing and calls no allocating routine.
+ * Limits and behaviour:
+ *  - n_events <= GAPS_NOALLOC_MAX_EVENTS, 4 <= capacity <= 255, sqrt_s > 0,
+ *    else GAPS_ERR_INVALID before any work; n_events == 0 is a no-op.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture on the device.
+ *  - All calls share the array and it keeps the last call's contents; each
+ *    call clears what must start at zero on its own stream.  Calls whose
+ *    work overlaps on the GPU race on the array: order them on one stream or
+ *    synchronise between them.
+ *  - Asynchronous on `stream`; results equal gaps_observables' for the same
+ *    events. */
+int gaps_event_shapes_noalloc(const double* px, const double* py, const double* pz, const double* e,
+                              const int32_t* n_partons, const int32_t* status, int64_t n_events,
+                              int32_t capacity, double sqrt_s, double* obs, void* stream);
+
 /* --------------------------------------------------------------- misc */
 
 /* Measurement helper (no counterpart in the paper): FP64 results per second

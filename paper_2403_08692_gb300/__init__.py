@@ -11,5 +11,5 @@ from .gaps import (  # noqa: F401
     ACTIVE, DONE, OVERFLOW, STEP_LIMIT, SHOWER_PLAIN, HIST_DOUBLES, N_OBS, HIST_ROW,
     GapsError, Params, Stats, Workspace, check_params, generate_me, histograms, layout, load, shower_timed,
     make_params, observables, reduce_stats, run, shower, shower_step, validate, workspace_bytes,
-    probe_fp64_rates,
+    event_shapes_noalloc, probe_fp64_rates,
 )

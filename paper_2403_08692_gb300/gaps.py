@@ -65,6 +65,9 @@ SIGNATURES = {
     "gaps_histograms": (C.c_int, [_P(Params), _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_reduce_stats": (C.c_int, [_P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_run": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_double), _P(Stats), C.c_void_p]),
+    "gaps_event_shapes_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
+                                            C.c_void_p]),
     "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
     "gaps_last_cuda_error": (C.c_char_p, []),
@@ -192,6 +195,19 @@ def probe_fp64_rates(stream=None):
     _check(load().gaps_probe_fp64_rates(C.c_void_p(sink.data_ptr()), rates, _stream_handle(stream)),
            "gaps_probe_fp64_rates")
     return dict(zip(("dfma", "log", "exp", "div", "sqrt", "sincospi"), list(rates)))
+
+
+NOALLOC_MAX_EVENTS = 1 << 20
+
+
+def event_shapes_noalloc(px, py, pz, e, n_partons, status, n_events, capacity, sqrt_s, obs, stream=None):
+    """gaps_event_shapes_noalloc on caller-owned device tensors (no workspace,
+    no allocation): momenta [capacity][n_events] float64, n_partons and
+    status int32 [n_events]; writes obs [6][n_events] float64."""
+    ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)
+    _check(load().gaps_event_shapes_noalloc(ptr(px), ptr(py), ptr(pz), ptr(e), ptr(n_partons), ptr(status),
+                                            int(n_events), int(capacity), float(sqrt_s), ptr(obs),
+                                            _stream_handle(stream)), "gaps_event_shapes_noalloc")
 
 
 def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):
