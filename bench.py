@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle events for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-variants", action="store_true", help="skip the persistent-form variants")
     return ap.parse_args()
 
 
@@ -270,6 +271,69 @@ def main():
     clock_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = 2.0 * DFMA_PER_SM_PER_CLOCK * sms * clock_mhz * 1e6 / 1e12
 
+    # The batched persistent form on the same workload: autotuned launch shape,
+    # the whole pass captured once in a CUDA graph and replayed (no host
+    # synchronisation inside the pass).  Same events as the plain form.
+    variants = {}
+    if not args.no_variants:
+        cfg, _ = g.autotune_persistent(p, ws, stream)
+
+        def pass_persistent():
+            hist_dev.zero_()
+            g.generate_me(p, ws, stream)
+            g.shower_persistent(p, ws, cfg, stream)
+            g.validate(p, ws, stream)
+            g.observables(p, ws, stream)
+            g.histograms(p, ws, hist_dev, stream)
+
+        for _ in range(3):
+            pass_persistent()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pass_persistent()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        variants["persistent"] = {"value": n * args.steps / (sum(times) / 1e3), "unit": UNIT,
+                                  "ms_per_step": sum(times) / args.steps, "config": cfg.as_dict(),
+                                  "launches_per_pass": kernels_outside_shower(args.capacity) + 1}
+        # CUDA graph of the whole pass
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            pass_persistent()  # warm-up on the capture stream
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                hist_dev.zero_()
+                g.generate_me(p, ws, side)
+                g.shower_persistent(p, ws, cfg, side)
+                g.validate(p, ws, side)
+                g.observables(p, ws, side)
+                g.histograms(p, ws, hist_dev, side)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            replay_stream = torch.cuda.current_stream()  # replay() launches on the current stream
+            e0.record(replay_stream)
+            graph.replay()
+            e1.record(replay_stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        variants["persistent_graph"] = {"value": n * args.steps / (sum(times) / 1e3), "unit": UNIT,
+                                        "ms_per_step": sum(times) / args.steps}
+        del graph
+
     # end to end through the C ABI with host buffers: params in, histograms and
     # statistics out, every step
     host_hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64).pin_memory()
@@ -320,6 +384,7 @@ def main():
                      "fp64_probe_per_s": {k: float(f"{v:.4g}") for k, v in rates.items()},
                      "probe_dfma_tflops": 2.0 * rates["dfma"] / 1e12},
         "clocks": clocks,
+        "variants": variants,
         "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,
                                       "winners": st.sum_winners, "emissions": st.sum_emissions},

@@ -104,10 +104,12 @@ typedef struct gaps_layout {
   int64_t obs;            /* double [6][n_events]: y23, y34, y45, y56, 1-T, rho_H (-1 = undefined) */
   int64_t buckets;        /* int32 [769]: scratch of gaps_observables (multiplicity buckets) */
   int64_t order;          /* int32 [n_events]: scratch of gaps_observables (events by multiplicity) */
+  int64_t active;         /* int32 [2][n_events]: scratch of the plain shower (active-event lists) */
   int64_t counters;       /* uint64 [16]: device counters of the last shower call: 0 finished events,
                              1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
-                             merges with several FP64 candidates */
+                             merges with several FP64 candidates; 6 the persistent form's event cursor;
+                             8, 9 the plain form's active-list lengths */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t total_bytes;
@@ -132,10 +134,22 @@ typedef struct gaps_stats {
   double sum_weight2;
 } gaps_stats;
 
-/* Shower forms for gaps_shower(). */
+/* Shower forms for gaps_shower() and gaps_run(). */
 enum {
-  GAPS_SHOWER_PLAIN = 0 /* one launch per veto cycle over all events, host all-done check (App. C) */
+  GAPS_SHOWER_PLAIN = 0,     /* one launch per veto cycle over all events, host all-done check (App. C) */
+  GAPS_SHOWER_PERSISTENT = 1 /* one launch; per-block event pools, compaction and refill (no host loop) */
 };
+
+/* Launch shape of the persistent form.  block_threads: 64, 128, 256 or 512
+ * events per block pool; compact_period: veto cycles between compactions
+ * and refills of a pool (>= 1); blocks_per_sm: resident blocks per SM (0 =
+ * as many as fit). */
+typedef struct gaps_persistent_config {
+  int32_t block_threads;
+  int32_t compact_period;
+  int32_t blocks_per_sm;
+  int32_t reserved; /* must be 0 */
+} gaps_persistent_config;
 
 /* ---------------------------------------------------------------- sizing */
 
@@ -172,6 +186,25 @@ int gaps_shower(const gaps_params* params, const gaps_batch* batch, int mode, in
  * CUDA events recorded on `stream` around every launch. */
 int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                       double* kernel_ms_out, void* stream);
+
+/* The persistent form (Sec. 2, without the cutoff wait of Fig. 3): one
+ * launch runs every event to the cutoff.  Each block keeps a pool of events,
+ * runs cfg->compact_period veto cycles on it, packs the still-active events
+ * to the front (warp ballot) and refills the free threads from a global
+ * event cursor.  Events are identical to the plain form's (same draws, same
+ * cycle code).  cfg = NULL uses {256, 1, 0}.  Fully asynchronous: no host
+ * synchronisation; the workspace counters record finished and step-limited
+ * events. */
+int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
+                           const gaps_persistent_config* cfg, void* stream);
+
+/* Autotuner of the persistent form: times every block size in {128, 256,
+ * 512} with compaction periods {1, 2, 4} on this batch (matrix element +
+ * shower each time, CUDA events on `stream`) and returns the fastest in
+ * *best (and its time in *best_ms, may be NULL).  Overwrites the batch's
+ * events.  Synchronous. */
+int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch, gaps_persistent_config* best,
+                             double* best_ms, void* stream);
 
 /* One veto cycle of the plain form for every active event (one launch). */
 int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* stream);

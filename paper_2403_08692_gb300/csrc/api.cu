@@ -61,6 +61,7 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->obs = take(8 * 6 * n);
   L->buckets = take(4 * 769);
   L->order = take(4 * n);
+  L->active = take(8 * n);
   L->counters = take(8 * 16);
   L->hist = take(8 * GAPS_HIST_DOUBLES);
   L->stats = take(sizeof(gaps_stats));
@@ -139,6 +140,7 @@ Events make_events(const gaps_batch& b) {
   E.obs = reinterpret_cast<double*>(base + L.obs);
   E.buckets = reinterpret_cast<int*>(base + L.buckets);
   E.order = reinterpret_cast<int*>(base + L.order);
+  E.active = reinterpret_cast<int*>(base + L.active);
   E.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
   E.hist = reinterpret_cast<double*>(base + L.hist);
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
@@ -190,16 +192,32 @@ int gaps_generate_me(const gaps_params* params, const gaps_batch* batch, void* s
 int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* stream) {
   if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
   const cudaError_t e =
-      launch_step_plain(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+      launch_step_plain(make_dev_params(*params), make_events(*batch), nullptr, batch->n_events, nullptr, nullptr,
+                        nullptr, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 namespace {
 
+constexpr gaps_persistent_config kDefaultPersistent = {256, 1, 0, 0};
+
+bool config_ok(const gaps_persistent_config& c) {
+  const bool threads_ok = c.block_threads == 64 || c.block_threads == 128 || c.block_threads == 256 ||
+                          c.block_threads == 512;
+  return threads_ok && c.compact_period >= 1 && c.compact_period <= 64 && c.blocks_per_sm >= 0 &&
+         c.blocks_per_sm <= 32 && c.reserved == 0;
+}
+
+// Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
+// persistent form's event cursor).
+cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
+  return cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
+}
+
 int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                 double* kernel_ms_out, void* stream) {
   if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
-  if (mode != GAPS_SHOWER_PLAIN) return GAPS_ERR_INVALID;
+  if (mode != GAPS_SHOWER_PLAIN && mode != GAPS_SHOWER_PERSISTENT) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const DevParams P = make_dev_params(*params);
   const Events E = make_events(*batch);
@@ -221,24 +239,50 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
       if (b) cudaEventDestroy(b);
     }
   } guard{ev0, ev1};
-  e = cudaMemsetAsync(E.counters, 0, 4 * sizeof(unsigned long long), s);
+  e = clear_shower_counters(E, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  // The host loop of App. C: one cycle for every event per launch, then the
-  // finished-event counter is read back; an event stops after max_steps
-  // cycles, so the loop ends after at most max_steps + 1 launches.
   unsigned long long cnt[2] = {0, 0};  // finished events, events stopped at max_steps
-  double total_ms = 0.0;
-  while (cnt[0] < static_cast<unsigned long long>(E.n)) {
-    if (launches > static_cast<int64_t>(P.max_steps)) break;
+  if (mode == GAPS_SHOWER_PERSISTENT) {
     if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
-    e = launch_step_plain(P, E, s);
+    e = launch_shower_persistent(P, E, kDefaultPersistent, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
+    e = cudaMemcpyAsync(cnt, E.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ev0) {
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, ev0, ev1)) != cudaSuccess) return cuda_fail(e);
+      *kernel_ms_out = ms;
+    }
+    if (launches_out) *launches_out = 1;
+    return cnt[1] > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
+  }
+  // The host loop of App. C: one cycle for every active event per launch,
+  // then the host reads back how many events are still active.  Each launch
+  // appends its survivors to the other half of the active-list double
+  // buffer, so the next launch covers only those.  An event stops after
+  // max_steps cycles, so the loop ends after at most max_steps + 1 launches.
+  double total_ms = 0.0;
+  unsigned long long readback[10] = {0};  // counter words 0..9
+  int64_t n_in = E.n;
+  while (n_in > 0) {
+    if (launches > static_cast<int64_t>(P.max_steps)) break;
+    const int in_half = static_cast<int>(launches & 1), out_half = 1 - in_half;
+    const int* list_in = launches == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
+    int* list_out = E.active + static_cast<size_t>(out_half) * E.n;
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
+    e = launch_step_plain(P, E, list_in, n_in, list_out, &E.counters[8 + out_half], &E.counters[8 + in_half], s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
     ++launches;
-    e = cudaMemcpyAsync(cnt, E.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(readback, E.counters, sizeof(readback), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
+    cnt[0] = readback[0];
+    cnt[1] = readback[1];
+    n_in = static_cast<int64_t>(readback[8 + out_half]);
     if (ev0) {
       float ms = 0.0f;
       e = cudaEventElapsedTime(&ms, ev0, ev1);
@@ -261,6 +305,58 @@ int gaps_shower(const gaps_params* params, const gaps_batch* batch, int mode, in
 int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                       double* kernel_ms_out, void* stream) {
   return shower_impl(params, batch, mode, launches_out, kernel_ms_out, stream);
+}
+
+int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
+                           const gaps_persistent_config* cfg, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
+  if (!config_ok(c)) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Events E = make_events(*batch);
+  if (E.n == 0) return GAPS_OK;
+  cudaError_t e = clear_shower_counters(E, s);
+  if (e == cudaSuccess) e = launch_shower_persistent(make_dev_params(*params), E, c, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch, gaps_persistent_config* best,
+                             double* best_ms, void* stream) {
+  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !best) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevParams P = make_dev_params(*params);
+  const Events E = make_events(*batch);
+  *best = kDefaultPersistent;
+  if (best_ms) *best_ms = 0.0;
+  if (E.n == 0) return GAPS_OK;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  double best_time = -1.0;
+  const int threads[3] = {128, 256, 512};
+  const int periods[3] = {1, 2, 4};
+  for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
+    for (int pi = 0; pi < 3 && e == cudaSuccess; ++pi) {
+      const gaps_persistent_config c = {threads[ti], periods[pi], 0, 0};
+      e = launch_me(P, E, s);
+      if (e == cudaSuccess) e = clear_shower_counters(E, s);
+      if (e == cudaSuccess) e = cudaEventRecord(a, s);
+      if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && (best_time < 0.0 || ms < best_time)) {
+        best_time = ms;
+        *best = c;
+      }
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (best_ms) *best_ms = best_time;
+  return GAPS_OK;
 }
 
 int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream) {
@@ -298,15 +394,19 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
              gaps_stats* host_stats, void* stream) {
   if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !host_hist)
     return GAPS_ERR_INVALID;
-  if (mode != GAPS_SHOWER_PLAIN) return GAPS_ERR_INVALID;
+  if (mode != GAPS_SHOWER_PLAIN && mode != GAPS_SHOWER_PERSISTENT) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Events E = make_events(*batch);
   cudaError_t e = cudaMemsetAsync(E.hist, 0, sizeof(double) * GAPS_HIST_DOUBLES, s);
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = gaps_generate_me(params, batch, stream);
   if (rc != GAPS_OK) return rc;
-  int64_t launches = 0;
-  rc = gaps_shower(params, batch, mode, &launches, stream);
+  int64_t launches = 1;
+  if (mode == GAPS_SHOWER_PERSISTENT) {
+    rc = gaps_shower_persistent(params, batch, nullptr, stream);  // no host synchronisation
+  } else {
+    rc = gaps_shower(params, batch, mode, &launches, stream);
+  }
   if (rc != GAPS_OK && rc != GAPS_ERR_STEP_LIMIT) return rc;
   rc = gaps_validate(params, batch, stream);
   if (rc != GAPS_OK) return rc;

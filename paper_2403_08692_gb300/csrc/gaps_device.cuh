@@ -57,6 +57,7 @@ struct Events {
   double* obs;  // [6][n]
   int* buckets;  // [769] scratch of the observables' multiplicity buckets
   int* order;    // [n] scratch: finished events ordered by multiplicity
+  int* active;   // [2][n] scratch: the plain form's active-event lists
   unsigned long long* counters;
   double* hist;
   gaps_stats* stats;

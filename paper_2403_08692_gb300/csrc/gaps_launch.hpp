@@ -12,7 +12,14 @@ int record_cuda_error(cudaError_t e);
 Events make_events(const gaps_batch& b);
 
 cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);
-cudaError_t launch_step_plain(const DevParams& P, const Events& E, cudaStream_t s);
+// One plain-form cycle over list_in[0 .. n_in) (list_in = NULL: events
+// 0 .. n_in); survivors are appended to list_out (may be NULL) through
+// *out_count; *reset_count is zeroed.
+cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in, int* list_out,
+                              unsigned long long* out_count, unsigned long long* reset_count, cudaStream_t s);
+// Persistent form; counters word 6 is the event cursor and must be zero.
+cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
+                                     cudaStream_t s);
 cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s);
 // buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
 // scratch [n_events].

@@ -122,7 +122,7 @@ __device__ __forceinline__ double inv_c_fp64(const DevParams& P, int kind, doubl
 // momenta); the fallback of the FP32 screen.  The log-space scale of trial
 // j is L + ln(r_j)/c_j; the highest above ln t_C wins, the first on ties.
 // Returns false if no trial is above t_C.
-__device__ bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+__device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
                                    double lnt, EmitTask& w) {
   double best = P.ln_tc;
   bool found = false;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int st
 // Phase 1 of a cycle for active event ev.  Returns kCycleFinished when the
 // event left the active state (status written), kCycleAccepted with `task`
 // filled when an emission must be generated, kCycleVetoed otherwise.
-__device__ int cycle_select_veto(const DevParams& P, const Events& E, int64_t ev, EmitTask& task) {
+__device__ inline int cycle_select_veto(const DevParams& P, const Events& E, int64_t ev, EmitTask& task) {
   const uint32_t id = E.first + static_cast<uint32_t>(ev);
   const int n = E.n_partons[ev];
   const int step = E.n_steps[ev];
@@ -351,7 +351,7 @@ __device__ int cycle_select_veto(const DevParams& P, const Events& E, int64_t ev
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours,
 // the new parton in slot n, and the dipoles whose invariant mass moved.
-__device__ void cycle_emit(const DevParams& P, const Events& E, const EmitTask& w) {
+__device__ inline void cycle_emit(const DevParams& P, const Events& E, const EmitTask& w) {
   const int64_t ev = w.ev;
   const uint32_t id = E.first + static_cast<uint32_t>(ev);
   const double t = exp(w.lnt);

@@ -1,0 +1,120 @@
+// Persistent shower form: one launch runs every event to the cutoff.
+//
+// Each block keeps a pool of events, one per thread.  It runs `period` veto
+// cycles on the pool (select/veto for every live event, then the accepted
+// emissions by packed threads), then compacts the still-active events to the
+// front of the pool with a warp ballot and refills the freed threads from a
+// global event cursor (one atomic per block per round).  Events therefore
+// leave as soon as they finish -- the paper's cutoff inefficiency (Sec. 2,
+// Fig. 3: finished events wait for the last one) disappears -- and no
+// lane is spent on a finished event for more than `period` cycles.
+//
+// Nothing waits on another block: a block exits when its pool is empty and
+// the cursor has passed the last event.  Every event stops after at most
+// max_steps cycles (step-limit status), so the launch always terminates.
+// The per-event cycle is the same code as the plain form's, and every draw
+// is keyed by (seed, event, cycle), so both forms give identical events.
+#include "gaps_launch.hpp"
+#include "shower_cycle.cuh"
+
+namespace gaps {
+
+namespace {
+
+template <int T>
+__global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, int period) {
+  __shared__ int64_t s_pool[T];
+  __shared__ EmitTask s_task[T];
+  __shared__ int s_count[4];  // pool size, accepted emissions, refill base (low), refill count
+  __shared__ unsigned long long s_base;
+  const int tid = threadIdx.x;
+  unsigned long long* cursor = &E.counters[6];
+  int pool = 0;
+  for (;;) {
+    // Refill the free threads from the global cursor.
+    if (tid == 0) {
+      const int want = T - pool;
+      unsigned long long base = 0;
+      int take = 0;
+      if (want > 0) {
+        base = atomicAdd(cursor, static_cast<unsigned long long>(want));
+        const long long left = static_cast<long long>(E.n) - static_cast<long long>(base);
+        take = left <= 0 ? 0 : (left < want ? static_cast<int>(left) : want);
+      }
+      s_base = base;
+      s_count[3] = take;
+    }
+    __syncthreads();
+    const int take = s_count[3];
+    if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int64_t>(s_base) + (tid - pool);
+    pool += take;
+    __syncthreads();
+    if (pool == 0) break;
+
+    bool alive = tid < pool;
+    for (int c = 0; c < period; ++c) {
+      if (tid == 0) s_count[1] = 0;
+      __syncthreads();
+      if (alive) {
+        const int64_t ev = s_pool[tid];
+        EmitTask task;
+        const int r = cycle_select_veto(P, E, ev, task);
+        if (r == kCycleAccepted) {
+          s_task[atomicAdd(&s_count[1], 1)] = task;
+        } else if (r == kCycleFinished) {
+          alive = false;
+          atomicAdd(&E.counters[0], 1ull);
+          if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+        }
+      }
+      __syncthreads();
+      if (tid < s_count[1]) cycle_emit(P, E, s_task[tid]);
+      __syncthreads();
+    }
+
+    // Compact: the still-active events move to the front of the pool.
+    const int64_t mine = alive ? s_pool[tid] : 0;
+    if (tid == 0) s_count[0] = 0;
+    __syncthreads();
+    const unsigned mask = __ballot_sync(0xffffffffu, alive);
+    int base = 0;
+    if ((tid & 31) == 0 && mask) base = atomicAdd(&s_count[0], __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncthreads();
+    if (alive) s_pool[base + __popc(mask & ((1u << (tid & 31)) - 1u))] = mine;
+    pool = s_count[0];
+    __syncthreads();
+  }
+}
+
+template <int T>
+cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks_per_sm, cudaStream_t s) {
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T>, T, 0);
+  if (e != cudaSuccess) return e;
+  if (fit < 1) fit = 1;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
+  int64_t blocks = static_cast<int64_t>(sms) * per_sm;
+  const int64_t needed = (E.n + T - 1) / T;
+  if (blocks > needed) blocks = needed;
+  k_shower_persistent<T><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
+                                     cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  switch (cfg.block_threads) {
+    case 64: return launch_t<64>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 128: return launch_t<128>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 256: return launch_t<256>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 512: return launch_t<512>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gaps

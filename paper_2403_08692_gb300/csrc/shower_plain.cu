@@ -62,41 +62,79 @@ __global__ void __launch_bounds__(256) k_me(DevParams P, Events E) {
 }
 
 constexpr int kStepThreads = 256;
+constexpr int kStepWarps = kStepThreads / 32;
 
-// One veto cycle for the block's kStepThreads consecutive events.  The
-// block first packs its still-active events into the leading threads, so
-// finished events (the paper's endShower early exit) cost no warp time; the
-// accepted emissions are then packed again and generated by the leading
-// threads.  Counter word 0 counts finished events (the paper's
-// completedEventsCounter), word 1 those stopped by the veto-cycle limit.
-__global__ void __launch_bounds__(kStepThreads) k_step_plain(DevParams P, Events E) {
-  __shared__ int64_t s_ev[kStepThreads];
-  __shared__ EmitTask s_task[kStepThreads];
-  __shared__ int s_count[2];
-  const int tid = threadIdx.x;
-  if (tid == 0) s_count[0] = s_count[1] = 0;
+// Rank of this thread among the block's threads with `flag` set, in thread
+// order, and their number (*total).  Contains two block barriers.
+__device__ __forceinline__ int block_rank(bool flag, int* s_warp, int* total) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned mask = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) s_warp[warp] = __popc(mask);
   __syncthreads();
-  const int64_t ev0 = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
-  const bool active = ev0 < E.n && E.status[ev0] == GAPS_ACTIVE;
-  const unsigned mask = __ballot_sync(0xffffffffu, active);
-  int base = 0;
-  if ((tid & 31) == 0 && mask) base = atomicAdd(&s_count[0], __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (active) s_ev[base + __popc(mask & ((1u << (tid & 31)) - 1u))] = ev0;
-  __syncthreads();
-  if (tid < s_count[0]) {
-    const int64_t ev = s_ev[tid];
-    EmitTask task;
-    const int r = cycle_select_veto(P, E, ev, task);
-    if (r == kCycleAccepted) {
-      s_task[atomicAdd(&s_count[1], 1)] = task;
-    } else if (r == kCycleFinished) {
-      atomicAdd(&E.counters[0], 1ull);
-      if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+  if (tid == 0) {
+    int run = 0;
+    for (int w = 0; w < kStepWarps; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = run;
+      run += c;
     }
+    s_warp[kStepWarps] = run;
   }
   __syncthreads();
-  if (tid < s_count[1]) cycle_emit(P, E, s_task[tid]);
+  *total = s_warp[kStepWarps];
+  return s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
+}
+
+// One veto cycle over the events list_in[0 .. n_in) (the first cycle passes
+// no list: events 0 .. n_in).  The block packs its still-active events into
+// its leading threads in event order, so finished events (the paper's
+// endShower early exit) cost no warp time, runs the select/veto phase, packs
+// the accepted emissions again for the emission phase, and appends its
+// surviving events, in order, to list_out with one atomic per block.  The
+// host reads *out_count to size the next launch and to end the loop; this
+// launch zeroes *reset_count, the output counter of the next launch.
+// Counter word 0 counts finished events (the paper's
+// completedEventsCounter), word 1 those stopped by the veto-cycle limit.
+__global__ void __launch_bounds__(kStepThreads, 3)
+    k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, int* list_out,
+                 unsigned long long* out_count, unsigned long long* reset_count) {
+  __shared__ int64_t s_ev[kStepThreads];
+  __shared__ EmitTask s_task[kStepThreads];
+  __shared__ int s_warp[kStepWarps + 1];
+  __shared__ int s_naccept;
+  __shared__ unsigned long long s_out_base;
+  const int tid = threadIdx.x;
+  if (blockIdx.x == 0 && tid == 0 && reset_count) *reset_count = 0ull;
+  if (tid == 0) s_naccept = 0;
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
+  int64_t ev = -1;
+  if (idx < n_in) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
+  const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
+  int n_active = 0;
+  const int slot = block_rank(active, s_warp, &n_active);
+  if (active) s_ev[slot] = ev;
+  __syncthreads();
+  bool survive = false;
+  if (tid < n_active) {
+    const int64_t e = s_ev[tid];
+    EmitTask task;
+    const int r = cycle_select_veto(P, E, e, task);
+    if (r == kCycleAccepted) {
+      s_task[atomicAdd(&s_naccept, 1)] = task;
+    } else if (r == kCycleFinished) {
+      atomicAdd(&E.counters[0], 1ull);
+      if (E.status[e] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+    }
+    survive = r != kCycleFinished;
+  }
+  __syncthreads();
+  if (tid < s_naccept) cycle_emit(P, E, s_task[tid]);
+  if (!list_out) return;
+  int n_survive = 0;
+  const int rank = block_rank(survive, s_warp, &n_survive);
+  if (tid == 0 && n_survive > 0) s_out_base = atomicAdd(out_count, static_cast<unsigned long long>(n_survive));
+  __syncthreads();
+  if (survive) list_out[s_out_base + rank] = static_cast<int>(s_ev[tid]);
 }
 
 }  // namespace
@@ -109,10 +147,11 @@ cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_plain(const DevParams& P, const Events& E, cudaStream_t s) {
-  if (E.n == 0) return cudaSuccess;
-  const unsigned blocks = static_cast<unsigned>((E.n + kStepThreads - 1) / kStepThreads);
-  k_step_plain<<<blocks, kStepThreads, 0, s>>>(P, E);
+cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in, int* list_out,
+                              unsigned long long* out_count, unsigned long long* reset_count, cudaStream_t s) {
+  if (n_in <= 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((n_in + kStepThreads - 1) / kStepThreads);
+  k_step_plain<<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, list_out, out_count, reset_count);
   return cudaGetLastError();
 }
 

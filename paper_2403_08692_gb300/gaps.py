@@ -10,7 +10,7 @@ from . import build as _build
 
 GAPS_OK, GAPS_ERR_INVALID, GAPS_ERR_CUDA, GAPS_ERR_STEP_LIMIT, GAPS_ERR_NO_DEVICE = 0, -1, -2, -3, -4
 ACTIVE, DONE, OVERFLOW, STEP_LIMIT = 0, 1, 2, 3
-SHOWER_PLAIN = 0
+SHOWER_PLAIN, SHOWER_PERSISTENT = 0, 1
 N_OBS, N_BINS, HIST_ROW = 6, 100, 102
 HIST_DOUBLES = N_OBS * HIST_ROW * 3
 
@@ -21,6 +21,14 @@ class Params(C.Structure):
                 ("max_steps", C.c_int32), ("reserved", C.c_int32)]
 
 
+class PersistentConfig(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("compact_period", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class Batch(C.Structure):
     _fields_ = [("workspace", C.c_void_p), ("n_events", C.c_int64), ("capacity", C.c_int32),
                 ("first_event", C.c_uint32)]
@@ -29,7 +37,8 @@ class Batch(C.Structure):
 _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "dq2", "dzp", "dinv", "t", "lnt",
                   "weight", "hash",
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
-                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "counters", "hist",
+                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "counters",
+                  "hist",
                   "stats", "total_bytes"]
 
 
@@ -59,6 +68,9 @@ SIGNATURES = {
     "gaps_shower": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), C.c_void_p]),
     "gaps_shower_timed": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), _P(C.c_double),
                                     C.c_void_p]),
+    "gaps_shower_persistent": (C.c_int, [_P(Params), _P(Batch), _P(PersistentConfig), C.c_void_p]),
+    "gaps_autotune_persistent": (C.c_int, [_P(Params), _P(Batch), _P(PersistentConfig), _P(C.c_double),
+                                           C.c_void_p]),
     "gaps_shower_step": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
     "gaps_validate": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
     "gaps_observables": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
@@ -162,6 +174,26 @@ def shower_timed(p, ws, mode=SHOWER_PLAIN, stream=None):
     rc = _check(load().gaps_shower_timed(C.byref(p), C.byref(_batch(ws)), int(mode), C.byref(n), C.byref(ms),
                                          _stream_handle(stream)), "gaps_shower_timed", allow=(GAPS_ERR_STEP_LIMIT,))
     return rc, n.value, ms.value
+
+
+def shower_persistent(p, ws, cfg=None, stream=None):
+    """gaps_shower_persistent: asynchronous, one launch.  cfg: PersistentConfig,
+    a dict of its fields, or None for the library default."""
+    if isinstance(cfg, dict):
+        cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
+                               int(cfg.get("blocks_per_sm", 0)), 0)
+    ptr = C.byref(cfg) if cfg is not None else None
+    _check(load().gaps_shower_persistent(C.byref(p), C.byref(_batch(ws)), ptr, _stream_handle(stream)),
+           "gaps_shower_persistent")
+
+
+def autotune_persistent(p, ws, stream=None):
+    """gaps_autotune_persistent: returns (PersistentConfig, best ms)."""
+    cfg = PersistentConfig()
+    ms = C.c_double(0.0)
+    _check(load().gaps_autotune_persistent(C.byref(p), C.byref(_batch(ws)), C.byref(cfg), C.byref(ms),
+                                           _stream_handle(stream)), "gaps_autotune_persistent")
+    return cfg, ms.value
 
 
 def shower_step(p, ws, stream=None):
