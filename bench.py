@@ -44,6 +44,28 @@ WORK_PER_EMISSION = {"simple": 164, "div": 18, "sqrt": 7, "log": 4, "exp": 2, "s
 DFMA_PER_SM_PER_CLOCK = 2
 
 
+def step_kernel_traffic(event_cycles_per_launch):
+    """DRAM bytes per launch of the veto-cycle kernel: the per-event-cycle
+    traffic of the committed ncu capture times this run's event-cycles per
+    launch; None once the kernel sources differ from the captured ones."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "k_step_plain_500k.md")
+    try:
+        text = open(path).read()
+        per_unit = float(re.search(r"dram_bytes_per_event_cycle:\s*([0-9.]+)", text).group(1))
+        want = re.search(r"source_sha256:\s*([0-9a-f]+)", text).group(1)
+        files = re.search(r"sources:\s*(.+)", text).group(1).split()
+        h = hashlib.sha256()
+        for f in files:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != want:
+            return None
+        return per_unit * event_cycles_per_launch
+    except (OSError, AttributeError, ValueError):
+        return None
+
+
 def dfma_equivalents(counts, rates):
     return sum(n * (1.0 if op == "simple" else rates["dfma"] / rates[op]) for op, n in counts.items())
 
@@ -372,7 +394,10 @@ def main():
         "gpu_launches": int(args.steps * kernels_outside_shower(args.capacity) + launches_total),
         "roofline": {"bound": "alu", "kernel": "k_step_plain (fused veto cycle)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "frac": achieved_tflops / peak_tflops,
+                     "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
+                     "traffic_source": "profiles/k_step_plain_500k.md: DRAM bytes per event-cycle from one ncu "
+                                       "capture x this run's event-cycles per launch",
                      "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "
                                     f"x {clock_mhz:.0f} MHz (median SM clock under load) x 2 flops; "
                                     f"MEASURED_PEAKS.json has no FP64 entry",
