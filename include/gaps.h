@@ -112,8 +112,23 @@ typedef struct gaps_layout {
                              8, 9 the plain form's active-list lengths */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
+  int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
+  int64_t job_begin;      /* int64 [GAPS_MAX_JOBS + 1]: first batch event of every job */
+  int64_t job_of;         /* uint16 [n_events]: job of every event of a multi-job batch */
   int64_t total_bytes;
 } gaps_layout;
+
+/* Largest number of jobs in one multi-job batch. */
+#define GAPS_MAX_JOBS 1024
+
+/* One job of a multi-job batch: its own physics parameters and seed, and a
+ * contiguous range of the batch's events. */
+typedef struct gaps_job {
+  gaps_params params;
+  int64_t n_events;     /* events of this job (>= 0) */
+  uint32_t first_event; /* Philox event id of the job's first event */
+  int32_t reserved;     /* must be 0 */
+} gaps_job;
 
 /* Event status values. */
 enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3 };
@@ -159,6 +174,19 @@ size_t gaps_workspace_bytes(int64_t n_events, int32_t capacity);
 int gaps_workspace_layout(int64_t n_events, int32_t capacity, gaps_layout* out);
 /* GAPS_OK if the parameters are physical (see gaps_params). */
 int gaps_check_params(const gaps_params* params);
+
+/* ------------------------------------------------------- multi-job batches */
+
+/* Make the batch a multi-job batch: jobs[0..n_jobs) take consecutive ranges
+ * of the batch's events in order (their n_events must add up to the batch's).
+ * Each job keeps its own sqrt(s), alpha_s, cutoff, flavours and seed, and its
+ * events their own ids (first_event + k), so every event is the one a
+ * single-job batch of that job would produce.  After this call pass
+ * params = NULL to gaps_generate_me, gaps_shower, gaps_shower_persistent,
+ * gaps_validate, gaps_observables and gaps_histograms; gaps_histograms then
+ * fills one histogram set per job (hist_device holds n_jobs *
+ * GAPS_HIST_DOUBLES doubles).  Synchronous. */
+int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch, void* stream);
 
 /* ------------------------------------------------------------- hot path */
 
@@ -211,7 +239,7 @@ int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* s
 
 /* Validation of the finished record (the paper's "Validate Events" stage):
  * sets valid bits 1 momentum not conserved to 1e-10 GeV, 2 a parton off
- * shell (|p^2| > 1e-10 E^2), 4 non-positive energy, 8 broken colour flow,
+ * shell (|p^2| > 1e-10 E sqrt(s)), 4 non-positive energy, 8 broken colour flow,
  * 16 flavour imbalance, 32 non-finite momentum.  Asynchronous. */
 int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream);
 

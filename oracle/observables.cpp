@@ -126,7 +126,9 @@ void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double 
 }
 
 // Validation bits: 1 momentum not conserved to 1e-10 GeV, 2 a parton off
-// shell (|p^2| > 1e-10 E^2), 4 non-positive energy, 8 broken colour flow,
+// shell (|p^2| > 1e-10 E sqrt(s): the dipole map forms every component from
+// momenta of the event's scale, so FP64 masslessness holds to ~eps E sqrt(s),
+// not eps E^2), 4 non-positive energy, 8 broken colour flow,
 // 16 flavour imbalance, 32 non-finite component.
 int validate(const std::vector<Parton>& ps, double sqrt_s) {
   int bits = 0;
@@ -137,7 +139,7 @@ int validate(const std::vector<Parton>& ps, double sqrt_s) {
       bits |= 32;
     sum = sum + m;
     if (!(m.e > 0.0)) bits |= 4;
-    if (std::fabs(dot(m, m)) > 1e-10 * m.e * m.e) bits |= 2;
+    if (std::fabs(dot(m, m)) > 1e-10 * m.e * sqrt_s) bits |= 2;
   }
   if (std::fabs(sum.e - sqrt_s) > 1e-10 || std::fabs(sum.x) > 1e-10 || std::fabs(sum.y) > 1e-10 ||
       std::fabs(sum.z) > 1e-10)

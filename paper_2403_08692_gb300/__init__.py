@@ -9,7 +9,7 @@ include/gaps.h); this package is its thin Python binding.
 """
 from .gaps import (  # noqa: F401
     ACTIVE, DONE, OVERFLOW, STEP_LIMIT, SHOWER_PLAIN, SHOWER_PERSISTENT, HIST_DOUBLES, N_OBS, HIST_ROW,
-    PersistentConfig, shower_persistent, autotune_persistent,
+    PersistentConfig, shower_persistent, autotune_persistent, Job, set_jobs, MAX_JOBS,
     GapsError, Params, Stats, Workspace, check_params, generate_me, histograms, layout, load, shower_timed,
     make_params, observables, reduce_stats, run, shower, shower_step, validate, workspace_bytes,
     event_shapes_noalloc, probe_fp64_rates,

@@ -65,6 +65,9 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->counters = take(8 * 16);
   L->hist = take(8 * GAPS_HIST_DOUBLES);
   L->stats = take(sizeof(gaps_stats));
+  L->jobs = take(static_cast<int64_t>(sizeof(DevParams)) * GAPS_MAX_JOBS);
+  L->job_begin = take(8 * (GAPS_MAX_JOBS + 1));
+  L->job_of = take(2 * n);
   L->total_bytes = off;
 }
 
@@ -80,8 +83,9 @@ int check_batch(const gaps_batch* b) {
 
 int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
 
-DevParams make_dev_params(const gaps_params& p) {
+DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   DevParams d{};
+  d.id_offset = id_offset;
   d.sqrt_s = p.sqrt_s;
   d.s = p.sqrt_s * p.sqrt_s;
   d.tc = p.t_cutoff;
@@ -110,7 +114,7 @@ Events make_events(const gaps_batch& b) {
   gaps_layout L;
   compute_layout(b.n_events, b.capacity, &L);
   char* base = static_cast<char*>(b.workspace);
-  Events E;
+  Events E{};
   E.px = reinterpret_cast<double*>(base + L.px);
   E.py = reinterpret_cast<double*>(base + L.py);
   E.pz = reinterpret_cast<double*>(base + L.pz);
@@ -146,8 +150,29 @@ Events make_events(const gaps_batch& b) {
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
   E.n = b.n_events;
   E.cap = b.capacity;
-  E.first = b.first_event;
   return E;
+}
+
+// The launch parameters and event view of a call.  With params, a single-job
+// batch whose event j has id first_event + j.  Without, a multi-job batch
+// prepared by gaps_set_jobs: every event takes its job's parameters from the
+// workspace's job table; the host-side step bound is then only a guard.
+int prepare(const gaps_params* params, const gaps_batch* batch, DevParams* P, Events* E) {
+  if (check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  *E = make_events(*batch);
+  if (params) {
+    if (gaps_check_params(params) != GAPS_OK) return GAPS_ERR_INVALID;
+    *P = make_dev_params(*params, batch->first_event);
+    return GAPS_OK;
+  }
+  gaps_layout L;
+  compute_layout(batch->n_events, batch->capacity, &L);
+  char* base = static_cast<char*>(batch->workspace);
+  E->jobs = reinterpret_cast<const DevParams*>(base + L.jobs);
+  E->job_of = reinterpret_cast<const uint16_t*>(base + L.job_of);
+  *P = DevParams{};
+  P->max_steps = 0x7fffffff;
+  return GAPS_OK;
 }
 
 }  // namespace gaps
@@ -184,16 +209,49 @@ int gaps_check_params(const gaps_params* p) {
 }
 
 int gaps_generate_me(const gaps_params* params, const gaps_batch* batch, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
-  const cudaError_t e = launch_me(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_me(P, E, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   const cudaError_t e =
-      launch_step_plain(make_dev_params(*params), make_events(*batch), nullptr, batch->n_events, nullptr, nullptr,
-                        nullptr, static_cast<cudaStream_t>(stream));
+      launch_step_plain(P, E, nullptr, batch->n_events, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch, void* stream) {
+  if (!jobs || n_jobs < 1 || n_jobs > GAPS_MAX_JOBS || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  DevParams table[GAPS_MAX_JOBS];
+  int64_t begin[GAPS_MAX_JOBS + 1];
+  int64_t at = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const gaps_job& job = jobs[j];
+    if (gaps_check_params(&job.params) != GAPS_OK || job.n_events < 0 || job.reserved != 0) return GAPS_ERR_INVALID;
+    if (static_cast<uint64_t>(job.first_event) + static_cast<uint64_t>(job.n_events) > 0x100000000ull)
+      return GAPS_ERR_INVALID;
+    table[j] = make_dev_params(job.params, static_cast<int64_t>(job.first_event) - at);
+    begin[j] = at;
+    at += job.n_events;
+  }
+  begin[n_jobs] = at;
+  if (at != batch->n_events) return GAPS_ERR_INVALID;
+  gaps_layout L;
+  compute_layout(batch->n_events, batch->capacity, &L);
+  char* base = static_cast<char*>(batch->workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(base + L.jobs, table, sizeof(DevParams) * n_jobs, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + L.job_begin, begin, sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_fill_job_of(reinterpret_cast<uint16_t*>(base + L.job_of),
+                           reinterpret_cast<const int64_t*>(base + L.job_begin), n_jobs, batch->n_events, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables live on this stack
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
@@ -216,11 +274,11 @@ cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
 
 int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                 double* kernel_ms_out, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   if (mode != GAPS_SHOWER_PLAIN && mode != GAPS_SHOWER_PERSISTENT) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const DevParams P = make_dev_params(*params);
-  const Events E = make_events(*batch);
   int64_t launches = 0;
   if (launches_out) *launches_out = 0;
   if (kernel_ms_out) *kernel_ms_out = 0.0;
@@ -309,23 +367,24 @@ int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mo
 
 int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
                            const gaps_persistent_config* cfg, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
   if (!config_ok(c)) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Events E = make_events(*batch);
   if (E.n == 0) return GAPS_OK;
   cudaError_t e = clear_shower_counters(E, s);
-  if (e == cudaSuccess) e = launch_shower_persistent(make_dev_params(*params), E, c, s);
+  if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch, gaps_persistent_config* best,
                              double* best_ms, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !best) return GAPS_ERR_INVALID;
+  DevParams P;
+  Events E;
+  if (!best || prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const DevParams P = make_dev_params(*params);
-  const Events E = make_events(*batch);
   *best = kDefaultPersistent;
   if (best_ms) *best_ms = 0.0;
   if (E.n == 0) return GAPS_OK;
@@ -360,24 +419,26 @@ int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch,
 }
 
 int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
-  const cudaError_t e =
-      launch_validate(make_dev_params(*params), make_events(*batch), static_cast<cudaStream_t>(stream));
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_validate(P, E, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
-  const cudaError_t e =
-      launch_observables(make_dev_params(*params), make_events(*batch), make_events(*batch).buckets,
-                         make_events(*batch).order, static_cast<cudaStream_t>(stream));
+  DevParams P;
+  Events E;
+  if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_observables(P, E, E.buckets, E.order, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 int gaps_histograms(const gaps_params* params, const gaps_batch* batch, double* hist_device, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !hist_device)
-    return GAPS_ERR_INVALID;
-  const cudaError_t e = launch_histograms(make_events(*batch), hist_device, static_cast<cudaStream_t>(stream));
+  DevParams P;
+  Events E;
+  if (!hist_device || prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_histograms(E, hist_device, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
@@ -392,7 +453,8 @@ int gaps_reduce_stats(const gaps_batch* batch, gaps_stats* stats_device, void* s
 
 int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, double* host_hist,
              gaps_stats* host_stats, void* stream) {
-  if (gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !host_hist)
+  // single-job batches only: the workspace holds one histogram accumulator
+  if (!params || gaps_check_params(params) != GAPS_OK || check_batch(batch) != GAPS_OK || !host_hist)
     return GAPS_ERR_INVALID;
   if (mode != GAPS_SHOWER_PLAIN && mode != GAPS_SHOWER_PERSISTENT) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

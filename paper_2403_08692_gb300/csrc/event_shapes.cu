@@ -102,7 +102,8 @@ struct Top2 {
 };
 
 template <int MAXJ>
-__device__ void event_shapes(const DevParams& P, const Events& E, int64_t ev, int n) {
+__device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, int n) {
+  const DevParams& P = params_of(P0, E, ev);
   const int64_t N = E.n;
   double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
   float fx[MAXJ], fy[MAXJ], fz[MAXJ];

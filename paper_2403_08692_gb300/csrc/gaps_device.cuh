@@ -39,6 +39,8 @@ struct DevParams {
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
   // FP32 copies used by the screens
   float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;
+  // Philox event id of batch event ev: ev + id_offset (mod 2^32)
+  int64_t id_offset;
 };
 
 // Pointers into the workspace (gaps_layout) for one batch.
@@ -61,9 +63,12 @@ struct Events {
   unsigned long long* counters;
   double* hist;
   gaps_stats* stats;
+  // Multi-job batches: parameters per job and the job of every event
+  // (NULL for a single-job batch, whose parameters come with the launch).
+  const DevParams* jobs;
+  const uint16_t* job_of;
   int64_t n;
   int cap;
-  uint32_t first;
 
   __device__ __forceinline__ size_t at(int slot, int64_t ev) const {
     return static_cast<size_t>(slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
@@ -72,6 +77,17 @@ struct Events {
     return (static_cast<size_t>(side) * cap + slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
   }
 };
+
+// The parameters of event ev: its job's in a multi-job batch, else the
+// launch's.
+__device__ __forceinline__ const DevParams& params_of(const DevParams& launch, const Events& E, int64_t ev) {
+  return E.jobs ? E.jobs[E.job_of[ev]] : launch;
+}
+
+// The Philox event id (first counter word) of batch event ev.
+__device__ __forceinline__ uint32_t event_id(const DevParams& P, int64_t ev) {
+  return static_cast<uint32_t>(ev + P.id_offset);
+}
 
 // --------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

@@ -6,7 +6,9 @@
 
 namespace gaps {
 
-DevParams make_dev_params(const gaps_params& p);
+// Launch parameters of a job whose batch event ev has Philox event id
+// ev + id_offset.
+DevParams make_dev_params(const gaps_params& p, int64_t id_offset);
 // Remember a CUDA error for gaps_last_cuda_error() and return GAPS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 Events make_events(const gaps_batch& b);
@@ -24,7 +26,10 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s)
 // buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
 // scratch [n_events].
 cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s);
+// Single-job batch: hist is one histogram set; multi-job batch (E.jobs set):
+// hist holds one set per job.
 cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s);
+cudaError_t launch_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s);
 
 }  // namespace gaps

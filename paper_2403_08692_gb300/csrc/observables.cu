@@ -8,11 +8,14 @@ namespace {
 
 // ------------------------------------------------------------ validation
 // One thread per event.  Bits: 1 momentum not conserved to 1e-10 GeV, 2 a
-// parton off shell, 4 non-positive energy, 8 broken colour flow, 16 flavour
+// parton off shell (|p^2| > 1e-10 E sqrt(s): every component is formed from
+// momenta of the event's scale, so FP64 masslessness holds to ~eps E
+// sqrt(s)), 4 non-positive energy, 8 broken colour flow, 16 flavour
 // imbalance, 32 non-finite momentum.
-__global__ void __launch_bounds__(128) k_validate(DevParams P, Events E) {
+__global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
   const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (ev >= E.n) return;
+  const DevParams& P = params_of(P0, E, ev);
   const int n = E.n_partons[ev];
   int bits = 0;
   double se = 0, sx = 0, sy = 0, sz = 0;
@@ -28,7 +31,7 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P, Events E) {
     sy += y;
     sz += z;
     if (!(e > 0.0)) bits |= 4;
-    if (fabs(e * e - x * x - y * y - z * z) > 1e-10 * e * e) bits |= 2;
+    if (fabs(e * e - x * x - y * y - z * z) > 1e-10 * e * P.sqrt_s) bits |= 2;
     const int fl = E.flav[a];
     const int c = E.col[a], ac = E.acol[a];
     const int l0 = E.link[E.link_at(0, i, ev)], l1 = E.link[E.link_at(1, i, ev)];
@@ -92,7 +95,27 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P, Events E) {
 }
 
 // ---------------------------------------------------------- histograms
-// Block-private histograms in shared memory, then one atomic merge per bin.
+// Bin of observable h with value o (log10 y23..y56 on [-4.3, -0.3], 1-T and
+// rho_H on [0, 0.5]; 100 bins plus underflow 0 and overflow 101), or -1 when
+// the value is undefined.
+__device__ __forceinline__ int hist_bin(int h, double o) {
+  double x, lo, hi;
+  if (h < 4) {
+    if (!(o > 0.0)) return -1;
+    x = log10(o);
+    lo = -4.3;
+    hi = -0.3;
+  } else {
+    x = o;
+    lo = 0.0;
+    hi = 0.5;
+  }
+  const double f = (x - lo) / (hi - lo) * GAPS_N_BINS;
+  return f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
+}
+
+// Single-job batch: block-private histograms in shared memory, then one
+// atomic merge per bin.
 __global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
   __shared__ double sh[GAPS_HIST_DOUBLES];
   for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x) sh[i] = 0.0;
@@ -103,20 +126,8 @@ __global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
     if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
     const double w = E.weight[ev];
     for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const double o = E.obs[h * N + ev];
-      double x, lo, hi;
-      if (h < 4) {
-        if (!(o > 0.0)) continue;
-        x = log10(o);
-        lo = -4.3;
-        hi = -0.3;
-      } else {
-        x = o;
-        lo = 0.0;
-        hi = 0.5;
-      }
-      const double f = (x - lo) / (hi - lo) * GAPS_N_BINS;
-      const int bin = f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
+      const int bin = hist_bin(h, E.obs[h * N + ev]);
+      if (bin < 0) continue;
       double* cell = sh + (h * GAPS_HIST_ROW + bin) * 3;
       atomicAdd(cell + 0, w);
       atomicAdd(cell + 1, w * w);
@@ -126,6 +137,40 @@ __global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
   __syncthreads();
   for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x)
     if (sh[i] != 0.0) atomicAdd(hist + i, sh[i]);
+}
+
+// Multi-job batch: every event fills its own job's histograms (hist +
+// job * GAPS_HIST_DOUBLES) with global atomics.
+__global__ void __launch_bounds__(256) k_histograms_jobs(Events E, double* hist) {
+  const int64_t N = E.n;
+  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < N;
+       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
+    const double w = E.weight[ev];
+    double* base = hist + static_cast<size_t>(E.job_of[ev]) * GAPS_HIST_DOUBLES;
+    for (int h = 0; h < GAPS_N_OBS; ++h) {
+      const int bin = hist_bin(h, E.obs[h * N + ev]);
+      if (bin < 0) continue;
+      double* cell = base + (h * GAPS_HIST_ROW + bin) * 3;
+      atomicAdd(cell + 0, w);
+      atomicAdd(cell + 1, w * w);
+      atomicAdd(cell + 2, 1.0);
+    }
+  }
+}
+
+// Job index of every event of a multi-job batch: job j covers
+// [begin[j], begin[j + 1]).
+__global__ void __launch_bounds__(256) k_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n) {
+  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (ev >= n) return;
+  int lo = 0, hi = n_jobs - 1;  // last job whose begin <= ev
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (begin[mid] <= ev) lo = mid;
+    else hi = mid - 1;
+  }
+  job_of[ev] = static_cast<uint16_t>(lo);
 }
 
 // -------------------------------------------------------------- stats
@@ -207,7 +252,17 @@ cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (E.n + 255) / 256;
   const unsigned blocks = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
-  k_histograms<<<blocks, 256, 0, s>>>(E, hist);
+  if (E.jobs) {
+    k_histograms_jobs<<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(E, hist);
+  } else {
+    k_histograms<<<blocks, 256, 0, s>>>(E, hist);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_fill_job_of<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(job_of, begin, n_jobs, n);
   return cudaGetLastError();
 }
 

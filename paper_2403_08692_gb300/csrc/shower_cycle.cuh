@@ -192,8 +192,9 @@ __device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int st
 // Phase 1 of a cycle for active event ev.  Returns kCycleFinished when the
 // event left the active state (status written), kCycleAccepted with `task`
 // filled when an emission must be generated, kCycleVetoed otherwise.
-__device__ inline int cycle_select_veto(const DevParams& P, const Events& E, int64_t ev, EmitTask& task) {
-  const uint32_t id = E.first + static_cast<uint32_t>(ev);
+__device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
+  const DevParams& P = params_of(P0, E, ev);
+  const uint32_t id = event_id(P, ev);
   const int n = E.n_partons[ev];
   const int step = E.n_steps[ev];
   const double lnt = E.lnt[ev];
@@ -351,9 +352,10 @@ __device__ inline int cycle_select_veto(const DevParams& P, const Events& E, int
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours,
 // the new parton in slot n, and the dipoles whose invariant mass moved.
-__device__ inline void cycle_emit(const DevParams& P, const Events& E, const EmitTask& w) {
+__device__ inline void cycle_emit(const DevParams& P0, const Events& E, const EmitTask& w) {
   const int64_t ev = w.ev;
-  const uint32_t id = E.first + static_cast<uint32_t>(ev);
+  const DevParams& P = params_of(P0, E, ev);
+  const uint32_t id = event_id(P, ev);
   const double t = exp(w.lnt);
   const double z = z_fp64(w.kind, w.zp, 1.0 / w.inv_ls, to_unit(w.rz_hi, w.rz_lo));
   const double y = t / (w.q2 * z * (1.0 - z));

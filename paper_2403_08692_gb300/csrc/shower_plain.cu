@@ -15,10 +15,11 @@ namespace gaps {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_me(DevParams P, Events E) {
+__global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
   const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (ev >= E.n) return;
-  const uint32_t id = E.first + static_cast<uint32_t>(ev);
+  const DevParams& P = params_of(P0, E, ev);
+  const uint32_t id = event_id(P, ev);
   const Uniforms r0 = draw2(P, id, 0, 0, kDrawME);
   const Uniforms r1 = draw2(P, id, 0, 1, kDrawME);
   int fl = 1 + static_cast<int>(r0.a * P.nf);

@@ -39,7 +39,14 @@ _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
                   "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "counters",
                   "hist",
-                  "stats", "total_bytes"]
+                  "stats", "jobs", "job_begin", "job_of", "total_bytes"]
+
+
+MAX_JOBS = 1024
+
+
+class Job(C.Structure):
+    _fields_ = [("params", Params), ("n_events", C.c_int64), ("first_event", C.c_uint32), ("reserved", C.c_int32)]
 
 
 class Layout(C.Structure):
@@ -68,6 +75,7 @@ SIGNATURES = {
     "gaps_shower": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), C.c_void_p]),
     "gaps_shower_timed": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_int64), _P(C.c_double),
                                     C.c_void_p]),
+    "gaps_set_jobs": (C.c_int, [_P(Job), C.c_int32, _P(Batch), C.c_void_p]),
     "gaps_shower_persistent": (C.c_int, [_P(Params), _P(Batch), _P(PersistentConfig), C.c_void_p]),
     "gaps_autotune_persistent": (C.c_int, [_P(Params), _P(Batch), _P(PersistentConfig), _P(C.c_double),
                                            C.c_void_p]),
@@ -151,18 +159,23 @@ def _stream_handle(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _pp(p):
+    """Parameters of a single-job call, or NULL for a multi-job batch."""
+    return C.byref(p) if p is not None else None
+
+
 def _batch(ws) -> Batch:
     return Batch(C.c_void_p(ws.buffer.data_ptr()), ws.n_events, ws.capacity, ws.first_event)
 
 
 def generate_me(p, ws, stream=None):
-    _check(load().gaps_generate_me(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_generate_me")
+    _check(load().gaps_generate_me(_pp(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_generate_me")
 
 
 def shower(p, ws, mode=SHOWER_PLAIN, stream=None):
     """Returns (status code, launches); GAPS_ERR_STEP_LIMIT is not raised."""
     n = C.c_int64(0)
-    rc = _check(load().gaps_shower(C.byref(p), C.byref(_batch(ws)), int(mode), C.byref(n), _stream_handle(stream)),
+    rc = _check(load().gaps_shower(_pp(p), C.byref(_batch(ws)), int(mode), C.byref(n), _stream_handle(stream)),
                 "gaps_shower", allow=(GAPS_ERR_STEP_LIMIT,))
     return rc, n.value
 
@@ -171,9 +184,18 @@ def shower_timed(p, ws, mode=SHOWER_PLAIN, stream=None):
     """gaps_shower_timed: returns (status code, launches, summed kernel ms)."""
     n = C.c_int64(0)
     ms = C.c_double(0.0)
-    rc = _check(load().gaps_shower_timed(C.byref(p), C.byref(_batch(ws)), int(mode), C.byref(n), C.byref(ms),
+    rc = _check(load().gaps_shower_timed(_pp(p), C.byref(_batch(ws)), int(mode), C.byref(n), C.byref(ms),
                                          _stream_handle(stream)), "gaps_shower_timed", allow=(GAPS_ERR_STEP_LIMIT,))
     return rc, n.value, ms.value
+
+
+def set_jobs(jobs, ws, stream=None):
+    """gaps_set_jobs: jobs is a list of (Params, n_events, first_event); the
+    batch's events are split into consecutive ranges in that order."""
+    arr = (Job * len(jobs))()
+    for k, (p, n, first) in enumerate(jobs):
+        arr[k] = Job(p, int(n), int(first), 0)
+    _check(load().gaps_set_jobs(arr, len(jobs), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_set_jobs")
 
 
 def shower_persistent(p, ws, cfg=None, stream=None):
@@ -183,7 +205,7 @@ def shower_persistent(p, ws, cfg=None, stream=None):
         cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
                                int(cfg.get("blocks_per_sm", 0)), 0)
     ptr = C.byref(cfg) if cfg is not None else None
-    _check(load().gaps_shower_persistent(C.byref(p), C.byref(_batch(ws)), ptr, _stream_handle(stream)),
+    _check(load().gaps_shower_persistent(_pp(p), C.byref(_batch(ws)), ptr, _stream_handle(stream)),
            "gaps_shower_persistent")
 
 
@@ -191,25 +213,25 @@ def autotune_persistent(p, ws, stream=None):
     """gaps_autotune_persistent: returns (PersistentConfig, best ms)."""
     cfg = PersistentConfig()
     ms = C.c_double(0.0)
-    _check(load().gaps_autotune_persistent(C.byref(p), C.byref(_batch(ws)), C.byref(cfg), C.byref(ms),
+    _check(load().gaps_autotune_persistent(_pp(p), C.byref(_batch(ws)), C.byref(cfg), C.byref(ms),
                                            _stream_handle(stream)), "gaps_autotune_persistent")
     return cfg, ms.value
 
 
 def shower_step(p, ws, stream=None):
-    _check(load().gaps_shower_step(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_shower_step")
+    _check(load().gaps_shower_step(_pp(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_shower_step")
 
 
 def validate(p, ws, stream=None):
-    _check(load().gaps_validate(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_validate")
+    _check(load().gaps_validate(_pp(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_validate")
 
 
 def observables(p, ws, stream=None):
-    _check(load().gaps_observables(C.byref(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_observables")
+    _check(load().gaps_observables(_pp(p), C.byref(_batch(ws)), _stream_handle(stream)), "gaps_observables")
 
 
 def histograms(p, ws, hist_device, stream=None):
-    _check(load().gaps_histograms(C.byref(p), C.byref(_batch(ws)), C.c_void_p(hist_device.data_ptr()),
+    _check(load().gaps_histograms(_pp(p), C.byref(_batch(ws)), C.c_void_p(hist_device.data_ptr()),
                                   _stream_handle(stream)), "gaps_histograms")
 
 
@@ -248,7 +270,7 @@ def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):
     Returns (status code, Stats)."""
     st = Stats()
     ptr = host_hist.data_ptr() if hasattr(host_hist, "data_ptr") else host_hist.ctypes.data
-    rc = _check(load().gaps_run(C.byref(p), C.byref(_batch(ws)), int(mode), C.cast(ptr, C.POINTER(C.c_double)),
+    rc = _check(load().gaps_run(_pp(p), C.byref(_batch(ws)), int(mode), C.cast(ptr, C.POINTER(C.c_double)),
                                 C.byref(st), _stream_handle(stream)), "gaps_run", allow=(GAPS_ERR_STEP_LIMIT,))
     return rc, st
 

@@ -40,7 +40,7 @@ def test_every_event_is_physical(oracle_mod, kw):
         tot = m.sum(axis=0)
         assert np.allclose(tot, [kw["sqrt_s"], 0, 0, 0], atol=1e-10, rtol=0)
         m2 = m[:, 0] ** 2 - (m[:, 1:] ** 2).sum(axis=1)
-        assert np.all(np.abs(m2) <= 1e-10 * m[:, 0] ** 2)
+        assert np.all(np.abs(m2) <= 1e-10 * m[:, 0] * kw["sqrt_s"])
     assert ev["n_emissions"].sum() > 2000
     assert np.all(ev["n_partons"] == 2 + ev["n_emissions"])
 
