@@ -115,6 +115,7 @@ typedef struct gaps_layout {
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
   int64_t job_begin;      /* int64 [GAPS_MAX_JOBS + 1]: first batch event of every job */
   int64_t job_of;         /* uint16 [n_events]: job of every event of a multi-job batch */
+  int64_t job_done;       /* uint64 [GAPS_MAX_JOBS]: finished events per job slot */
   int64_t total_bytes;
 } gaps_layout;
 
@@ -187,6 +188,47 @@ int gaps_check_params(const gaps_params* params);
  * fills one histogram set per job (hist_device holds n_jobs *
  * GAPS_HIST_DOUBLES doubles).  Synchronous. */
 int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch, void* stream);
+
+/* ------------------------------------------------ serving: the event pool */
+
+/* Continuous batching over one resident workspace (the pool).  Jobs arrive
+ * while others shower: each is admitted into a free range of the pool and a
+ * free job slot, its events join the live active list, and every veto cycle
+ * advances all live events of all jobs (the plain cycle over the active
+ * list, Sec. 2).  A job whose events have all finished is finalised on its
+ * own range and its range and slot are reused.  The caller keeps the
+ * schedule: the number of cycles launched so far (`cycle`), the free ranges
+ * and slots, and an upper bound on the live events.  Every event equals the
+ * event a single-job batch of its job produces. */
+
+/* Clear the pool's active lists and per-job counters.  Asynchronous. */
+int gaps_pool_reset(const gaps_batch* pool, void* stream);
+
+/* Admit a job: n_events events in pool range [ev_begin, ev_begin +
+ * n_events), job slot job_slot (0 .. GAPS_MAX_JOBS-1), event ids
+ * first_event + k; generates their matrix elements and appends them to the
+ * active list read by the next cycle (cycle = cycles launched so far).
+ * Asynchronous. */
+int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begin, int64_t n_events,
+                    uint32_t first_event, const gaps_batch* pool, int64_t cycle, void* stream);
+
+/* Enqueue n_cycles veto cycles, numbered first_cycle.., over the live
+ * events; max_active bounds their number (it sizes the grids).  No host
+ * synchronisation. */
+int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
+                     void* stream);
+
+/* Read the number of live events before cycle `cycle` and, if job_done_out
+ * is not NULL, the finished-event count of every job slot
+ * (GAPS_MAX_JOBS values).  Synchronises the stream. */
+int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_out, uint64_t* job_done_out,
+                       void* stream);
+
+/* Validation, observables and histograms of a finished job's range; adds
+ * its histograms to hist_device (one set, GAPS_HIST_DOUBLES doubles, not
+ * cleared).  Asynchronous. */
+int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const gaps_batch* pool,
+                     double* hist_device, void* stream);
 
 /* ------------------------------------------------------------- hot path */
 

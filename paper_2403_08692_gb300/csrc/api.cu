@@ -68,6 +68,7 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->jobs = take(static_cast<int64_t>(sizeof(DevParams)) * GAPS_MAX_JOBS);
   L->job_begin = take(8 * (GAPS_MAX_JOBS + 1));
   L->job_of = take(2 * n);
+  L->job_done = take(8 * GAPS_MAX_JOBS);
   L->total_bytes = off;
 }
 
@@ -149,8 +150,48 @@ Events make_events(const gaps_batch& b) {
   E.hist = reinterpret_cast<double*>(base + L.hist);
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
   E.n = b.n_events;
+  E.stride = b.n_events;
+  E.base = 0;
   E.cap = b.capacity;
   return E;
+}
+
+// The view of workspace events [a, a + count) of E: same arrays, every
+// per-event pointer moved to event a, indices still strided by the whole
+// workspace.
+Events sub_view(const Events& E, int64_t a, int64_t count) {
+  Events V = E;
+  V.px += a;
+  V.py += a;
+  V.pz += a;
+  V.e += a;
+  V.flav += a;
+  V.col += a;
+  V.acol += a;
+  V.link += a;
+  V.dip += a;
+  V.dq2 += a;
+  V.dzp += a;
+  V.dinv += a;
+  V.lnt += a;
+  V.t += a;
+  V.weight += a;
+  V.hash += a;
+  V.n_partons += a;
+  V.status += a;
+  V.n_steps += a;
+  V.n_emissions += a;
+  V.n_winners += a;
+  V.n_trials += a;
+  V.n_dipoles += a;
+  V.next_colour += a;
+  V.me_flavour += a;
+  V.valid += a;
+  V.obs += a;
+  if (V.job_of) V.job_of += a;
+  V.n = count;
+  V.base = E.base + a;
+  return V;
 }
 
 // The launch parameters and event view of a call.  With params, a single-job
@@ -170,6 +211,7 @@ int prepare(const gaps_params* params, const gaps_batch* batch, DevParams* P, Ev
   char* base = static_cast<char*>(batch->workspace);
   E->jobs = reinterpret_cast<const DevParams*>(base + L.jobs);
   E->job_of = reinterpret_cast<const uint16_t*>(base + L.job_of);
+  E->job_done = reinterpret_cast<unsigned long long*>(base + L.job_done);
   *P = DevParams{};
   P->max_steps = 0x7fffffff;
   return GAPS_OK;
@@ -221,7 +263,8 @@ int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* s
   Events E;
   if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   const cudaError_t e =
-      launch_step_plain(P, E, nullptr, batch->n_events, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+      launch_step_plain(P, E, nullptr, batch->n_events, nullptr, nullptr, nullptr, nullptr,
+                        static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
@@ -330,7 +373,8 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     const int* list_in = launches == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
     int* list_out = E.active + static_cast<size_t>(out_half) * E.n;
     if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
-    e = launch_step_plain(P, E, list_in, n_in, list_out, &E.counters[8 + out_half], &E.counters[8 + in_half], s);
+    e = launch_step_plain(P, E, list_in, n_in, nullptr, list_out, &E.counters[8 + out_half],
+                          &E.counters[8 + in_half], s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
     ++launches;
@@ -488,6 +532,99 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
   st.launches = launches;
   if (host_stats) *host_stats = st;
   return st.n_step_limit > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
+}
+
+// ---------------------------------------------------------- serving pool
+// Counter words 10..12 hold the pool's active-list lengths: cycle c reads
+// word 10 + c%3, writes its survivors' count to 10 + (c+1)%3 and clears
+// 10 + (c+2)%3 for the cycle after it; the lists are active[c%2].
+
+int gaps_pool_reset(const gaps_batch* pool, void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(E.counters, 0, 16 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.job_done, 0, GAPS_MAX_JOBS * sizeof(unsigned long long), s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begin, int64_t n_events,
+                    uint32_t first_event, const gaps_batch* pool, int64_t cycle, void* stream) {
+  DevParams P;
+  Events E;
+  if (!params || gaps_check_params(params) != GAPS_OK || prepare(nullptr, pool, &P, &E) != GAPS_OK)
+    return GAPS_ERR_INVALID;
+  if (job_slot < 0 || job_slot >= GAPS_MAX_JOBS || ev_begin < 0 || n_events < 0 || cycle < 0 ||
+      ev_begin + n_events > pool->n_events ||
+      static_cast<uint64_t>(first_event) + static_cast<uint64_t>(n_events) > 0x100000000ull)
+    return GAPS_ERR_INVALID;
+  if (n_events == 0) return GAPS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevParams job = make_dev_params(*params, static_cast<int64_t>(first_event) - ev_begin);
+  // A pageable host-to-device copy returns once the source has been staged.
+  cudaError_t e = cudaMemcpyAsync(const_cast<DevParams*>(E.jobs) + job_slot, &job, sizeof(job),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.job_done + job_slot, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_set_job(const_cast<uint16_t*>(E.job_of), ev_begin, n_events, job_slot, s);
+  if (e == cudaSuccess) e = launch_me(P, sub_view(E, ev_begin, n_events), s);
+  if (e == cudaSuccess)
+    e = launch_append_range(E.active + static_cast<size_t>(cycle % 2) * E.stride, &E.counters[10 + cycle % 3],
+                            ev_begin, n_events, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
+                     void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || first_cycle < 0 || n_cycles < 0 || max_active < 0 ||
+      max_active > pool->n_events)
+    return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int64_t c = first_cycle; c < first_cycle + n_cycles; ++c) {
+    const cudaError_t e = launch_step_plain(
+        P, E, E.active + static_cast<size_t>(c % 2) * E.stride, max_active, &E.counters[10 + c % 3],
+        E.active + static_cast<size_t>((c + 1) % 2) * E.stride, &E.counters[10 + (c + 1) % 3],
+        &E.counters[10 + (c + 2) % 3], s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return GAPS_OK;
+}
+
+int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_out, uint64_t* job_done_out,
+                       void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || cycle < 0 || !active_out) return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long active = 0;
+  cudaError_t e = cudaMemcpyAsync(&active, &E.counters[10 + cycle % 3], sizeof(active), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && job_done_out)
+    e = cudaMemcpyAsync(job_done_out, E.job_done, GAPS_MAX_JOBS * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *active_out = static_cast<int64_t>(active);
+  return GAPS_OK;
+}
+
+int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const gaps_batch* pool,
+                     double* hist_device, void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || !hist_device || job_slot < 0 || job_slot >= GAPS_MAX_JOBS ||
+      ev_begin < 0 || n_events < 0 || ev_begin + n_events > pool->n_events)
+    return GAPS_ERR_INVALID;
+  if (n_events == 0) return GAPS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Events V = sub_view(E, ev_begin, n_events);
+  cudaError_t e = launch_validate(P, V, s);
+  if (e == cudaSuccess) e = launch_observables(P, V, E.buckets, E.order, s);
+  Events H = V;  // one histogram set: the range is one job
+  H.jobs = nullptr;
+  H.job_of = nullptr;
+  if (e == cudaSuccess) e = launch_histograms(H, hist_device, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
 const char* gaps_strerror(int status) {

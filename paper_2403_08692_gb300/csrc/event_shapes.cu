@@ -103,8 +103,7 @@ struct Top2 {
 
 template <int MAXJ>
 __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, int n) {
-  const DevParams& P = params_of(P0, E, ev);
-  const int64_t N = E.n;
+  const DevParams& P = params_of_event(P0, E, ev);
   double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
   float fx[MAXJ], fy[MAXJ], fz[MAXJ];
   double sum_abs = 0.0;
@@ -203,8 +202,8 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   }
   const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
   const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
-  E.obs[4 * N + ev] = 1.0 - thrust;
-  E.obs[5 * N + ev] = fmax(mp, mm) / P.s;
+  E.obs[4 * E.stride + ev] = 1.0 - thrust;
+  E.obs[5 * E.stride + ev] = fmax(mp, mm) / P.s;
 
   // ---- Durham (E-scheme)
   float fe2[MAXJ];
@@ -276,7 +275,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
       fz[bi] = z * r;
     }
   }
-  for (int h = 0; h < 4; ++h) E.obs[h * N + ev] = yres[h];
+  for (int h = 0; h < 4; ++h) E.obs[h * E.stride + ev] = yres[h];
 }
 
 // ------------------------------------------------------------- buckets
@@ -319,7 +318,7 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Events E, int* cursor, i
   if (E.status[ev] == GAPS_DONE) {
     order[atomicAdd(&cursor[E.n_partons[ev]], 1)] = static_cast<int>(ev);
   } else {
-    for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.n + ev] = -1.0;
+    for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.stride + ev] = -1.0;
   }
 }
 

@@ -83,6 +83,8 @@ extern "C" int gaps_event_shapes_noalloc(const double* px, const double* py, con
   E.obs = obs;
   E.counters = scratch->counters;
   E.n = n_events;
+  E.stride = n_events;
+  E.base = 0;
   E.cap = capacity;
   DevParams P{};
   P.sqrt_s = sqrt_s;

@@ -67,26 +67,41 @@ struct Events {
   // (NULL for a single-job batch, whose parameters come with the launch).
   const DevParams* jobs;
   const uint16_t* job_of;
-  int64_t n;
+  unsigned long long* job_done;  // [GAPS_MAX_JOBS] finished events per job (multi-job batches)
+  int64_t n;       // events in this view
+  int64_t stride;  // events in the whole workspace (the slot-major row length)
+  int64_t base;    // workspace index of this view's event 0
   int cap;
 
   __device__ __forceinline__ size_t at(int slot, int64_t ev) const {
-    return static_cast<size_t>(slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
+    return static_cast<size_t>(slot) * static_cast<size_t>(stride) + static_cast<size_t>(ev);
   }
   __device__ __forceinline__ size_t link_at(int side, int slot, int64_t ev) const {
-    return (static_cast<size_t>(side) * cap + slot) * static_cast<size_t>(n) + static_cast<size_t>(ev);
+    return (static_cast<size_t>(side) * cap + slot) * static_cast<size_t>(stride) + static_cast<size_t>(ev);
   }
 };
 
-// The parameters of event ev: its job's in a multi-job batch, else the
-// launch's.
+// The parameters of event ev: its job's in a multi-job batch (kMulti), else
+// the launch's.  A compile-time choice, so that single-job kernels read
+// their parameters from the kernel-argument bank.
+template <bool kMulti>
 __device__ __forceinline__ const DevParams& params_of(const DevParams& launch, const Events& E, int64_t ev) {
-  return E.jobs ? E.jobs[E.job_of[ev]] : launch;
+  if constexpr (kMulti) {
+    return E.jobs[E.job_of[ev]];
+  } else {
+    return launch;
+  }
 }
 
-// The Philox event id (first counter word) of batch event ev.
-__device__ __forceinline__ uint32_t event_id(const DevParams& P, int64_t ev) {
-  return static_cast<uint32_t>(ev + P.id_offset);
+// The same choice at run time, for kernels that read the parameters once per
+// event.
+__device__ __forceinline__ const DevParams& params_of_event(const DevParams& launch, const Events& E, int64_t ev) {
+  return E.jobs ? params_of<true>(launch, E, ev) : launch;
+}
+
+// The Philox event id (first counter word) of view event ev.
+__device__ __forceinline__ uint32_t event_id(const DevParams& P, const Events& E, int64_t ev) {
+  return static_cast<uint32_t>(E.base + ev + P.id_offset);
 }
 
 // --------------------------------------------------------------- Philox

@@ -17,8 +17,13 @@ cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);
 // One plain-form cycle over list_in[0 .. n_in) (list_in = NULL: events
 // 0 .. n_in); survivors are appended to list_out (may be NULL) through
 // *out_count; *reset_count is zeroed.
-cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in, int* list_out,
-                              unsigned long long* out_count, unsigned long long* reset_count, cudaStream_t s);
+// n_in_dev (may be NULL): the list length on the device, n_in then only
+// bounds it.
+cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in,
+                              const unsigned long long* n_in_dev, int* list_out, unsigned long long* out_count,
+                              unsigned long long* reset_count, cudaStream_t s);
+cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s);
+cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, cudaStream_t s);
 // Persistent form; counters word 6 is the event cursor and must be zero.
 cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
                                      cudaStream_t s);

@@ -15,7 +15,7 @@ namespace {
 __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
   const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (ev >= E.n) return;
-  const DevParams& P = params_of(P0, E, ev);
+  const DevParams& P = params_of_event(P0, E, ev);
   const int n = E.n_partons[ev];
   int bits = 0;
   double se = 0, sx = 0, sy = 0, sz = 0;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
     if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
     const double w = E.weight[ev];
     for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const int bin = hist_bin(h, E.obs[h * N + ev]);
+      const int bin = hist_bin(h, E.obs[h * E.stride + ev]);
       if (bin < 0) continue;
       double* cell = sh + (h * GAPS_HIST_ROW + bin) * 3;
       atomicAdd(cell + 0, w);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_histograms_jobs(Events E, double* hist)
     const double w = E.weight[ev];
     double* base = hist + static_cast<size_t>(E.job_of[ev]) * GAPS_HIST_DOUBLES;
     for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const int bin = hist_bin(h, E.obs[h * N + ev]);
+      const int bin = hist_bin(h, E.obs[h * E.stride + ev]);
       if (bin < 0) continue;
       double* cell = base + (h * GAPS_HIST_ROW + bin) * 3;
       atomicAdd(cell + 0, w);

@@ -192,9 +192,10 @@ __device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int st
 // Phase 1 of a cycle for active event ev.  Returns kCycleFinished when the
 // event left the active state (status written), kCycleAccepted with `task`
 // filled when an emission must be generated, kCycleVetoed otherwise.
+template <bool kMulti>
 __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
-  const DevParams& P = params_of(P0, E, ev);
-  const uint32_t id = event_id(P, ev);
+  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const uint32_t id = event_id(P, E, ev);
   const int n = E.n_partons[ev];
   const int step = E.n_steps[ev];
   const double lnt = E.lnt[ev];
@@ -352,10 +353,11 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours,
 // the new parton in slot n, and the dipoles whose invariant mass moved.
+template <bool kMulti>
 __device__ inline void cycle_emit(const DevParams& P0, const Events& E, const EmitTask& w) {
   const int64_t ev = w.ev;
-  const DevParams& P = params_of(P0, E, ev);
-  const uint32_t id = event_id(P, ev);
+  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const uint32_t id = event_id(P, E, ev);
   const double t = exp(w.lnt);
   const double z = z_fp64(w.kind, w.zp, 1.0 / w.inv_ls, to_unit(w.rz_hi, w.rz_lo));
   const double y = t / (w.q2 * z * (1.0 - z));

@@ -21,7 +21,7 @@ namespace gaps {
 
 namespace {
 
-template <int T>
+template <int T, bool kMulti>
 __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, int period) {
   __shared__ int64_t s_pool[T];
   __shared__ EmitTask s_task[T];
@@ -58,17 +58,18 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, 
       if (alive) {
         const int64_t ev = s_pool[tid];
         EmitTask task;
-        const int r = cycle_select_veto(P, E, ev, task);
+        const int r = cycle_select_veto<kMulti>(P, E, ev, task);
         if (r == kCycleAccepted) {
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
           alive = false;
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+          if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
       __syncthreads();
-      if (tid < s_count[1]) cycle_emit(P, E, s_task[tid]);
+      if (tid < s_count[1]) cycle_emit<kMulti>(P, E, s_task[tid]);
       __syncthreads();
     }
 
@@ -87,19 +88,19 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, 
   }
 }
 
-template <int T>
+template <int T, bool kMulti>
 cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks_per_sm, cudaStream_t s) {
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T>, T, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T, kMulti>, T, 0);
   if (e != cudaSuccess) return e;
   if (fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
   int64_t blocks = static_cast<int64_t>(sms) * per_sm;
   const int64_t needed = (E.n + T - 1) / T;
   if (blocks > needed) blocks = needed;
-  k_shower_persistent<T><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period);
+  k_shower_persistent<T, kMulti><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period);
   return cudaGetLastError();
 }
 
@@ -108,11 +109,16 @@ cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks
 cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
                                      cudaStream_t s) {
   if (E.n == 0) return cudaSuccess;
+  const bool multi = E.jobs != nullptr;
   switch (cfg.block_threads) {
-    case 64: return launch_t<64>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 128: return launch_t<128>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 256: return launch_t<256>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 512: return launch_t<512>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 64: return multi ? launch_t<64, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
+                          : launch_t<64, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 128: return multi ? launch_t<128, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
+                           : launch_t<128, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 256: return multi ? launch_t<256, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
+                           : launch_t<256, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
+    case 512: return multi ? launch_t<512, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
+                           : launch_t<512, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

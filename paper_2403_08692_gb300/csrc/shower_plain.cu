@@ -15,11 +15,12 @@ namespace gaps {
 
 namespace {
 
+template <bool kMulti>
 __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
   const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (ev >= E.n) return;
-  const DevParams& P = params_of(P0, E, ev);
-  const uint32_t id = event_id(P, ev);
+  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const uint32_t id = event_id(P, E, ev);
   const Uniforms r0 = draw2(P, id, 0, 0, kDrawME);
   const Uniforms r1 = draw2(P, id, 0, 1, kDrawME);
   int fl = 1 + static_cast<int>(r0.a * P.nf);
@@ -96,9 +97,10 @@ __device__ __forceinline__ int block_rank(bool flag, int* s_warp, int* total) {
 // launch zeroes *reset_count, the output counter of the next launch.
 // Counter word 0 counts finished events (the paper's
 // completedEventsCounter), word 1 those stopped by the veto-cycle limit.
+template <bool kMulti>
 __global__ void __launch_bounds__(kStepThreads, 3)
-    k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, int* list_out,
-                 unsigned long long* out_count, unsigned long long* reset_count) {
+    k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
+                 int* list_out, unsigned long long* out_count, unsigned long long* reset_count) {
   __shared__ int64_t s_ev[kStepThreads];
   __shared__ EmitTask s_task[kStepThreads];
   __shared__ int s_warp[kStepWarps + 1];
@@ -108,8 +110,11 @@ __global__ void __launch_bounds__(kStepThreads, 3)
   if (blockIdx.x == 0 && tid == 0 && reset_count) *reset_count = 0ull;
   if (tid == 0) s_naccept = 0;
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
+  // The list length comes from the previous launch when it is on the device
+  // (n_in is then only the bound the grid was sized for).
+  const int64_t len = n_in_dev ? min(n_in, static_cast<int64_t>(*n_in_dev)) : n_in;
   int64_t ev = -1;
-  if (idx < n_in) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
+  if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
   const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
   int n_active = 0;
   const int slot = block_rank(active, s_warp, &n_active);
@@ -119,17 +124,18 @@ __global__ void __launch_bounds__(kStepThreads, 3)
   if (tid < n_active) {
     const int64_t e = s_ev[tid];
     EmitTask task;
-    const int r = cycle_select_veto(P, E, e, task);
+    const int r = cycle_select_veto<kMulti>(P, E, e, task);
     if (r == kCycleAccepted) {
       s_task[atomicAdd(&s_naccept, 1)] = task;
     } else if (r == kCycleFinished) {
       atomicAdd(&E.counters[0], 1ull);
       if (E.status[e] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+      if (E.job_done) atomicAdd(&E.job_done[E.job_of[e]], 1ull);
     }
     survive = r != kCycleFinished;
   }
   __syncthreads();
-  if (tid < s_naccept) cycle_emit(P, E, s_task[tid]);
+  if (tid < s_naccept) cycle_emit<kMulti>(P, E, s_task[tid]);
   if (!list_out) return;
   int n_survive = 0;
   const int rank = block_rank(survive, s_warp, &n_survive);
@@ -144,15 +150,57 @@ cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s) {
   if (E.n == 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((E.n + threads - 1) / threads);
-  k_me<<<blocks, threads, 0, s>>>(P, E);
+  if (E.jobs)
+    k_me<true><<<blocks, threads, 0, s>>>(P, E);
+  else
+    k_me<false><<<blocks, threads, 0, s>>>(P, E);
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in, int* list_out,
-                              unsigned long long* out_count, unsigned long long* reset_count, cudaStream_t s) {
+cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in,
+                              const unsigned long long* n_in_dev, int* list_out, unsigned long long* out_count,
+                              unsigned long long* reset_count, cudaStream_t s) {
   if (n_in <= 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n_in + kStepThreads - 1) / kStepThreads);
-  k_step_plain<<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, list_out, out_count, reset_count);
+  if (E.jobs)
+    k_step_plain<true>
+        <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+  else
+    k_step_plain<false>
+        <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Append events base .. base + n of the workspace to an active list.
+__global__ void __launch_bounds__(256) k_append_range(int* list, unsigned long long* count, int64_t base, int64_t n) {
+  __shared__ unsigned long long s_pos;
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+  const int64_t take = min(static_cast<int64_t>(blockDim.x), n - first);
+  if (take <= 0) return;
+  if (threadIdx.x == 0) s_pos = atomicAdd(count, static_cast<unsigned long long>(take));
+  __syncthreads();
+  if (threadIdx.x < take) list[s_pos + threadIdx.x] = static_cast<int>(base + first + threadIdx.x);
+}
+
+// Job index of events base .. base + n of the workspace.
+__global__ void __launch_bounds__(256) k_set_job(uint16_t* job_of, int64_t base, int64_t n, int job) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) job_of[base + k] = static_cast<uint16_t>(job);
+}
+
+}  // namespace
+
+cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_append_range<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(list, count, base, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_set_job<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(job_of, base, n, job);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
                   "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "counters",
                   "hist",
-                  "stats", "jobs", "job_begin", "job_of", "total_bytes"]
+                  "stats", "jobs", "job_begin", "job_of", "job_done", "total_bytes"]
 
 
 MAX_JOBS = 1024
@@ -89,6 +89,12 @@ SIGNATURES = {
                                             C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
                                             C.c_void_p]),
     "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
+    "gaps_pool_reset": (C.c_int, [_P(Batch), C.c_void_p]),
+    "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
+                                  C.c_void_p]),
+    "gaps_pool_cycles": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, C.c_void_p]),
+    "gaps_pool_progress": (C.c_int, [_P(Batch), C.c_int64, _P(C.c_int64), C.c_void_p, C.c_void_p]),
+    "gaps_pool_finish": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
     "gaps_last_cuda_error": (C.c_char_p, []),
     "gaps_version": (C.c_int, []),
@@ -262,6 +268,35 @@ def event_shapes_noalloc(px, py, pz, e, n_partons, status, n_events, capacity, s
     _check(load().gaps_event_shapes_noalloc(ptr(px), ptr(py), ptr(pz), ptr(e), ptr(n_partons), ptr(status),
                                             int(n_events), int(capacity), float(sqrt_s), ptr(obs),
                                             _stream_handle(stream)), "gaps_event_shapes_noalloc")
+
+
+def pool_reset(ws, stream=None):
+    _check(load().gaps_pool_reset(C.byref(_batch(ws)), _stream_handle(stream)), "gaps_pool_reset")
+
+
+def pool_admit(p, job_slot, ev_begin, n_events, first_event, ws, cycle, stream=None):
+    _check(load().gaps_pool_admit(C.byref(p), int(job_slot), int(ev_begin), int(n_events), int(first_event),
+                                  C.byref(_batch(ws)), int(cycle), _stream_handle(stream)), "gaps_pool_admit")
+
+
+def pool_cycles(ws, first_cycle, n_cycles, max_active, stream=None):
+    _check(load().gaps_pool_cycles(C.byref(_batch(ws)), int(first_cycle), int(n_cycles), int(max_active),
+                                   _stream_handle(stream)), "gaps_pool_cycles")
+
+
+def pool_progress(ws, cycle, job_done=None, stream=None):
+    """Live events before cycle `cycle`; fills job_done (a host uint64 array
+    of MAX_JOBS elements) when given.  Synchronises the stream."""
+    active = C.c_int64(0)
+    ptr = None if job_done is None else C.c_void_p(job_done.ctypes.data)
+    _check(load().gaps_pool_progress(C.byref(_batch(ws)), int(cycle), C.byref(active), ptr,
+                                     _stream_handle(stream)), "gaps_pool_progress")
+    return active.value
+
+
+def pool_finish(job_slot, ev_begin, n_events, ws, hist_device, stream=None):
+    _check(load().gaps_pool_finish(int(job_slot), int(ev_begin), int(n_events), C.byref(_batch(ws)),
+                                   C.c_void_p(hist_device.data_ptr()), _stream_handle(stream)), "gaps_pool_finish")
 
 
 def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):

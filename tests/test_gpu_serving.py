@@ -1,0 +1,118 @@
+"""Serving loop (continuous batching over a resident pool): jobs that arrive
+while others shower share the veto-cycle launches, wait for pool room when
+the pool is full, and every job's results are the same alone and in the mix.
+Requires a GB300."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_08692_gb300 as g
+    g.load()
+    return g
+
+
+SCALARS = ("hash", "n_partons", "status", "n_steps", "n_trials", "n_winners", "n_emissions", "t", "weight",
+           "me_flavour", "valid")
+
+
+def _capture(ws, begin, n):
+    sc = {k: v[begin:begin + n].cpu().numpy() for k, v in ws.scalars().items()}
+    obs = ws.obs()[:, begin:begin + n].cpu().numpy()
+    mom = {c: v[:, begin:begin + n].cpu().numpy() for c, v in ws.momenta().items()}
+    return sc, obs, mom
+
+
+def _alone(g, p, n, first_event, capacity):
+    import torch
+    ws = g.Workspace(n, capacity, first_event)
+    g.generate_me(p, ws)
+    g.shower(p, ws)
+    g.validate(p, ws)
+    g.observables(p, ws)
+    hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
+    g.histograms(p, ws, hist)
+    torch.cuda.synchronize()
+    return _capture(ws, 0, n), hist.cpu().numpy()
+
+
+def _assert_same_events(a, b, tag):
+    sa, oa, ma = a
+    sb, ob, mb = b
+    for k in SCALARS:
+        assert np.array_equal(sa[k], sb[k]), (tag, k)
+    assert np.array_equal(oa, ob), tag
+    n_partons = sa["n_partons"]
+    live = np.arange(ma["e"].shape[0])[:, None] < n_partons[None, :]
+    for c in ("e", "px", "py", "pz"):
+        assert np.array_equal(ma[c][live], mb[c][live]), (tag, c)
+
+
+def test_pool_allocator_and_slots_reuse(g):
+    """Jobs admitted at different cycles into a pool too small for all of
+    them at once: later jobs wait for room, ranges are reused, and each job
+    equals the same job run alone."""
+    cap = 128
+    specs = [  # (sqrt_s, t_cutoff, seed, n_events, first_event, arrival round)
+        (91.2, 1.0, 11, 20000, 0, 0),
+        (200.0, 0.5, 12, 3000, 0, 0),
+        (91.2, 1.0, 13, 1, 0, 2),
+        (133.0, 2.0, 14, 15000, 777777, 3),
+        (91.2, 1.0, 15, 777, 0, 5),
+        (91.2, 1.0, 16, 25000, 0, 6),   # does not fit until the first jobs finish
+        (200.0, 1.0, 17, 5000, 0, 40),
+    ]
+    jobs = []
+    for k, (rs, tc, seed, n, first, arr) in enumerate(specs):
+        p = g.make_params(sqrt_s=rs, t_cutoff=tc, seed=seed)
+        jobs.append(g.ServeJob(p, n, first, float(arr), tag=k))
+    srv = g.Server(pool_events=40000, capacity=cap, cycles_per_round=3, clock="rounds")
+    seen = {}
+    tag_of = {}
+
+    def on_finish(job, ws, begin, stream):
+        seen[job.tag] = _capture(ws, begin, job.n_events)
+        tag_of[job.tag] = begin
+
+    results = srv.serve(jobs, on_finish=on_finish, max_rounds=100000)
+    assert sorted(r.tag for r in results) == list(range(len(specs)))
+    assert srv.peak_live_jobs >= 3
+    by_tag = {r.tag: r for r in results}
+    # the 25000-event job had to wait for room
+    assert by_tag[5].admitted > by_tag[5].arrival
+    assert srv.alloc.free_events() == srv.pool_events
+    for k, (rs, tc, seed, n, first, arr) in enumerate(specs):
+        p = g.make_params(sqrt_s=rs, t_cutoff=tc, seed=seed)
+        ev_alone, hist_alone = _alone(g, p, n, first, cap)
+        _assert_same_events(seen[k], ev_alone, k)
+        np.testing.assert_allclose(by_tag[k].hist, hist_alone, rtol=1e-12, atol=1e-12)
+        # thrust and heavy-jet mass count every finished valid event once
+        sc = seen[k][0]
+        good = int(((sc["status"] == g.DONE) & (sc["valid"] == 0)).sum())
+        counts = by_tag[k].hist.reshape(6, 102, 3)[:, :, 2].sum(axis=1)
+        assert counts[4] == good and counts[5] == good
+
+
+def test_wall_clock_poisson(g):
+    """Real-time Poisson arrivals: every job completes with its events all
+    counted, latencies are positive, and the pool ends empty."""
+    from paper_2403_08692_gb300 import workloads
+    arrivals = workloads.poisson_arrivals(rate_per_s=100.0, duration_s=0.5, seed=9, n_min=1000, n_max=30000)
+    jobs = [g.ServeJob(g.make_params(seed=s), n, 0, t, tag=k) for k, (t, n, s) in enumerate(arrivals)]
+    srv = g.Server(pool_events=60000, capacity=128, cycles_per_round=8, clock="wall")
+    results = srv.serve(jobs)
+    assert len(results) == len(jobs)
+    for r in results:
+        assert r.latency > 0.0
+        h = r.hist.reshape(6, 102, 3)
+        # thrust counts every finished valid event once (under/overflow included)
+        assert 0.99 * r.n_events <= h[4, :, 2].sum() <= r.n_events
+    assert srv.alloc.free_events() == srv.pool_events
+    s = g.latency_summary(results, max(r.finished for r in results))
+    assert s["jobs"] == len(jobs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0.0
