@@ -193,7 +193,10 @@ int validate(const std::vector<Parton>& ps, double sqrt_s) {
 
 // Binning: log10 y23..y56 on [-4.3, -0.3], 1-T and rho_H on [0, 0.5]; 100
 // bins each plus underflow (row 0) and overflow (row 101).  Undefined values
-// (y <= 0) are not filled.
+// (y <= 0) are not filled.  1-T and rho_H are non-negative by definition
+// (Sec. 3.1); a negative value is the rounding of an exact zero (a two-parton
+// event) and is binned as zero, so that it never depends on the sign of an
+// ulp.
 void histogram_fill(double* hist, const double obs[6], double w) {
   for (int h = 0; h < kNObs; ++h) {
     double x, lo, hi;
@@ -203,7 +206,7 @@ void histogram_fill(double* hist, const double obs[6], double w) {
       lo = -4.3;
       hi = -0.3;
     } else {
-      x = obs[h];
+      x = obs[h] > 0.0 ? obs[h] : 0.0;
       lo = 0.0;
       hi = 0.5;
     }

@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
 // ---------------------------------------------------------- histograms
 // Bin of observable h with value o (log10 y23..y56 on [-4.3, -0.3], 1-T and
 // rho_H on [0, 0.5]; 100 bins plus underflow 0 and overflow 101), or -1 when
-// the value is undefined.
+// the value is undefined.  1-T and rho_H cannot be negative (Sec. 3.1): a
+// negative value is an exact zero after rounding and is binned as zero.
 __device__ __forceinline__ int hist_bin(int h, double o) {
   double x, lo, hi;
   if (h < 4) {
@@ -106,7 +107,7 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
     lo = -4.3;
     hi = -0.3;
   } else {
-    x = o;
+    x = o > 0.0 ? o : 0.0;
     lo = 0.0;
     hi = 0.5;
   }

@@ -72,6 +72,8 @@ def test_config3_persistent_graph_1e7(g, oracle_mod):
     orc = oracle_mod.run(op, 0, n, threads=oracle_mod.threads_available(), want_obs=False)
     chi2, ndf = H.hist_chi2(hist.cpu().numpy().reshape(6, 102, 3), orc["hist"])
     assert chi2 < 1.5, (chi2, ndf)
+    # the same events on both sides: only bin-edge rounding could still differ
+    assert chi2 < 0.05, (chi2, ndf)
     print("config3", cfg.as_dict(), "max steps", st.max_steps, "chi2/ndf", chi2)
     del graph, ws
     torch.cuda.empty_cache()

@@ -158,7 +158,7 @@ def test_histograms_are_the_binned_observables(oracle_mod):
             ok &= x > 0
             v, lo, hi = np.log10(np.where(ok, x, 1.0)), -4.3, -0.3
         else:
-            v, lo, hi = x, 0.0, 0.5
+            v, lo, hi = np.maximum(x, 0.0), 0.0, 0.5   # non-negative by definition
         f = (v - lo) / (hi - lo) * 100
         b = np.where(f < 0, 0, np.where(f >= 100, 101, 1 + np.floor(np.clip(f, 0, 99.999999)).astype(int)))
         sw = np.bincount(b[ok], weights=w[ok], minlength=102)
@@ -167,3 +167,18 @@ def test_histograms_are_the_binned_observables(oracle_mod):
         assert np.array_equal(hist[h, :, 2], n.astype(float))
     # y23 is defined for every event with >= 3 partons
     assert hist[0, :, 2].sum() == np.sum(ev["n_partons"] >= 3)
+
+
+def test_two_parton_shapes_bin_as_zero(oracle_mod):
+    """Events without an emission (the cutoff just below s/4 leaves no phase
+    space) have 1-T = rho_H = 0 up to FP64 rounding in either direction; the
+    histogram puts every one of them in the first bin of [0, 0.5], never in
+    the underflow, whatever the sign of the rounding."""
+    s = 91.2 ** 2
+    p = oracle_mod.make_params(seed=8, t_cutoff=0.2499 * s)
+    r = oracle_mod.run(p, 0, 2000, threads=1)
+    assert np.all(r["events"]["n_partons"] == 2)
+    obs, hist = r["obs"], r["hist"]
+    assert np.all(np.abs(obs[:, 4:6]) < 1e-12)
+    for h in (4, 5):
+        assert hist[h, 0, 2] == 0.0 and hist[h, 1, 2] == 2000.0
