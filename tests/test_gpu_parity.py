@@ -136,7 +136,7 @@ def test_histograms_and_pipeline(g, oracle_mod):
             ok &= x > 0
             v, lo, hi = np.log10(np.where(ok, x, 1.0)), -4.3, -0.3
         else:
-            v, lo, hi = x, 0.0, 0.5
+            v, lo, hi = np.maximum(x, 0.0), 0.0, 0.5   # non-negative by definition
         f = (v - lo) / (hi - lo) * 100
         b = np.where(f < 0, 0, np.where(f >= 100, 101, 1 + np.floor(np.clip(f, 0, 99.999999)).astype(int)))
         np.testing.assert_allclose(h2[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=102), rtol=1e-12)
