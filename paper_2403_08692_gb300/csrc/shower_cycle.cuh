@@ -103,13 +103,24 @@ __device__ __forceinline__ float unit_float(uint32_t hi, uint32_t lo) {
   return fmaf(a, 0x1p-26f, fmaf(b, 0x1p-52f, 0x1p-53f));
 }
 
-// Everything GenerateEmission needs about an accepted winner.
+// Everything GenerateEmission needs about an accepted winner (56 bytes:
+// workspaces hold fewer than 2^31 events and at most 255 partons each).
 struct EmitTask {
-  int64_t ev;
   double lnt, q2, zp, inv_ls;
   uint32_t rz_hi, rz_lo;
-  int i, k, side, kappa, kind, n, step, pad;
+  int32_t ev, step;
+  uint8_t i, k, n, side, kappa, kind, pad0, pad1;
 };
+
+// A dipole whose cache entry an emission invalidated: parton slots x and k,
+// partners on x's side `side`, of the event of task t in the block's queue.
+// An emission invalidates at most kMaxRefresh dipoles: (i, j), (j, k) and
+// the other partners of the splitter and of the spectator.
+constexpr int kMaxRefresh = 4;
+__device__ __forceinline__ uint32_t pack_refresh(int t, int x, int side, int k) {
+  return static_cast<uint32_t>(t) | (static_cast<uint32_t>(x) << 10) | (static_cast<uint32_t>(k) << 18) |
+         (static_cast<uint32_t>(side) << 26);
+}
 
 // 1/c of a kernel for a dipole, c = alpha_s^over/(2 pi) * integral of
 // P^over over [z-, z+].
@@ -343,7 +354,7 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
     finish_event(E, ev, GAPS_OVERFLOW, exp(task.lnt));
     return kCycleFinished;
   }
-  task.ev = ev;
+  task.ev = static_cast<int32_t>(ev);
   task.rz_hi = rw.x;
   task.rz_lo = rw.y;
   task.n = n;
@@ -351,10 +362,14 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
   return kCycleAccepted;
 }
 
-// Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours,
-// the new parton in slot n, and the dipoles whose invariant mass moved.
+// Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours
+// and the new parton in slot n.  The dipoles whose invariant mass moved are
+// appended to the block's refresh list (jobs, *n_jobs) under task_index; the
+// caller recomputes them with refresh_dipole after a block barrier, spread
+// over all of its threads, so that this FP64-heavy step runs in full warps.
 template <bool kMulti>
-__device__ inline void cycle_emit(const DevParams& P0, const Events& E, const EmitTask& w) {
+__device__ inline void cycle_emit(const DevParams& P0, const Events& E, const EmitTask& w, int task_index,
+                                  uint32_t* jobs, int* n_jobs) {
   const int64_t ev = w.ev;
   const DevParams& P = params_of<kMulti>(P0, E, ev);
   const uint32_t id = event_id(P, E, ev);
@@ -410,11 +425,12 @@ __device__ inline void cycle_emit(const DevParams& P0, const Events& E, const Em
       E.link[E.link_at(0, w.k, ev)] = static_cast<uint8_t>(j);
     }
   }
-  // Recompute every dipole with a moved parton once: dipole (x, side) and
-  // its partner's opposite side share Q^2; a pair whose partner is a moved
-  // parton listed earlier was already done from that side.
+  // Every dipole with a moved parton, once: dipole (x, side) and its
+  // partner's opposite side share Q^2; a pair whose partner is a moved parton
+  // listed earlier was already taken from that side.
   const int moved[3] = {w.i, j, w.k};
-  const V4 mp[3] = {pi, pj, pb};
+  uint32_t mine[kMaxRefresh];
+  int count = 0;
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const int x = moved[m];
@@ -425,14 +441,27 @@ __device__ inline void cycle_emit(const DevParams& P0, const Events& E, const Em
       bool seen = false;
 #pragma unroll
       for (int m2 = 0; m2 < m; ++m2) seen |= (k == moved[m2]);
-      if (seen) continue;
-      const DipoleEntry d = make_dipole(P, 2.0 * mdot(mp[m], load_p(E, k, ev)));
-      store_dipole(E, ev, x, side, d);
-      store_dipole(E, ev, k, 1 - side, d);
+      if (seen || count == kMaxRefresh) continue;
+      mine[count++] = pack_refresh(task_index, x, side, k);
     }
   }
+  const int at = atomicAdd(n_jobs, count);
+  for (int c = 0; c < count; ++c) jobs[at + c] = mine[c];
   E.n_partons[ev] = j + 1;
   E.n_emissions[ev] += 1;
+}
+
+// Recompute one dipole of the refresh list from the stored momenta of its
+// two partons (the oracle's formulas, in the oracle's operand order).
+template <bool kMulti>
+__device__ inline void refresh_dipole(const DevParams& P0, const Events& E, const EmitTask* tasks, uint32_t job) {
+  const int t = static_cast<int>(job & 1023u), x = static_cast<int>((job >> 10) & 255u);
+  const int k = static_cast<int>((job >> 18) & 255u), side = static_cast<int>((job >> 26) & 1u);
+  const int64_t ev = tasks[t].ev;
+  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const DipoleEntry d = make_dipole(P, 2.0 * mdot(load_p(E, x, ev), load_p(E, k, ev)));
+  store_dipole(E, ev, x, side, d);
+  store_dipole(E, ev, k, 1 - side, d);
 }
 
 }  // namespace gaps

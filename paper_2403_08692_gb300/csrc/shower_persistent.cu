@@ -23,9 +23,10 @@ namespace {
 
 template <int T, bool kMulti>
 __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, int period) {
-  __shared__ int64_t s_pool[T];
+  __shared__ int32_t s_pool[T];
   __shared__ EmitTask s_task[T];
-  __shared__ int s_count[4];  // pool size, accepted emissions, refill base (low), refill count
+  __shared__ uint32_t s_jobs[kMaxRefresh * T];
+  __shared__ int s_count[5];  // pool size, accepted emissions, unused, refill count, refresh jobs
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   unsigned long long* cursor = &E.counters[6];
@@ -46,14 +47,17 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, 
     }
     __syncthreads();
     const int take = s_count[3];
-    if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int64_t>(s_base) + (tid - pool);
+    if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int32_t>(s_base + (tid - pool));
     pool += take;
     __syncthreads();
     if (pool == 0) break;
 
     bool alive = tid < pool;
     for (int c = 0; c < period; ++c) {
-      if (tid == 0) s_count[1] = 0;
+      if (tid == 0) {
+        s_count[1] = 0;
+        s_count[4] = 0;
+      }
       __syncthreads();
       if (alive) {
         const int64_t ev = s_pool[tid];
@@ -69,12 +73,14 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, 
         }
       }
       __syncthreads();
-      if (tid < s_count[1]) cycle_emit<kMulti>(P, E, s_task[tid]);
+      if (tid < s_count[1]) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_count[4]);
+      __syncthreads();
+      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
       __syncthreads();
     }
 
     // Compact: the still-active events move to the front of the pool.
-    const int64_t mine = alive ? s_pool[tid] : 0;
+    const int32_t mine = alive ? s_pool[tid] : 0;
     if (tid == 0) s_count[0] = 0;
     __syncthreads();
     const unsigned mask = __ballot_sync(0xffffffffu, alive);

@@ -63,7 +63,14 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
   E.valid[ev] = 0;
 }
 
-constexpr int kStepThreads = 256;
+// Launch shape of the veto-cycle kernel (compile-time tuning knobs).
+#ifndef GAPS_STEP_THREADS
+#define GAPS_STEP_THREADS 256
+#endif
+#ifndef GAPS_STEP_MIN_BLOCKS
+#define GAPS_STEP_MIN_BLOCKS 4
+#endif
+constexpr int kStepThreads = GAPS_STEP_THREADS;
 constexpr int kStepWarps = kStepThreads / 32;
 
 // Rank of this thread among the block's threads with `flag` set, in thread
@@ -98,17 +105,21 @@ __device__ __forceinline__ int block_rank(bool flag, int* s_warp, int* total) {
 // Counter word 0 counts finished events (the paper's
 // completedEventsCounter), word 1 those stopped by the veto-cycle limit.
 template <bool kMulti>
-__global__ void __launch_bounds__(kStepThreads, 3)
+__global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
                  int* list_out, unsigned long long* out_count, unsigned long long* reset_count) {
   __shared__ int64_t s_ev[kStepThreads];
   __shared__ EmitTask s_task[kStepThreads];
+  __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
   __shared__ int s_warp[kStepWarps + 1];
-  __shared__ int s_naccept;
+  __shared__ int s_naccept, s_njobs;
   __shared__ unsigned long long s_out_base;
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid == 0 && reset_count) *reset_count = 0ull;
-  if (tid == 0) s_naccept = 0;
+  if (tid == 0) {
+    s_naccept = 0;
+    s_njobs = 0;
+  }
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
   // The list length comes from the previous launch when it is on the device
   // (n_in is then only the bound the grid was sized for).
@@ -135,7 +146,9 @@ __global__ void __launch_bounds__(kStepThreads, 3)
     survive = r != kCycleFinished;
   }
   __syncthreads();
-  if (tid < s_naccept) cycle_emit<kMulti>(P, E, s_task[tid]);
+  if (tid < s_naccept) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
+  __syncthreads();
+  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
   if (!list_out) return;
   int n_survive = 0;
   const int rank = block_rank(survive, s_warp, &n_survive);
