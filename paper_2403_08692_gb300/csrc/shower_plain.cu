@@ -71,50 +71,29 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
 #define GAPS_STEP_MIN_BLOCKS 4
 #endif
 constexpr int kStepThreads = GAPS_STEP_THREADS;
-constexpr int kStepWarps = kStepThreads / 32;
 
-// Rank of this thread among the block's threads with `flag` set, in thread
-// order, and their number (*total).  Contains two block barriers.
-__device__ __forceinline__ int block_rank(bool flag, int* s_warp, int* total) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned mask = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) s_warp[warp] = __popc(mask);
-  __syncthreads();
-  if (tid == 0) {
-    int run = 0;
-    for (int w = 0; w < kStepWarps; ++w) {
-      const int c = s_warp[w];
-      s_warp[w] = run;
-      run += c;
-    }
-    s_warp[kStepWarps] = run;
-  }
-  __syncthreads();
-  *total = s_warp[kStepWarps];
-  return s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
-}
-
-// One veto cycle over the events list_in[0 .. n_in) (the first cycle passes
-// no list: events 0 .. n_in).  The block packs its still-active events into
-// its leading threads in event order, so finished events (the paper's
-// endShower early exit) cost no warp time, runs the select/veto phase, packs
-// the accepted emissions again for the emission phase, and appends its
-// surviving events, in order, to list_out with one atomic per block.  The
-// host reads *out_count to size the next launch and to end the loop; this
-// launch zeroes *reset_count, the output counter of the next launch.
-// Counter word 0 counts finished events (the paper's
-// completedEventsCounter), word 1 those stopped by the veto-cycle limit.
+// One veto cycle over the events list_in[0 .. n_in): the list holds the
+// active events only (the previous launch wrote it), so every thread of a
+// full block has an event to shower.  Without a list (the first cycle, or a
+// single step over the whole batch) the thread of event idx runs it if it is
+// still active.  The select/veto phase runs per thread; the accepted
+// emissions (about one in ten) are packed into the block's leading threads
+// for the emission phase and their dipole refreshes spread over the whole
+// block, so the FP64-heavy work runs in full warps.  Surviving events are
+// appended to list_out with one atomic per warp (the list order does not
+// matter: every draw is keyed by event and cycle).  The host reads
+// *out_count to size the next launch and to end the loop; this launch zeroes
+// *reset_count, the output counter of the next launch.  Counter word 0 counts
+// finished events (the paper's completedEventsCounter), word 1 those stopped
+// by the veto-cycle limit.
 template <bool kMulti>
 __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
                  int* list_out, unsigned long long* out_count, unsigned long long* reset_count) {
-  __shared__ int64_t s_ev[kStepThreads];
   __shared__ EmitTask s_task[kStepThreads];
   __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
-  __shared__ int s_warp[kStepWarps + 1];
   __shared__ int s_naccept, s_njobs;
-  __shared__ unsigned long long s_out_base;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (blockIdx.x == 0 && tid == 0 && reset_count) *reset_count = 0ull;
   if (tid == 0) {
     s_naccept = 0;
@@ -127,34 +106,34 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   int64_t ev = -1;
   if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
   const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
-  int n_active = 0;
-  const int slot = block_rank(active, s_warp, &n_active);
-  if (active) s_ev[slot] = ev;
   __syncthreads();
   bool survive = false;
-  if (tid < n_active) {
-    const int64_t e = s_ev[tid];
+  if (active) {
     EmitTask task;
-    const int r = cycle_select_veto<kMulti>(P, E, e, task);
+    const int r = cycle_select_veto<kMulti>(P, E, ev, task);
     if (r == kCycleAccepted) {
       s_task[atomicAdd(&s_naccept, 1)] = task;
     } else if (r == kCycleFinished) {
       atomicAdd(&E.counters[0], 1ull);
-      if (E.status[e] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
-      if (E.job_done) atomicAdd(&E.job_done[E.job_of[e]], 1ull);
+      if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+      if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
     }
     survive = r != kCycleFinished;
+  }
+  if (list_out) {
+    const unsigned mask = __ballot_sync(0xffffffffu, survive);
+    if (mask != 0u) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(out_count, static_cast<unsigned long long>(__popc(mask)));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (survive) list_out[base + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(ev);
+    }
   }
   __syncthreads();
   if (tid < s_naccept) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
   __syncthreads();
   for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
-  if (!list_out) return;
-  int n_survive = 0;
-  const int rank = block_rank(survive, s_warp, &n_survive);
-  if (tid == 0 && n_survive > 0) s_out_base = atomicAdd(out_count, static_cast<unsigned long long>(n_survive));
-  __syncthreads();
-  if (survive) list_out[s_out_base + rank] = static_cast<int>(s_ev[tid]);
 }
 
 }  // namespace
