@@ -105,11 +105,14 @@ typedef struct gaps_layout {
   int64_t buckets;        /* int32 [769]: scratch of gaps_observables (multiplicity buckets) */
   int64_t order;          /* int32 [n_events]: scratch of gaps_observables (events by multiplicity) */
   int64_t active;         /* int32 [2][n_events]: scratch of the plain shower (active-event lists) */
-  int64_t counters;       /* uint64 [16]: device counters of the last shower call: 0 finished events,
+  int64_t tasks;          /* [2][n_events] 56-byte records: scratch of the plain shower (the accepted
+                             emissions deferred to the next launch) */
+  int64_t counters;       /* uint64 [32]: device counters of the last shower call: 0 finished events,
                              1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
                              merges with several FP64 candidates; 6 the persistent form's event cursor;
-                             8, 9 the plain form's active-list lengths */
+                             8, 9 the plain form's active-list lengths, 16, 17 its deferred-emission
+                             counts; 10..12 and 18..20 the same for the serving pool */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
@@ -212,13 +215,15 @@ int gaps_pool_reset(const gaps_batch* pool, void* stream);
 int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begin, int64_t n_events,
                     uint32_t first_event, const gaps_batch* pool, int64_t cycle, void* stream);
 
-/* Enqueue n_cycles veto cycles, numbered first_cycle.., over the live
- * events; max_active bounds their number (it sizes the grids).  No host
+/* Enqueue n_cycles shower steps, numbered first_cycle.., over the live
+ * events: each step runs the select/veto phase of the events in the active
+ * list and the splittings the previous step accepted (gaps_shower's plain
+ * form).  max_active bounds the live events (it sizes the grids).  No host
  * synchronisation. */
 int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
                      void* stream);
 
-/* Read the number of live events before cycle `cycle` and, if job_done_out
+/* Read the number of live events before step `cycle` and, if job_done_out
  * is not NULL, the finished-event count of every job slot
  * (GAPS_MAX_JOBS values).  Synchronises the stream. */
 int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_out, uint64_t* job_done_out,

@@ -62,7 +62,8 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->buckets = take(4 * 769);
   L->order = take(4 * n);
   L->active = take(8 * n);
-  L->counters = take(8 * 16);
+  L->tasks = take(2 * static_cast<int64_t>(kEmitTaskBytes) * n);
+  L->counters = take(8 * kCounterWords);
   L->hist = take(8 * GAPS_HIST_DOUBLES);
   L->stats = take(sizeof(gaps_stats));
   L->jobs = take(static_cast<int64_t>(sizeof(DevParams)) * GAPS_MAX_JOBS);
@@ -146,6 +147,7 @@ Events make_events(const gaps_batch& b) {
   E.buckets = reinterpret_cast<int*>(base + L.buckets);
   E.order = reinterpret_cast<int*>(base + L.order);
   E.active = reinterpret_cast<int*>(base + L.active);
+  E.tasks = reinterpret_cast<EmitTask*>(base + L.tasks);
   E.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
   E.hist = reinterpret_cast<double*>(base + L.hist);
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
@@ -312,7 +314,10 @@ bool config_ok(const gaps_persistent_config& c) {
 // Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
 // persistent form's event cursor).
 cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
-  return cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
+  // words 0..9 and the plain form's deferred-emission counts 16, 17
+  cudaError_t e = cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + 16, 0, 2 * sizeof(unsigned long long), s);
+  return e;
 }
 
 int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
@@ -359,22 +364,28 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     if (launches_out) *launches_out = 1;
     return cnt[1] > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
   }
-  // The host loop of App. C: one cycle for every active event per launch,
-  // then the host reads back how many events are still active.  Each launch
-  // appends its survivors to the other half of the active-list double
-  // buffer, so the next launch covers only those.  An event stops after
-  // max_steps cycles, so the loop ends after at most max_steps + 1 launches.
+  // The host loop of App. C: one step for every active event per launch,
+  // then the host reads back how many events are still active.  A step
+  // runs the select/veto phase of the listed events and the splittings the
+  // previous step accepted; each launch writes its vetoed and emitted events
+  // to the other half of the active-list double buffer and its accepted
+  // emissions to the other half of the task double buffer.  An event stops
+  // after max_steps cycles and each cycle takes at most two launches, so the
+  // loop ends after at most 2 max_steps + 1 launches.
   double total_ms = 0.0;
-  unsigned long long readback[10] = {0};  // counter words 0..9
-  int64_t n_in = E.n;
-  while (n_in > 0) {
-    if (launches > static_cast<int64_t>(P.max_steps)) break;
+  unsigned long long readback[kCounterWords] = {0};
+  int64_t n_list = E.n, n_tasks = 0;
+  while (n_list + n_tasks > 0) {
+    if (launches > 2 * static_cast<int64_t>(P.max_steps) + 1) break;
     const int in_half = static_cast<int>(launches & 1), out_half = 1 - in_half;
     const int* list_in = launches == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
     int* list_out = E.active + static_cast<size_t>(out_half) * E.n;
+    const EmitTask* tasks_in = E.tasks + static_cast<size_t>(in_half) * E.n;
+    EmitTask* tasks_out = E.tasks + static_cast<size_t>(out_half) * E.n;
     if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
-    e = launch_step_plain(P, E, list_in, n_in, nullptr, list_out, &E.counters[8 + out_half],
-                          &E.counters[8 + in_half], s);
+    e = launch_step_deferred(P, E, list_in, n_list, nullptr, tasks_in, n_tasks, nullptr, list_out,
+                             &E.counters[8 + out_half], tasks_out, &E.counters[16 + out_half],
+                             &E.counters[8 + in_half], &E.counters[16 + in_half], s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
     ++launches;
@@ -384,7 +395,8 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     if (e != cudaSuccess) return cuda_fail(e);
     cnt[0] = readback[0];
     cnt[1] = readback[1];
-    n_in = static_cast<int64_t>(readback[8 + out_half]);
+    n_list = static_cast<int64_t>(readback[8 + out_half]);
+    n_tasks = static_cast<int64_t>(readback[16 + out_half]);
     if (ev0) {
       float ms = 0.0f;
       e = cudaEventElapsedTime(&ms, ev0, ev1);
@@ -535,16 +547,18 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
 }
 
 // ---------------------------------------------------------- serving pool
-// Counter words 10..12 hold the pool's active-list lengths: cycle c reads
-// word 10 + c%3, writes its survivors' count to 10 + (c+1)%3 and clears
-// 10 + (c+2)%3 for the cycle after it; the lists are active[c%2].
+// Counter words 10..12 hold the pool's active-list lengths and 18..20 its
+// deferred-emission counts: step c reads words 10 + c%3 and 18 + c%3, writes
+// its outputs' counts to 10 + (c+1)%3 and 18 + (c+1)%3 and clears
+// 10 + (c+2)%3 and 18 + (c+2)%3 for the step after it; the lists are
+// active[c%2] and tasks[c%2].  A live event is in one of them.
 
 int gaps_pool_reset(const gaps_batch* pool, void* stream) {
   DevParams P;
   Events E;
   if (prepare(nullptr, pool, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(E.counters, 0, 16 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(E.counters, 0, kCounterWords * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(E.job_done, 0, GAPS_MAX_JOBS * sizeof(unsigned long long), s);
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
@@ -583,10 +597,11 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
     return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t c = first_cycle; c < first_cycle + n_cycles; ++c) {
-    const cudaError_t e = launch_step_plain(
-        P, E, E.active + static_cast<size_t>(c % 2) * E.stride, max_active, &E.counters[10 + c % 3],
-        E.active + static_cast<size_t>((c + 1) % 2) * E.stride, &E.counters[10 + (c + 1) % 3],
-        &E.counters[10 + (c + 2) % 3], s);
+    const size_t in = static_cast<size_t>(c % 2) * E.stride, out = static_cast<size_t>((c + 1) % 2) * E.stride;
+    const cudaError_t e = launch_step_deferred(
+        P, E, E.active + in, max_active, &E.counters[10 + c % 3], E.tasks + in, max_active,
+        &E.counters[18 + c % 3], E.active + out, &E.counters[10 + (c + 1) % 3], E.tasks + out,
+        &E.counters[18 + (c + 1) % 3], &E.counters[10 + (c + 2) % 3], &E.counters[18 + (c + 2) % 3], s);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return GAPS_OK;
@@ -598,13 +613,13 @@ int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_ou
   Events E;
   if (prepare(nullptr, pool, &P, &E) != GAPS_OK || cycle < 0 || !active_out) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned long long active = 0;
-  cudaError_t e = cudaMemcpyAsync(&active, &E.counters[10 + cycle % 3], sizeof(active), cudaMemcpyDeviceToHost, s);
+  unsigned long long counts[kCounterWords] = {0};
+  cudaError_t e = cudaMemcpyAsync(counts, E.counters, sizeof(counts), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && job_done_out)
     e = cudaMemcpyAsync(job_done_out, E.job_done, GAPS_MAX_JOBS * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e);
-  *active_out = static_cast<int64_t>(active);
+  *active_out = static_cast<int64_t>(counts[10 + cycle % 3] + counts[18 + cycle % 3]);
   return GAPS_OK;
 }
 

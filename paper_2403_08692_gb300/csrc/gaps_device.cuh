@@ -43,6 +43,19 @@ struct DevParams {
   int64_t id_offset;
 };
 
+// Everything GenerateEmission needs about an accepted winner (56 bytes:
+// workspaces hold fewer than 2^31 events and at most 255 partons each).
+struct EmitTask {
+  double lnt, q2, zp, inv_ls;
+  uint32_t rz_hi, rz_lo;
+  int32_t ev, step;
+  uint8_t i, k, n, side, kappa, kind, pad0, pad1;
+};
+constexpr int kEmitTaskBytes = 56;
+static_assert(sizeof(EmitTask) == kEmitTaskBytes, "EmitTask layout");
+// Device counter words in the workspace.
+constexpr int kCounterWords = 32;
+
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {
   double *px, *py, *pz, *e;
@@ -60,6 +73,7 @@ struct Events {
   int* buckets;  // [769] scratch of the observables' multiplicity buckets
   int* order;    // [n] scratch: finished events ordered by multiplicity
   int* active;   // [2][n] scratch: the plain form's active-event lists
+  EmitTask* tasks;  // [2][n] scratch: the plain form's deferred emissions
   unsigned long long* counters;
   double* hist;
   gaps_stats* stats;

@@ -22,6 +22,17 @@ cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s);
 cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* list_in, int64_t n_in,
                               const unsigned long long* n_in_dev, int* list_out, unsigned long long* out_count,
                               unsigned long long* reset_count, cudaStream_t s);
+// One plain-form step with deferred emissions: the select/veto phase for
+// list_in[0 .. n_list) (list_in = NULL: events 0 .. n_list) and the
+// emissions tasks_in[0 .. n_tasks) accepted by the previous step.  Vetoed and
+// emitted events go to list_out, accepted ones to tasks_out; *reset_list and
+// *reset_tasks are zeroed.  n_list_dev / n_tasks_dev (may be NULL): the
+// lengths on the device, the host ones then only bound them.
+cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int* list_in, int64_t n_list,
+                                 const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
+                                 const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
+                                 EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
+                                 unsigned long long* reset_tasks, cudaStream_t s);
 cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s);
 cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, cudaStream_t s);
 // Persistent form; counters word 6 is the event cursor and must be zero.

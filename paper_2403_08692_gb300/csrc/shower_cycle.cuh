@@ -103,14 +103,6 @@ __device__ __forceinline__ float unit_float(uint32_t hi, uint32_t lo) {
   return fmaf(a, 0x1p-26f, fmaf(b, 0x1p-52f, 0x1p-53f));
 }
 
-// Everything GenerateEmission needs about an accepted winner (56 bytes:
-// workspaces hold fewer than 2^31 events and at most 255 partons each).
-struct EmitTask {
-  double lnt, q2, zp, inv_ls;
-  uint32_t rz_hi, rz_lo;
-  int32_t ev, step;
-  uint8_t i, k, n, side, kappa, kind, pad0, pad1;
-};
 
 // A dipole whose cache entry an emission invalidated: parton slots x and k,
 // partners on x's side `side`, of the event of task t in the block's queue.

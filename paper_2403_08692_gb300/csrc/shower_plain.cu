@@ -136,6 +136,84 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
 }
 
+// Slot of this thread's item in an output list shared by the grid: one
+// atomic per warp.  Every lane of the warp must call it; returns -1 where
+// flag is false.
+__device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long long* count) {
+  const unsigned mask = __ballot_sync(0xffffffffu, flag);
+  if (mask == 0u) return -1;
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, static_cast<unsigned long long>(__popc(mask)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return flag ? static_cast<int64_t>(base + __popc(mask & ((1u << lane) - 1u))) : -1;
+}
+
+// One step of the plain form with the emissions deferred by one launch.
+// Blocks [0, select_blocks) run SelectWinnerEmission, CheckCutoff and
+// AcceptOrVeto for the events list_in[0 .. n_list) (no list: events
+// 0 .. n_list), one event per thread and without a block barrier: a vetoed
+// event goes back to list_out, an accepted one leaves its emission in
+// tasks_out, a finished one leaves.  The remaining blocks run
+// GenerateEmission for the accepted emissions of the previous launch,
+// tasks_in[0 .. n_tasks), 256 per block in full warps, refresh the dipoles
+// they moved block-wide, and put their events back in list_out.  An event
+// with a pending emission is in no list, so it never runs two phases in one
+// launch, and its history is the one the fused cycle gives (every draw is
+// keyed by event and cycle).  Lengths given on the device (n_list_dev,
+// n_tasks_dev) replace the host ones, which then only bound them.  The
+// launch zeroes *reset_list and *reset_tasks, the output counters of the
+// next launch.
+template <bool kMulti>
+__global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
+    k_step_deferred(DevParams P, Events E, int64_t select_blocks, const int* list_in, int64_t n_list,
+                    const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
+                    const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
+                    EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
+                    unsigned long long* reset_tasks) {
+  __shared__ EmitTask s_task[kStepThreads];
+  __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
+  __shared__ int s_njobs;
+  const int tid = threadIdx.x;
+  if (blockIdx.x == 0 && tid == 0) {
+    if (reset_list) *reset_list = 0ull;
+    if (reset_tasks) *reset_tasks = 0ull;
+  }
+  if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
+    const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
+    int64_t ev = -1;
+    if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
+    const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
+    int r = kCycleFinished;
+    EmitTask task;
+    if (active) {
+      r = cycle_select_veto<kMulti>(P, E, ev, task);
+      if (r == kCycleFinished) {
+        atomicAdd(&E.counters[0], 1ull);
+        if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
+        if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
+      }
+    }
+    const int64_t at_task = warp_append_slot(r == kCycleAccepted, task_count);
+    if (at_task >= 0) tasks_out[at_task] = task;
+    const int64_t at_list = warp_append_slot(r == kCycleVetoed, list_count);
+    if (at_list >= 0) list_out[at_list] = static_cast<int>(ev);
+    return;
+  }
+  const int64_t k = (static_cast<int64_t>(blockIdx.x) - select_blocks) * kStepThreads + tid;
+  const int64_t len = n_tasks_dev ? min(n_tasks, static_cast<int64_t>(*n_tasks_dev)) : n_tasks;
+  const bool has = k < len;
+  if (tid == 0) s_njobs = 0;
+  if (has) s_task[tid] = tasks_in[k];
+  __syncthreads();
+  if (has) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
+  __syncthreads();
+  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
+  const int64_t at_list = warp_append_slot(has, list_count);
+  if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
+}
+
 }  // namespace
 
 cudaError_t launch_me(const DevParams& P, const Events& E, cudaStream_t s) {
@@ -160,6 +238,26 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
   else
     k_step_plain<false>
         <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int* list_in, int64_t n_list,
+                                 const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
+                                 const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
+                                 EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
+                                 unsigned long long* reset_tasks, cudaStream_t s) {
+  const int64_t select_blocks = (n_list + kStepThreads - 1) / kStepThreads;
+  const int64_t emit_blocks = (n_tasks + kStepThreads - 1) / kStepThreads;
+  if (select_blocks + emit_blocks == 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>(select_blocks + emit_blocks);
+  if (E.jobs)
+    k_step_deferred<true><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
+                                                         n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
+                                                         task_count, reset_list, reset_tasks);
+  else
+    k_step_deferred<false><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
+                                                          n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
+                                                          task_count, reset_list, reset_tasks);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ class Batch(C.Structure):
 _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "dq2", "dzp", "dinv", "t", "lnt",
                   "weight", "hash",
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
-                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "counters",
+                  "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "tasks",
+                  "counters",
                   "hist",
                   "stats", "jobs", "job_begin", "job_of", "job_done", "total_bytes"]
 

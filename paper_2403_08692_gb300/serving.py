@@ -33,6 +33,8 @@ import numpy as np
 
 from . import gaps
 
+COUNTER_WORDS = 32   # device counter words of a workspace (include/gaps.h)
+
 
 @dataclasses.dataclass
 class ServeJob:
@@ -129,9 +131,10 @@ class Server:
         self.stream = torch.cuda.Stream(device=device)
         self.hist = torch.zeros((gaps.MAX_JOBS, gaps.HIST_DOUBLES), dtype=torch.float64, device=device)
         self.hist_host = torch.empty((gaps.MAX_JOBS, gaps.HIST_DOUBLES), dtype=torch.float64).pin_memory()
-        self._counters = self.ws.view("counters", torch.int64, (16,))
+        self._counters = self.ws.view("counters", torch.int64, (COUNTER_WORDS,))
         self._job_done = self.ws.view("job_done", torch.int64, (gaps.MAX_JOBS,))
-        self._progress_host = [torch.empty(1 + gaps.MAX_JOBS, dtype=torch.int64).pin_memory() for _ in range(2)]
+        self._progress_host = [torch.empty(COUNTER_WORDS + gaps.MAX_JOBS, dtype=torch.int64).pin_memory()
+                               for _ in range(2)]
         self._torch = torch
         self.reset()
 
@@ -176,22 +179,22 @@ class Server:
         self.cycle += k
         self.launched_cycles += k
         buf = self._progress_host[self.rounds % 2]
-        w = 10 + self.cycle % 3
         with torch.cuda.stream(self.stream):
-            buf[0:1].copy_(self._counters[w:w + 1], non_blocking=True)
-            buf[1:].copy_(self._job_done, non_blocking=True)
+            buf[:COUNTER_WORDS].copy_(self._counters, non_blocking=True)
+            buf[COUNTER_WORDS:].copy_(self._job_done, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.stream)
-        self._inflight.append((ev, buf, self.admitted_events, self.rounds))
+        self._inflight.append((ev, buf, self.admitted_events, self.rounds, self.cycle))
         self.rounds += 1
 
     def _read_round(self, now, on_finish):
         torch = self._torch
-        ev, buf, admitted_at_copy, read_round = self._inflight.popleft()
+        ev, buf, admitted_at_copy, read_round, cycle = self._inflight.popleft()
         ev.synchronize()
-        active = int(buf[0])
+        # live events: the active list and the pending emissions of the next step
+        active = int(buf[10 + cycle % 3]) + int(buf[18 + cycle % 3])
         self.bound = active + (self.admitted_events - admitted_at_copy)
-        done = buf[1:].numpy()
+        done = buf[COUNTER_WORDS:].numpy()
         for slot in list(self.live):
             job, begin, admitted, admitted_round = self.live[slot]
             # A job admitted after this read was enqueued would see the

@@ -36,7 +36,9 @@ def test_config1_small_plain(g, oracle_mod):
     sc = gpu["scalars"]
     assert np.all(sc["status"] == g.DONE)
     assert np.all(sc["valid"] == 0)
-    assert gpu["launches"] == sc["n_steps"].max() + 0  # the last launch finishes the last event
+    # one launch per select/veto phase and one per deferred splitting: the
+    # last launch finishes the event with the most of both
+    assert gpu["launches"] == (sc["n_steps"] + sc["n_emissions"]).max()
     print("agreement", res)
 
 
@@ -85,7 +87,9 @@ def test_step_limit(g, oracle_mod):
     sc = gpu["scalars"]
     assert np.array_equal(sc["status"], orc["events"]["status"])
     assert np.any(sc["status"] == g.STEP_LIMIT)
-    assert gpu["launches"] == 7
+    # step-limited events need one more launch to notice the limit
+    lim = sc["status"] == g.STEP_LIMIT
+    assert gpu["launches"] == (sc["n_steps"] + sc["n_emissions"])[lim].max() + 1
 
 
 def test_empty_batch_is_a_no_op(g):
@@ -149,7 +153,7 @@ def test_histograms_and_pipeline(g, oracle_mod):
     assert st.sum_steps == int(sc["n_steps"].sum())
     assert st.sum_emissions == int(sc["n_emissions"].sum())
     assert st.max_steps == int(sc["n_steps"].max())
-    assert st.launches == st.max_steps
+    assert st.max_steps <= st.launches <= 2 * st.max_steps
     np.testing.assert_allclose(st.sum_weight, w.sum(), rtol=1e-12)
 
 

@@ -132,7 +132,7 @@ def test_run_with_persistent_form(g):
     rc1, st1 = g.run(p, g.Workspace(30000, 128), h1, g.SHOWER_PLAIN)
     rc2, st2 = g.run(p, g.Workspace(30000, 128), h2, g.SHOWER_PERSISTENT)
     assert rc1 == rc2 == 0
-    assert st2.launches == 1 and st1.launches == st1.max_steps
+    assert st2.launches == 1 and st1.max_steps <= st1.launches <= 2 * st1.max_steps
     for f in ("n_done", "sum_steps", "sum_trials", "sum_emissions", "max_steps"):
         assert getattr(st1, f) == getattr(st2, f), f
     np.testing.assert_allclose(h1.numpy(), h2.numpy(), rtol=1e-12, atol=1e-9)
