@@ -192,36 +192,40 @@ __device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int st
   E.t[ev] = t;
 }
 
-// Phase 1 of a cycle for active event ev.  Returns kCycleFinished when the
-// event left the active state (status written), kCycleAccepted with `task`
-// filled when an emission must be generated, kCycleVetoed otherwise.
-template <bool kMulti>
-__device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
-  const DevParams& P = params_of<kMulti>(P0, E, ev);
-  const uint32_t id = event_id(P, E, ev);
-  const int n = E.n_partons[ev];
-  const int step = E.n_steps[ev];
-  const double lnt = E.lnt[ev];
-  if (step >= P.max_steps) {
-    finish_event(E, ev, GAPS_STEP_LIMIT, exp(lnt));
-    return kCycleFinished;
-  }
+// The FP32 screen of SelectWinnerEmission over the trials of partons
+// first, first + stride, ... of an event: the best key (ties go to the
+// smallest code, i.e. the first trial in the loop order of the exact
+// selection), its error bound, the largest upper bound of every other
+// trial, and the work counts.
+struct Screen {
+  float best_key, best_m, others_hi;
+  int best_code;  // (2 i + side) * 8 + kappa, -1: no trial
+  uint32_t best_hi, best_lo;
+  int trials, dipoles;
+};
 
-  // ---- SelectWinnerEmission, FP32 screen over every trial.
-  float best_key = -INFINITY, best_m = 0.0f, others_hi = -INFINITY;
-  int best_code = -1;  // (2 i + side) * 8 + kappa
-  uint32_t best_hi = 0, best_lo = 0;
-  int trials = 0, dipoles = 0;
+__device__ __forceinline__ void screen_none(Screen& sc) {
+  sc.best_key = -INFINITY;
+  sc.best_m = 0.0f;
+  sc.others_hi = -INFINITY;
+  sc.best_code = -1;
+  sc.best_hi = sc.best_lo = 0;
+  sc.trials = sc.dipoles = 0;
+}
+
+__device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step,
+                                               int n, int first, int stride, Screen& sc) {
+  screen_none(sc);
   constexpr float kInvCF2 = static_cast<float>(1.0 / (2.0 * kCF));
   constexpr float kInvCA = static_cast<float>(1.0 / kCA);
-  for (int i = 0; i < n; ++i) {
+  for (int i = first; i < n; i += stride) {
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
     const int nk = gluon ? 1 + P.nf : 1;
     for (int side = 0; side < 2; ++side) {
       if (E.link[E.link_at(side, i, ev)] == kNoLink) continue;
       const float2 d = E.dip[dip_at(E, side, i, ev)];
       if (d.x < 0.0f) continue;
-      ++dipoles;
+      ++sc.dipoles;
       for (int kp = 0; kp < nk; kp += 2) {
         const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
                               kDrawTrial, P.seed_lo, P.seed_hi);
@@ -234,24 +238,75 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
           const float invc = !gluon ? d.x * kInvCF2 : (kappa == 0 ? d.x * kInvCA : d.y);
           const float key = lg2u * invc;
           const float m = kKeyRelInvc * invc + kKeyRelKey * fabsf(key);
-          ++trials;
-          if (key > best_key) {
-            others_hi = fmaxf(others_hi, best_key + best_m);
-            best_key = key;
-            best_m = m;
-            best_code = (2 * i + side) * 8 + kappa;
-            best_hi = whi;
-            best_lo = wlo;
+          ++sc.trials;
+          if (key > sc.best_key) {
+            sc.others_hi = fmaxf(sc.others_hi, sc.best_key + sc.best_m);
+            sc.best_key = key;
+            sc.best_m = m;
+            sc.best_code = (2 * i + side) * 8 + kappa;
+            sc.best_hi = whi;
+            sc.best_lo = wlo;
           } else {
-            others_hi = fmaxf(others_hi, key + m);
+            sc.others_hi = fmaxf(sc.others_hi, key + m);
           }
         }
       }
     }
   }
+}
+
+// Merge the screen of other trials into sc: the same result as one screen
+// over both sets in loop order (commutative and associative, so a butterfly
+// over lanes gives every lane the whole event's screen).
+__device__ __forceinline__ void screen_merge(Screen& sc, const Screen& o) {
+  const bool o_wins = o.best_code >= 0 &&
+                      (sc.best_code < 0 || o.best_key > sc.best_key ||
+                       (o.best_key == sc.best_key && o.best_code < sc.best_code));
+  const float lose = o_wins ? sc.best_key + sc.best_m : o.best_key + o.best_m;
+  sc.others_hi = fmaxf(fmaxf(sc.others_hi, o.others_hi), lose);
+  if (o_wins) {
+    sc.best_key = o.best_key;
+    sc.best_m = o.best_m;
+    sc.best_code = o.best_code;
+    sc.best_hi = o.best_hi;
+    sc.best_lo = o.best_lo;
+  }
+  sc.trials += o.trials;
+  sc.dipoles += o.dipoles;
+}
+
+// Butterfly merge of the screens of the L lanes of each aligned lane group
+// (every lane of the warp must call it).
+template <int L>
+__device__ __forceinline__ void screen_group_reduce(Screen& sc) {
+#pragma unroll
+  for (int off = 1; off < L; off <<= 1) {
+    Screen o;
+    o.best_key = __shfl_xor_sync(0xffffffffu, sc.best_key, off);
+    o.best_m = __shfl_xor_sync(0xffffffffu, sc.best_m, off);
+    o.others_hi = __shfl_xor_sync(0xffffffffu, sc.others_hi, off);
+    o.best_code = __shfl_xor_sync(0xffffffffu, sc.best_code, off);
+    o.best_hi = __shfl_xor_sync(0xffffffffu, sc.best_hi, off);
+    o.best_lo = __shfl_xor_sync(0xffffffffu, sc.best_lo, off);
+    o.trials = __shfl_xor_sync(0xffffffffu, sc.trials, off);
+    o.dipoles = __shfl_xor_sync(0xffffffffu, sc.dipoles, off);
+    screen_merge(sc, o);
+  }
+}
+
+// The rest of the cycle once the screen is known: the exact winner scale,
+// CheckCutoff, AcceptOrVeto and the decision hash.  Returns kCycleFinished
+// when the event left the active state (status written), kCycleAccepted
+// with `task` filled when an emission must be generated, kCycleVetoed
+// otherwise.
+__device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+                                   double lnt, const Screen& sc, EmitTask& task) {
+  const float best_key = sc.best_key, best_m = sc.best_m, others_hi = sc.others_hi;
+  const int best_code = sc.best_code;
+  const uint32_t best_hi = sc.best_hi, best_lo = sc.best_lo;
   E.n_steps[ev] = step + 1;
-  E.n_trials[ev] += trials;
-  E.n_dipoles[ev] += dipoles;
+  E.n_trials[ev] += sc.trials;
+  E.n_dipoles[ev] += sc.dipoles;
 
   // Cutoff threshold in key units: t' > t_C  <=>  key > log2(t_C / t).
   const float lt2 = static_cast<float>(lnt) * 1.44269504f;
@@ -352,6 +407,24 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
   task.n = n;
   task.step = step;
   return kCycleAccepted;
+}
+
+// Phase 1 of a cycle for active event ev, one thread: SelectWinnerEmission
+// (the FP32 screen over every trial), then cycle_decide.
+template <bool kMulti>
+__device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
+  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const uint32_t id = event_id(P, E, ev);
+  const int n = E.n_partons[ev];
+  const int step = E.n_steps[ev];
+  const double lnt = E.lnt[ev];
+  if (step >= P.max_steps) {
+    finish_event(E, ev, GAPS_STEP_LIMIT, exp(lnt));
+    return kCycleFinished;
+  }
+  Screen sc;
+  screen_partons(P, E, ev, id, step, n, 0, 1, sc);
+  return cycle_decide(P, E, ev, id, step, n, lnt, sc, task);
 }
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours

@@ -152,9 +152,13 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // One step of the plain form with the emissions deferred by one launch.
 // Blocks [0, select_blocks) run SelectWinnerEmission, CheckCutoff and
 // AcceptOrVeto for the events list_in[0 .. n_list) (no list: events
-// 0 .. n_list), one event per thread and without a block barrier: a vetoed
-// event goes back to list_out, an accepted one leaves its emission in
-// tasks_out, a finished one leaves.  The remaining blocks run
+// 0 .. n_list), one event per group of L lanes and without a block barrier:
+// the group's lanes screen every L-th parton's trials and merge their
+// screens exactly (the same winner and bounds as one thread's loop), its
+// first lane decides.  A vetoed event goes back to list_out, an accepted
+// one leaves its emission in tasks_out, a finished one leaves.  The host
+// widens L as the batch thins out, so the last, longest showers do not run
+// their whole trial loop in one thread.  The remaining blocks run
 // GenerateEmission for the accepted emissions of the previous launch,
 // tasks_in[0 .. n_tasks), 256 per block in full warps, refresh the dipoles
 // they moved block-wide, and put their events back in list_out.  An event
@@ -164,9 +168,9 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // n_tasks_dev) replace the host ones, which then only bound them.  The
 // launch zeroes *reset_list and *reset_tasks, the output counters of the
 // next launch.
-template <bool kMulti>
+template <bool kMulti, int L>
 __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
-    k_step_deferred(DevParams P, Events E, int64_t select_blocks, const int* list_in, int64_t n_list,
+    k_step_deferred(DevParams P0, Events E, int64_t select_blocks, const int* list_in, int64_t n_list,
                     const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                     const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                     EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
@@ -180,24 +184,43 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     if (reset_tasks) *reset_tasks = 0ull;
   }
   if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
-    const int64_t idx = static_cast<int64_t>(blockIdx.x) * kStepThreads + tid;
+    const int sub = tid & (L - 1);
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * (kStepThreads / L) + tid / L;
     const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
     int64_t ev = -1;
     if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
     const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
+    Screen sc;
+    screen_none(sc);
+    int n = 0, step = 0;
+    bool limited = false;
+    if (active) {
+      const DevParams& P = params_of<kMulti>(P0, E, ev);
+      n = E.n_partons[ev];
+      step = E.n_steps[ev];
+      limited = step >= P.max_steps;
+      if (!limited) screen_partons(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc);
+    }
+    screen_group_reduce<L>(sc);  // every lane of the warp, one call site
+    const bool lead = active && sub == 0;
     int r = kCycleFinished;
     EmitTask task;
-    if (active) {
-      r = cycle_select_veto<kMulti>(P, E, ev, task);
+    if (lead) {
+      const DevParams& P = params_of<kMulti>(P0, E, ev);
+      if (limited) {
+        finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
+      } else {
+        r = cycle_decide(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+      }
       if (r == kCycleFinished) {
         atomicAdd(&E.counters[0], 1ull);
         if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
         if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
       }
     }
-    const int64_t at_task = warp_append_slot(r == kCycleAccepted, task_count);
+    const int64_t at_task = warp_append_slot(lead && r == kCycleAccepted, task_count);
     if (at_task >= 0) tasks_out[at_task] = task;
-    const int64_t at_list = warp_append_slot(r == kCycleVetoed, list_count);
+    const int64_t at_list = warp_append_slot(lead && r == kCycleVetoed, list_count);
     if (at_list >= 0) list_out[at_list] = static_cast<int>(ev);
     return;
   }
@@ -207,9 +230,9 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   if (tid == 0) s_njobs = 0;
   if (has) s_task[tid] = tasks_in[k];
   __syncthreads();
-  if (has) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
+  if (has) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
   __syncthreads();
-  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
+  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
   const int64_t at_list = warp_append_slot(has, list_count);
   if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
 }
@@ -241,23 +264,83 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
   return cudaGetLastError();
 }
 
+namespace {
+
+template <bool kMulti, int L>
+void launch_deferred_t(unsigned grid, cudaStream_t s, const DevParams& P, const Events& E, int64_t select_blocks,
+                       const int* list_in, int64_t n_list, const unsigned long long* n_list_dev,
+                       const EmitTask* tasks_in, int64_t n_tasks, const unsigned long long* n_tasks_dev,
+                       int* list_out, unsigned long long* list_count, EmitTask* tasks_out,
+                       unsigned long long* task_count, unsigned long long* reset_list,
+                       unsigned long long* reset_tasks) {
+  k_step_deferred<kMulti, L><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
+                                                           n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
+                                                           task_count, reset_list, reset_tasks);
+}
+
+template <bool kMulti>
+void launch_deferred_l(int lanes, unsigned grid, cudaStream_t s, const DevParams& P, const Events& E,
+                       int64_t select_blocks, const int* list_in, int64_t n_list,
+                       const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
+                       const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
+                       EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
+                       unsigned long long* reset_tasks) {
+#define GAPS_DEFERRED_CASE(LN)                                                                                \
+  case LN:                                                                                                    \
+    launch_deferred_t<kMulti, LN>(grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks, \
+                                  n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list,       \
+                                  reset_tasks);                                                               \
+    break;
+  switch (lanes) {
+    GAPS_DEFERRED_CASE(1)
+    GAPS_DEFERRED_CASE(2)
+    GAPS_DEFERRED_CASE(4)
+    GAPS_DEFERRED_CASE(8)
+    GAPS_DEFERRED_CASE(16)
+    default: GAPS_DEFERRED_CASE(32)
+  }
+#undef GAPS_DEFERRED_CASE
+}
+
+// Resident threads the device runs at once (SMs x 1024), queried once per
+// device.
+int64_t resident_threads() {
+  static int64_t cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 1024;
+  if (cached[dev] == 0) {
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    cached[dev] = static_cast<int64_t>(sms) * 1024;
+  }
+  return cached[dev];
+}
+
+}  // namespace
+
+int lanes_per_event(int64_t n_list) {
+  const int64_t target = resident_threads();
+  int lanes = 1;
+  while (lanes < 32 && n_list * 2 * lanes <= target) lanes *= 2;
+  return lanes;
+}
+
 cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int* list_in, int64_t n_list,
                                  const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
                                  unsigned long long* reset_tasks, cudaStream_t s) {
-  const int64_t select_blocks = (n_list + kStepThreads - 1) / kStepThreads;
+  const int lanes = lanes_per_event(n_list);
+  const int64_t select_blocks = (n_list * lanes + kStepThreads - 1) / kStepThreads;
   const int64_t emit_blocks = (n_tasks + kStepThreads - 1) / kStepThreads;
   if (select_blocks + emit_blocks == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>(select_blocks + emit_blocks);
   if (E.jobs)
-    k_step_deferred<true><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
-                                                         n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
-                                                         task_count, reset_list, reset_tasks);
+    launch_deferred_l<true>(lanes, grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks,
+                            n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list, reset_tasks);
   else
-    k_step_deferred<false><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
-                                                          n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
-                                                          task_count, reset_list, reset_tasks);
+    launch_deferred_l<false>(lanes, grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks,
+                             n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list, reset_tasks);
   return cudaGetLastError();
 }
 
