@@ -21,65 +21,113 @@ namespace gaps {
 
 namespace {
 
+// Butterfly merge of the screens of each aligned group of `lanes` lanes
+// (block-uniform; every lane of the warp must call it).
+__device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
+  for (int off = 1; off < lanes; off <<= 1) {
+    Screen o;
+    o.best_key = __shfl_xor_sync(0xffffffffu, sc.best_key, off);
+    o.best_m = __shfl_xor_sync(0xffffffffu, sc.best_m, off);
+    o.others_hi = __shfl_xor_sync(0xffffffffu, sc.others_hi, off);
+    o.best_code = __shfl_xor_sync(0xffffffffu, sc.best_code, off);
+    o.best_hi = __shfl_xor_sync(0xffffffffu, sc.best_hi, off);
+    o.best_lo = __shfl_xor_sync(0xffffffffu, sc.best_lo, off);
+    o.trials = __shfl_xor_sync(0xffffffffu, sc.trials, off);
+    o.dipoles = __shfl_xor_sync(0xffffffffu, sc.dipoles, off);
+    screen_merge(sc, o);
+  }
+}
+
 template <int T, bool kMulti>
-__global__ void __launch_bounds__(T) k_shower_persistent(DevParams P, Events E, int period) {
+__global__ void __launch_bounds__(T) k_shower_persistent(DevParams P0, Events E, int period) {
   __shared__ int32_t s_pool[T];
+  __shared__ uint8_t s_alive[T];
   __shared__ EmitTask s_task[T];
   __shared__ uint32_t s_jobs[kMaxRefresh * T];
-  __shared__ int s_count[5];  // pool size, accepted emissions, unused, refill count, refresh jobs
+  __shared__ int s_count[6];  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   unsigned long long* cursor = &E.counters[6];
   int pool = 0;
+  if (tid == 0) s_count[5] = 0;
   for (;;) {
-    // Refill the free threads from the global cursor.
+    // Refill the free threads from the global cursor.  Once the cursor has
+    // passed the last event the pool only shrinks, and its events get
+    // several lanes each (the last, longest showers).
     if (tid == 0) {
       const int want = T - pool;
       unsigned long long base = 0;
       int take = 0;
-      if (want > 0) {
+      if (want > 0 && s_count[5] == 0) {
         base = atomicAdd(cursor, static_cast<unsigned long long>(want));
         const long long left = static_cast<long long>(E.n) - static_cast<long long>(base);
         take = left <= 0 ? 0 : (left < want ? static_cast<int>(left) : want);
+        if (take < want) s_count[5] = 1;
       }
+      int lanes = 1;
+      if (s_count[5])
+        while (lanes < 32 && (pool + take) * 2 * lanes <= T) lanes *= 2;
       s_base = base;
       s_count[3] = take;
+      s_count[2] = lanes;
     }
     __syncthreads();
     const int take = s_count[3];
     if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int32_t>(s_base + (tid - pool));
     pool += take;
+    s_alive[tid] = tid < pool ? 1 : 0;
     __syncthreads();
     if (pool == 0) break;
+    const int lanes = s_count[2];
+    const int g = tid / lanes, sub = tid - g * lanes;
 
-    bool alive = tid < pool;
     for (int c = 0; c < period; ++c) {
       if (tid == 0) {
         s_count[1] = 0;
         s_count[4] = 0;
       }
       __syncthreads();
-      if (alive) {
-        const int64_t ev = s_pool[tid];
+      const bool live = g < pool && s_alive[g];
+      const int64_t ev = live ? s_pool[g] : -1;
+      Screen sc;
+      screen_none(sc);
+      int n = 0, step = 0;
+      bool limited = false;
+      if (live) {
+        const DevParams& P = params_of<kMulti>(P0, E, ev);
+        n = E.n_partons[ev];
+        step = E.n_steps[ev];
+        limited = step >= P.max_steps;
+        if (!limited) screen_partons(P, E, ev, event_id(P, E, ev), step, n, sub, lanes, sc);
+      }
+      screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
+      if (live && sub == 0) {
+        const DevParams& P = params_of<kMulti>(P0, E, ev);
         EmitTask task;
-        const int r = cycle_select_veto<kMulti>(P, E, ev, task);
+        int r = kCycleFinished;
+        if (limited) {
+          finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
+        } else {
+          r = cycle_decide(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+        }
         if (r == kCycleAccepted) {
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
-          alive = false;
+          s_alive[g] = 0;
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
       __syncthreads();
-      if (tid < s_count[1]) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_count[4]);
+      if (tid < s_count[1]) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
       __syncthreads();
-      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
+      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
       __syncthreads();
     }
 
     // Compact: the still-active events move to the front of the pool.
+    const bool alive = tid < pool && s_alive[tid];
     const int32_t mine = alive ? s_pool[tid] : 0;
     if (tid == 0) s_count[0] = 0;
     __syncthreads();
