@@ -99,6 +99,7 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   d.as_over = d.fixed ? p.alphas_mz
                       : p.alphas_mz / (1.0 + p.alphas_mz * d.b0 * std::log(p.t_cutoff / (kMZ * kMZ)));
   d.ln_tc = std::log(p.t_cutoff);
+  d.ln_s = std::log(d.s);
   d.inv_as2pi_2cf = 1.0 / ((d.as_over / (2.0 * kPi)) * (2.0 * kCF));
   d.inv_as2pi_ca = 1.0 / ((d.as_over / (2.0 * kPi)) * kCA);
   d.tcf = static_cast<float>(p.t_cutoff);

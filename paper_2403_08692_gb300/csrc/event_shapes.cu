@@ -104,7 +104,7 @@ struct Top2 {
 template <int MAXJ>
 __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, int n) {
   const DevParams& P = params_of_event(P0, E, ev);
-  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ];
+  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ], ja[MAXJ];  // ja: |p| of every jet
   float fx[MAXJ], fy[MAXJ], fz[MAXJ];
   double sum_abs = 0.0;
   float sum_absf = 0.0f;
@@ -117,7 +117,8 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     fx[i] = static_cast<float>(jx[i]);
     fy[i] = static_cast<float>(jy[i]);
     fz[i] = static_cast<float>(jz[i]);
-    sum_abs += sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+    ja[i] = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
+    sum_abs += ja[i];
   }
   sum_absf = static_cast<float>(sum_abs);
 
@@ -216,41 +217,67 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     fz[i] *= r;
   }
   double yres[4] = {-1.0, -1.0, -1.0, -1.0};
+  // y of jets i, j with the oracle's FP64 formula (|p| cached per jet).
+  auto y_exact = [&](int i, int j) {
+    const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ja[i] * ja[j]);
+    return 2.0 * fmin(je[i] * je[i], je[j] * je[j]) * (1.0 - cosij) / P.s;
+  };
   for (int m = n; m > 1; --m) {
-    // pass 1: the smallest upper bound of the FP32 distances
+    // pass 1: the smallest upper bound of the FP32 distances, and its pair
     float ubest = INFINITY;
+    int ui = 0, uj = 1;
     for (int i = 0; i < m; ++i) {
       for (int j = i + 1; j < m; ++j) {
         const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
         const float d = dx * dx + dy * dy + dz * dz;
         const float y = fminf(fe2[i], fe2[j]) * d;
         const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
-        ubest = fminf(ubest, y * (1.0f + rel) + 1e-30f);
-      }
-    }
-    // pass 2: every pair whose lower bound reaches it, in FP64
-    double ymin = 0.0;
-    int bi = -1, bj = -1, n_exact = 0;
-    for (int i = 0; i < m; ++i) {
-      for (int j = i + 1; j < m; ++j) {
-        const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
-        const float d = dx * dx + dy * dy + dz * dz;
-        const float y = fminf(fe2[i], fe2[j]) * d;
-        const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
-        if (y * (1.0f - rel) > ubest) continue;
-        ++n_exact;
-        const double ai = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
-        const double aj = sqrt(jx[j] * jx[j] + jy[j] * jy[j] + jz[j] * jz[j]);
-        const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ai * aj);
-        const double yy = 2.0 * fmin(je[i] * je[i], je[j] * je[j]) * (1.0 - cosij) / P.s;
-        if (bi < 0 || yy < ymin) {
-          ymin = yy;
-          bi = i;
-          bj = j;
+        const float ub = y * (1.0f + rel) + 1e-30f;
+        if (ub < ubest) {
+          ubest = ub;
+          ui = i;
+          uj = j;
         }
       }
     }
-    if (n_exact > 1) atomicAdd(&E.counters[5], 1ull);  // merges with several FP64 candidates
+    // pass 2: how many pairs have a lower bound that reaches it
+    int n_cand = 0;
+    for (int i = 0; i < m; ++i) {
+      for (int j = i + 1; j < m; ++j) {
+        const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
+        const float d = dx * dx + dy * dy + dz * dz;
+        const float y = fminf(fe2[i], fe2[j]) * d;
+        const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
+        n_cand += y * (1.0f - rel) <= ubest ? 1 : 0;
+      }
+    }
+    // One candidate (nearly every merge): it is the pair of the smallest
+    // upper bound and the exact minimum, evaluated once, in step with the
+    // other lanes.  Otherwise every candidate in FP64, ties to the first
+    // pair as in the oracle.
+    double ymin = 0.0;
+    int bi = ui, bj = uj;
+    if (n_cand == 1) {
+      ymin = y_exact(ui, uj);
+    } else {
+      atomicAdd(&E.counters[5], 1ull);  // merges with several FP64 candidates
+      bi = -1;
+      for (int i = 0; i < m; ++i) {
+        for (int j = i + 1; j < m; ++j) {
+          const float dx = fx[i] - fx[j], dy = fy[i] - fy[j], dz = fz[i] - fz[j];
+          const float d = dx * dx + dy * dy + dz * dz;
+          const float y = fminf(fe2[i], fe2[j]) * d;
+          const float rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
+          if (y * (1.0f - rel) > ubest) continue;
+          const double yy = y_exact(i, j);
+          if (bi < 0 || yy < ymin) {
+            ymin = yy;
+            bi = i;
+            bj = j;
+          }
+        }
+      }
+    }
     const int idx = m - 3;
     if (idx >= 0 && idx < 4) yres[idx] = ymin;
     je[bi] += je[bj];
@@ -261,6 +288,8 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     jx[bj] = jx[m - 1];
     jy[bj] = jy[m - 1];
     jz[bj] = jz[m - 1];
+    ja[bj] = ja[m - 1];
+    ja[bi] = sqrt(jx[bi] * jx[bi] + jy[bi] * jy[bi] + jz[bi] * jz[bi]);
     fe2[bj] = fe2[m - 1];
     fx[bj] = fx[m - 1];
     fy[bj] = fy[m - 1];

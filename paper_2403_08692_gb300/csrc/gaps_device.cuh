@@ -36,6 +36,7 @@ struct DevParams {
   uint32_t seed_lo, seed_hi;
   int nf, fixed, max_steps;
   double ln_tc;                       // ln t_C
+  double ln_s;                        // ln s, the starting scale of the evolution variable
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
   // FP32 copies used by the screens
   float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
   E.weight[ev] = P.nf * 2.0 * dsigma_dcos(P.s, fl, cth);
   E.me_flavour[ev] = fl;
   E.t[ev] = P.s;  // starting scale t0 = s
-  E.lnt[ev] = log(P.s);
+  E.lnt[ev] = P.ln_s;
   E.hash[ev] = kFnvBasis;
   E.n_partons[ev] = 2;
   E.status[ev] = GAPS_ACTIVE;
