@@ -111,8 +111,9 @@ typedef struct gaps_layout {
                              1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
                              merges with several FP64 candidates; 6 the persistent form's event cursor;
-                             8, 9 the plain form's active-list lengths, 16, 17 its deferred-emission
-                             counts; 10..12 and 18..20 the same for the serving pool */
+                             7 scratch of the plain form's list rebuild; 8, 9 the plain form's
+                             active-list lengths, 16, 17 its deferred-emission counts; 10..12 and
+                             18..20 the same for the serving pool */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
@@ -134,8 +135,10 @@ typedef struct gaps_job {
   int32_t reserved;     /* must be 0 */
 } gaps_job;
 
-/* Event status values. */
-enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3 };
+/* Event status values.  GAPS_PENDING marks an active event whose accepted
+ * emission waits for the next launch of the plain form; it is seen only
+ * between the launches of a shower call, never after one returns. */
+enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3, GAPS_PENDING = 4 };
 
 /* Histograms: GAPS_N_OBS observables x GAPS_HIST_ROW bins (underflow, 100
  * bins, overflow) x (sum w, sum w^2, entries), double.  Binning: log10 y23,

@@ -398,6 +398,12 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     cnt[1] = readback[1];
     n_list = static_cast<int64_t>(readback[8 + out_half]);
     n_tasks = static_cast<int64_t>(readback[16 + out_half]);
+    // While the list is long, put it back in event order (appends scatter
+    // it); the same events, so n_list stands.
+    if (n_list > 0 && n_list * 16 >= E.n) {
+      e = launch_list_active(E, list_out, &E.counters[7], s);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (ev0) {
       float ms = 0.0f;
       e = cudaEventElapsedTime(&ms, ev0, ev1);

@@ -33,6 +33,9 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
                                  unsigned long long* reset_tasks, cudaStream_t s);
+// The active list of a batch rebuilt in event order (events with status
+// GAPS_ACTIVE); *count is a scratch counter.
+cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s);
 cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, cudaStream_t s);
 // Persistent form; counters word 6 is the event cursor and must be zero.

@@ -213,17 +213,42 @@ __device__ __forceinline__ void screen_none(Screen& sc) {
   sc.trials = sc.dipoles = 0;
 }
 
+// What the screen reads of one parton: flavour, colour partners and the
+// FP32 cache entries of its two dipoles (read whether or not a partner
+// exists; the entry is then ignored).
+struct PartonScreen {
+  int8_t flav;
+  uint8_t link0, link1;
+  float2 d0, d1;
+};
+
+__device__ __forceinline__ PartonScreen load_parton_screen(const Events& E, int64_t ev, int i) {
+  PartonScreen q;
+  q.flav = E.flav[E.at(i, ev)];
+  q.link0 = E.link[E.link_at(0, i, ev)];
+  q.link1 = E.link[E.link_at(1, i, ev)];
+  q.d0 = E.dip[dip_at(E, 0, i, ev)];
+  q.d1 = E.dip[dip_at(E, 1, i, ev)];
+  return q;
+}
+
+// The loads of the next parton are issued before the trials of the current
+// one are generated, so their latency hides behind the Philox rounds.
 __device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step,
                                                int n, int first, int stride, Screen& sc) {
   screen_none(sc);
+  if (first >= n) return;
   constexpr float kInvCF2 = static_cast<float>(1.0 / (2.0 * kCF));
   constexpr float kInvCA = static_cast<float>(1.0 / kCA);
+  PartonScreen cur = load_parton_screen(E, ev, first);
   for (int i = first; i < n; i += stride) {
-    const bool gluon = E.flav[E.at(i, ev)] == kGluon;
+    PartonScreen nxt = cur;
+    if (i + stride < n) nxt = load_parton_screen(E, ev, i + stride);
+    const bool gluon = cur.flav == kGluon;
     const int nk = gluon ? 1 + P.nf : 1;
     for (int side = 0; side < 2; ++side) {
-      if (E.link[E.link_at(side, i, ev)] == kNoLink) continue;
-      const float2 d = E.dip[dip_at(E, side, i, ev)];
+      if ((side ? cur.link1 : cur.link0) == kNoLink) continue;
+      const float2 d = side ? cur.d1 : cur.d0;
       if (d.x < 0.0f) continue;
       ++sc.dipoles;
       for (int kp = 0; kp < nk; kp += 2) {
@@ -252,6 +277,7 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
         }
       }
     }
+    cur = nxt;
   }
 }
 

@@ -219,7 +219,10 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
       }
     }
     const int64_t at_task = warp_append_slot(lead && r == kCycleAccepted, task_count);
-    if (at_task >= 0) tasks_out[at_task] = task;
+    if (at_task >= 0) {
+      tasks_out[at_task] = task;
+      E.status[ev] = GAPS_PENDING;
+    }
     const int64_t at_list = warp_append_slot(lead && r == kCycleVetoed, list_count);
     if (at_list >= 0) list_out[at_list] = static_cast<int>(ev);
     return;
@@ -233,8 +236,36 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   if (has) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
   __syncthreads();
   for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
+  if (has) E.status[s_task[tid].ev] = GAPS_ACTIVE;
   const int64_t at_list = warp_append_slot(has, list_count);
   if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
+}
+
+// The active list rebuilt in event order: the events of [0, n) with status
+// GAPS_ACTIVE (live and without a pending emission), each block's in order,
+// one atomic per block.  Appends scatter a warp's events over the batch as
+// the cycles go by; in event order a warp's events sit in one window of 256,
+// so its loads of the slot-major record coalesce again.
+__global__ void __launch_bounds__(256) k_list_active(Events E, int64_t n, int* list, unsigned long long* count) {
+  __shared__ int s_warp[8];
+  __shared__ unsigned long long s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ev = static_cast<int64_t>(blockIdx.x) * 256 + tid;
+  const bool live = ev < n && E.status[ev] == GAPS_ACTIVE;
+  const unsigned mask = __ballot_sync(0xffffffffu, live);
+  if (lane == 0) s_warp[warp] = __popc(mask);
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int w = 0; w < 8; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = run;
+      run += c;
+    }
+    s_base = run ? atomicAdd(count, static_cast<unsigned long long>(run)) : 0ull;
+  }
+  __syncthreads();
+  if (live) list[s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(ev);
 }
 
 }  // namespace
@@ -364,6 +395,14 @@ __global__ void __launch_bounds__(256) k_set_job(uint16_t* job_of, int64_t base,
 }
 
 }  // namespace
+
+cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s) {
+  if (E.n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_list_active<<<static_cast<unsigned>((E.n + 255) / 256), 256, 0, s>>>(E, E.n, list, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

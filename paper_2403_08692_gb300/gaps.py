@@ -9,7 +9,7 @@ import os
 from . import build as _build
 
 GAPS_OK, GAPS_ERR_INVALID, GAPS_ERR_CUDA, GAPS_ERR_STEP_LIMIT, GAPS_ERR_NO_DEVICE = 0, -1, -2, -3, -4
-ACTIVE, DONE, OVERFLOW, STEP_LIMIT = 0, 1, 2, 3
+ACTIVE, DONE, OVERFLOW, STEP_LIMIT, PENDING = 0, 1, 2, 3, 4
 SHOWER_PLAIN, SHOWER_PERSISTENT = 0, 1
 N_OBS, N_BINS, HIST_ROW = 6, 100, 102
 HIST_DOUBLES = N_OBS * HIST_ROW * 3
