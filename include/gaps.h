@@ -111,9 +111,9 @@ typedef struct gaps_layout {
                              1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
                              merges with several FP64 candidates; 6 the persistent form's event cursor;
-                             7 scratch of the plain form's list rebuild; 8, 9 the plain form's
-                             active-list lengths, 16, 17 its deferred-emission counts; 10..12 and
-                             18..20 the same for the serving pool */
+                             7 scratch of the plain form's list rebuild; 21..23 the plain form's
+                             active-list lengths and 24..26 its deferred-emission counts, rotating
+                             over three launches; 10..12 and 18..20 the same for the serving pool */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */

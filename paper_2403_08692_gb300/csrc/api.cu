@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "gaps_launch.hpp"
 
@@ -315,10 +316,36 @@ bool config_ok(const gaps_persistent_config& c) {
 // Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
 // persistent form's event cursor).
 cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
-  // words 0..9 and the plain form's deferred-emission counts 16, 17
+  // words 0..9 and the plain form's list and task counts
   cudaError_t e = cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + 16, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainListWord, 0, 6 * sizeof(unsigned long long), s);
   return e;
+}
+
+// Per host thread: pinned slots for the asynchronous readback of the
+// workspace counters, the events that mark each slot's copy, and the timing
+// events of gaps_shower_timed, created once and reused by every call the
+// thread makes (a few hundred bytes of page-locked host memory).
+struct HostCounters {
+  static constexpr int kSlots = 3;
+  unsigned long long* words = nullptr;
+  cudaEvent_t done[kSlots] = {};
+  std::vector<cudaEvent_t> timing;
+  bool ok = false;
+  cudaError_t err = cudaSuccess;
+  unsigned long long* slot(int k) { return words + static_cast<size_t>(k) * kCounterWords; }
+};
+
+HostCounters& host_counters() {
+  thread_local HostCounters hc;
+  if (!hc.ok) {
+    hc.err = cudaSuccess;
+    if (!hc.words) hc.err = cudaMallocHost(&hc.words, HostCounters::kSlots * kCounterWords * sizeof(unsigned long long));
+    for (int k = 0; k < HostCounters::kSlots && hc.err == cudaSuccess; ++k)
+      if (!hc.done[k]) hc.err = cudaEventCreateWithFlags(&hc.done[k], cudaEventDisableTiming);
+    hc.ok = hc.err == cudaSuccess;
+  }
+  return hc;
 }
 
 int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
@@ -328,7 +355,6 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
   if (prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   if (mode != GAPS_SHOWER_PLAIN && mode != GAPS_SHOWER_PERSISTENT) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int64_t launches = 0;
   if (launches_out) *launches_out = 0;
   if (kernel_ms_out) *kernel_ms_out = 0.0;
   if (E.n == 0) return GAPS_OK;
@@ -366,52 +392,93 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     return cnt[1] > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
   }
   // The host loop of App. C: one step for every active event per launch,
-  // then the host reads back how many events are still active.  A step
-  // runs the select/veto phase of the listed events and the splittings the
-  // previous step accepted; each launch writes its vetoed and emitted events
-  // to the other half of the active-list double buffer and its accepted
-  // emissions to the other half of the task double buffer.  An event stops
-  // after max_steps cycles and each cycle takes at most two launches, so the
-  // loop ends after at most 2 max_steps + 1 launches.
-  double total_ms = 0.0;
-  unsigned long long readback[kCounterWords] = {0};
-  int64_t n_list = E.n, n_tasks = 0;
-  while (n_list + n_tasks > 0) {
-    if (launches > 2 * static_cast<int64_t>(P.max_steps) + 1) break;
-    const int in_half = static_cast<int>(launches & 1), out_half = 1 - in_half;
-    const int* list_in = launches == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
+  // and the host checks how many events are still active.  A step runs the
+  // select/veto phase of the listed events and the splittings the previous
+  // step accepted; each launch writes its vetoed and emitted events to the
+  // other half of the active-list double buffer and its accepted emissions
+  // to the other half of the task double buffer, and reads its own input
+  // lengths on the device.  The host therefore never waits for a launch
+  // before queueing the next: it sizes the grids from a count one or two
+  // launches old (the number of live events only falls, so that count
+  // bounds them), and reads the counters back asynchronously.  An event
+  // stops after max_steps cycles and each cycle takes at most two launches,
+  // so at most 2 max_steps + 1 launches have work.
+  HostCounters& hc = host_counters();
+  if (!hc.ok) return cuda_fail(hc.err);
+  std::vector<cudaEvent_t>& tev = hc.timing;
+  int64_t bound = E.n;  // upper bound on the live events entering the next launch
+  int64_t queued = 0;   // launches queued
+  int64_t worked = 0;   // launches whose input held events
+  const int64_t max_launches = 2 * static_cast<int64_t>(P.max_steps) + 2;
+  auto enqueue = [&](int64_t c) -> cudaError_t {
+    const int in_half = static_cast<int>(c & 1), out_half = 1 - in_half;
+    const int* list_in = c == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
     int* list_out = E.active + static_cast<size_t>(out_half) * E.n;
     const EmitTask* tasks_in = E.tasks + static_cast<size_t>(in_half) * E.n;
     EmitTask* tasks_out = E.tasks + static_cast<size_t>(out_half) * E.n;
-    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return cuda_fail(e);
-    e = launch_step_deferred(P, E, list_in, n_list, nullptr, tasks_in, n_tasks, nullptr, list_out,
-                             &E.counters[8 + out_half], tasks_out, &E.counters[16 + out_half],
-                             &E.counters[8 + in_half], &E.counters[16 + in_half], s);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return cuda_fail(e);
-    ++launches;
-    e = cudaMemcpyAsync(readback, E.counters, sizeof(readback), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e);
-    cnt[0] = readback[0];
-    cnt[1] = readback[1];
-    n_list = static_cast<int64_t>(readback[8 + out_half]);
-    n_tasks = static_cast<int64_t>(readback[16 + out_half]);
-    // While the list is long, put it back in event order (appends scatter
-    // it); the same events, so n_list stands.
-    if (n_list > 0 && n_list * 16 >= E.n) {
-      e = launch_list_active(E, list_out, &E.counters[7], s);
-      if (e != cudaSuccess) return cuda_fail(e);
+    cudaError_t err = cudaSuccess;
+    if (kernel_ms_out) {
+      while (static_cast<int64_t>(tev.size()) < 2 * (c + 1)) {
+        cudaEvent_t x = nullptr;
+        if ((err = cudaEventCreate(&x)) != cudaSuccess) return err;
+        tev.push_back(x);
+      }
+      if ((err = cudaEventRecord(tev[2 * c], s)) != cudaSuccess) return err;
     }
-    if (ev0) {
+    // Counter words rotate over three launches: launch c reads its input
+    // lengths from words c%3, writes its outputs' to (c+1)%3 and clears
+    // (c+2)%3 for launch c+1 (never a word that it or a neighbour reads).
+    unsigned long long* lw = &E.counters[kPlainListWord];
+    unsigned long long* tw = &E.counters[kPlainTaskWord];
+    const int r0 = static_cast<int>(c % 3), r1 = static_cast<int>((c + 1) % 3), r2 = static_cast<int>((c + 2) % 3);
+    err = launch_step_deferred(P, E, list_in, c == 0 ? E.n : bound, c == 0 ? nullptr : lw + r0, tasks_in,
+                               c == 0 ? 0 : bound, c == 0 ? nullptr : tw + r0, list_out, lw + r1, tasks_out, tw + r1,
+                               lw + r2, tw + r2, s);
+    if (err != cudaSuccess) return err;
+    if (kernel_ms_out && (err = cudaEventRecord(tev[2 * c + 1], s)) != cudaSuccess) return err;
+    // While the list is long, put it back in event order (appends scatter
+    // it); the same events, so its length stands.
+    if (bound * 16 >= E.n && (err = launch_list_active(E, list_out, &E.counters[7], s)) != cudaSuccess) return err;
+    const int slot = static_cast<int>(c % HostCounters::kSlots);
+    err = cudaMemcpyAsync(hc.slot(slot), E.counters, kCounterWords * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaEventRecord(hc.done[slot], s);
+    return err;
+  };
+  // Counters of launch c once it has finished: the live events it leaves.
+  auto live_after = [&](int64_t c, const unsigned long long** words) -> cudaError_t {
+    const int slot = static_cast<int>(c % HostCounters::kSlots);
+    const cudaError_t err = cudaEventSynchronize(hc.done[slot]);
+    const int r1 = static_cast<int>((c + 1) % 3);
+    *words = hc.slot(slot);
+    bound = static_cast<int64_t>((*words)[kPlainListWord + r1] + (*words)[kPlainTaskWord + r1]);
+    return err;
+  };
+  const unsigned long long* words = nullptr;
+  if ((e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
+  for (int64_t c = 0;; ++c) {
+    // c: the oldest launch not yet read back; keep one more queued behind it
+    if (queued < max_launches && (e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
+    if ((e = live_after(c, &words)) != cudaSuccess) return cuda_fail(e);
+    worked = c + 1;
+    if (bound == 0 || queued >= max_launches) break;
+  }
+  // The launches queued after the last one with work have empty inputs; the
+  // counters after the last queued launch are final.
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  words = hc.slot(static_cast<int>((queued - 1) % HostCounters::kSlots));
+  cnt[0] = words[0];
+  cnt[1] = words[1];
+  double total_ms = 0.0;
+  if (kernel_ms_out) {
+    for (int64_t c = 0; c < worked; ++c) {
       float ms = 0.0f;
-      e = cudaEventElapsedTime(&ms, ev0, ev1);
-      if (e != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaEventElapsedTime(&ms, tev[2 * c], tev[2 * c + 1])) != cudaSuccess) return cuda_fail(e);
       total_ms += ms;
     }
   }
-  if (launches_out) *launches_out = launches;
+  if (launches_out) *launches_out = worked;
   if (kernel_ms_out) *kernel_ms_out = total_ms;
   return cnt[1] > 0 ? GAPS_ERR_STEP_LIMIT : GAPS_OK;
 }

@@ -54,8 +54,11 @@ struct EmitTask {
 };
 constexpr int kEmitTaskBytes = 56;
 static_assert(sizeof(EmitTask) == kEmitTaskBytes, "EmitTask layout");
-// Device counter words in the workspace.
+// Device counter words in the workspace; the plain form's active-list and
+// deferred-emission lengths rotate over three words each.
 constexpr int kCounterWords = 32;
+constexpr int kPlainListWord = 21;
+constexpr int kPlainTaskWord = 24;
 
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {

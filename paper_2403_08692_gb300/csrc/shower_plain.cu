@@ -8,6 +8,8 @@
 // registers for the whole cycle instead of making four round trips through
 // HBM.  Finished events leave at once (the paper's endShower early exit) and
 // bump the finished-event counter that the host polls between cycles.
+#include <algorithm>
+
 #include "gaps_launch.hpp"
 #include "shower_cycle.cuh"
 
@@ -169,24 +171,16 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // launch zeroes *reset_list and *reset_tasks, the output counters of the
 // next launch.
 template <bool kMulti, int L>
-__global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
-    k_step_deferred(DevParams P0, Events E, int64_t select_blocks, const int* list_in, int64_t n_list,
-                    const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
-                    const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
-                    EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                    unsigned long long* reset_tasks) {
-  __shared__ EmitTask s_task[kStepThreads];
-  __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
-  __shared__ int s_njobs;
+__device__ __forceinline__ void select_role(const DevParams& P0, const Events& E, const int* list_in, int64_t len,
+                                            int* list_out,
+                                            unsigned long long* list_count, EmitTask* tasks_out,
+                                            unsigned long long* task_count) {
   const int tid = threadIdx.x;
-  if (blockIdx.x == 0 && tid == 0) {
-    if (reset_list) *reset_list = 0ull;
-    if (reset_tasks) *reset_tasks = 0ull;
-  }
-  if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
-    const int sub = tid & (L - 1);
-    const int64_t idx = static_cast<int64_t>(blockIdx.x) * (kStepThreads / L) + tid / L;
-    const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
+  constexpr int kGroups = kStepThreads / L;
+  const int sub = tid & (L - 1);
+  // the host sizes the grid for any lanes choice: one pass
+  {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * kGroups + tid / L;
     int64_t ev = -1;
     if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
     const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
@@ -225,20 +219,55 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     }
     const int64_t at_list = warp_append_slot(lead && r == kCycleVetoed, list_count);
     if (at_list >= 0) list_out[at_list] = static_cast<int>(ev);
+  }
+}
+
+// Lanes per event for a list of len events: doubled, up to 32, while
+// len x 2 x lanes fits the device's resident threads (so len x lanes stays
+// within them).
+__host__ __device__ __forceinline__ int lanes_for(int64_t len, int64_t resident) {
+  int lanes = 1;
+  while (lanes < 32 && len * 2 * lanes <= resident) lanes *= 2;
+  return lanes;
+}
+
+template <bool kMulti, int L>
+__global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
+    k_step_deferred(DevParams P0, Events E, int64_t select_blocks, const int* list_in,
+                    int64_t n_list, const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
+                    const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
+                    EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
+                    unsigned long long* reset_tasks) {
+  __shared__ EmitTask s_task[kStepThreads];
+  __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
+  __shared__ int s_njobs;
+  const int tid = threadIdx.x;
+  if (blockIdx.x == 0 && tid == 0) {
+    if (reset_list) *reset_list = 0ull;
+    if (reset_tasks) *reset_tasks = 0ull;
+  }
+  if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
+    const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
+    select_role<kMulti, L>(P0, E, list_in, len, list_out, list_count, tasks_out, task_count);
     return;
   }
-  const int64_t k = (static_cast<int64_t>(blockIdx.x) - select_blocks) * kStepThreads + tid;
+  const int64_t emit_blocks = static_cast<int64_t>(gridDim.x) - select_blocks;
   const int64_t len = n_tasks_dev ? min(n_tasks, static_cast<int64_t>(*n_tasks_dev)) : n_tasks;
-  const bool has = k < len;
-  if (tid == 0) s_njobs = 0;
-  if (has) s_task[tid] = tasks_in[k];
-  __syncthreads();
-  if (has) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
-  __syncthreads();
-  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
-  if (has) E.status[s_task[tid].ev] = GAPS_ACTIVE;
-  const int64_t at_list = warp_append_slot(has, list_count);
-  if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
+  for (int64_t base = (static_cast<int64_t>(blockIdx.x) - select_blocks) * kStepThreads; base < len;
+       base += emit_blocks * kStepThreads) {
+    __syncthreads();  // the previous round is done with s_task and s_jobs
+    if (tid == 0) s_njobs = 0;
+    const int64_t k = base + tid;
+    const bool has = k < len;
+    if (has) s_task[tid] = tasks_in[k];
+    __syncthreads();
+    if (has) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
+    __syncthreads();
+    for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
+    if (has) E.status[s_task[tid].ev] = GAPS_ACTIVE;
+    const int64_t at_list = warp_append_slot(has, list_count);
+    if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
+  }
 }
 
 // The active list rebuilt in event order: the events of [0, n) with status
@@ -297,42 +326,6 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
 
 namespace {
 
-template <bool kMulti, int L>
-void launch_deferred_t(unsigned grid, cudaStream_t s, const DevParams& P, const Events& E, int64_t select_blocks,
-                       const int* list_in, int64_t n_list, const unsigned long long* n_list_dev,
-                       const EmitTask* tasks_in, int64_t n_tasks, const unsigned long long* n_tasks_dev,
-                       int* list_out, unsigned long long* list_count, EmitTask* tasks_out,
-                       unsigned long long* task_count, unsigned long long* reset_list,
-                       unsigned long long* reset_tasks) {
-  k_step_deferred<kMulti, L><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in,
-                                                           n_tasks, n_tasks_dev, list_out, list_count, tasks_out,
-                                                           task_count, reset_list, reset_tasks);
-}
-
-template <bool kMulti>
-void launch_deferred_l(int lanes, unsigned grid, cudaStream_t s, const DevParams& P, const Events& E,
-                       int64_t select_blocks, const int* list_in, int64_t n_list,
-                       const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
-                       const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
-                       EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                       unsigned long long* reset_tasks) {
-#define GAPS_DEFERRED_CASE(LN)                                                                                \
-  case LN:                                                                                                    \
-    launch_deferred_t<kMulti, LN>(grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks, \
-                                  n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list,       \
-                                  reset_tasks);                                                               \
-    break;
-  switch (lanes) {
-    GAPS_DEFERRED_CASE(1)
-    GAPS_DEFERRED_CASE(2)
-    GAPS_DEFERRED_CASE(4)
-    GAPS_DEFERRED_CASE(8)
-    GAPS_DEFERRED_CASE(16)
-    default: GAPS_DEFERRED_CASE(32)
-  }
-#undef GAPS_DEFERRED_CASE
-}
-
 // Resident threads the device runs at once (SMs x 1024), queried once per
 // device.
 int64_t resident_threads() {
@@ -349,29 +342,47 @@ int64_t resident_threads() {
 
 }  // namespace
 
-int lanes_per_event(int64_t n_list) {
-  const int64_t target = resident_threads();
-  int lanes = 1;
-  while (lanes < 32 && n_list * 2 * lanes <= target) lanes *= 2;
-  return lanes;
-}
-
 cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int* list_in, int64_t n_list,
                                  const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
                                  unsigned long long* reset_tasks, cudaStream_t s) {
-  const int lanes = lanes_per_event(n_list);
+  // The list length may be read on the device; n_list then bounds it, and
+  // the lanes per event follow from the bound (at most one step narrower
+  // than the exact length would give, since the bound is one or two launches
+  // old).  The select grid covers n_list x lanes threads in one pass; the
+  // emission blocks stride over the tasks, one wave at most.
+  const int64_t resident = resident_threads();
+  const int64_t resident_blocks = resident / kStepThreads;
+  const int lanes = lanes_for(n_list, resident);
   const int64_t select_blocks = (n_list * lanes + kStepThreads - 1) / kStepThreads;
-  const int64_t emit_blocks = (n_tasks + kStepThreads - 1) / kStepThreads;
+  const int64_t emit_blocks = std::min((n_tasks + kStepThreads - 1) / kStepThreads, resident_blocks);
   if (select_blocks + emit_blocks == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>(select_blocks + emit_blocks);
-  if (E.jobs)
-    launch_deferred_l<true>(lanes, grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks,
-                            n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list, reset_tasks);
-  else
-    launch_deferred_l<false>(lanes, grid, s, P, E, select_blocks, list_in, n_list, n_list_dev, tasks_in, n_tasks,
-                             n_tasks_dev, list_out, list_count, tasks_out, task_count, reset_list, reset_tasks);
+#define GAPS_DEFERRED_CASE(MULTI, LN)                                                                     \
+  case LN:                                                                                                \
+    k_step_deferred<MULTI, LN><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, \
+                                                             tasks_in, n_tasks, n_tasks_dev, list_out,         \
+                                                             list_count, tasks_out, task_count, reset_list,    \
+                                                             reset_tasks);                                     \
+    break;
+#define GAPS_DEFERRED_SWITCH(MULTI)  \
+  switch (lanes) {                   \
+    GAPS_DEFERRED_CASE(MULTI, 1)     \
+    GAPS_DEFERRED_CASE(MULTI, 2)     \
+    GAPS_DEFERRED_CASE(MULTI, 4)     \
+    GAPS_DEFERRED_CASE(MULTI, 8)     \
+    GAPS_DEFERRED_CASE(MULTI, 16)    \
+    default:                         \
+      GAPS_DEFERRED_CASE(MULTI, 32)  \
+  }
+  if (E.jobs) {
+    GAPS_DEFERRED_SWITCH(true)
+  } else {
+    GAPS_DEFERRED_SWITCH(false)
+  }
+#undef GAPS_DEFERRED_SWITCH
+#undef GAPS_DEFERRED_CASE
   return cudaGetLastError();
 }
 
