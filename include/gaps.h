@@ -158,7 +158,9 @@ typedef struct gaps_stats {
 
 /* Shower forms for gaps_shower() and gaps_run(). */
 enum {
-  GAPS_SHOWER_PLAIN = 0,     /* one launch per veto cycle over all events, host all-done check (App. C) */
+  GAPS_SHOWER_PLAIN = 0,     /* one launch per shower step over the active events, host all-done check
+                                (App. C); a step runs the select/veto phase and the splittings the
+                                previous step accepted */
   GAPS_SHOWER_PERSISTENT = 1 /* one launch; per-block event pools, compaction and refill (no host loop) */
 };
 
@@ -269,15 +271,17 @@ int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mo
  * launch runs every event to the cutoff.  Each block keeps a pool of events,
  * runs cfg->compact_period veto cycles on it, packs the still-active events
  * to the front (warp ballot) and refills the free threads from a global
- * event cursor.  Events are identical to the plain form's (same draws, same
- * cycle code).  cfg = NULL uses {256, 1, 0}.  Fully asynchronous: no host
- * synchronisation; the workspace counters record finished and step-limited
- * events. */
+ * event cursor.  Accepted emissions queue in the block and are generated
+ * together once 32 have gathered (and before every compaction); an event
+ * with a queued emission skips its selects until then.  Events are
+ * identical to the plain form's (same draws, same cycle code).  cfg = NULL
+ * uses {128, 8, 0}.  Fully asynchronous: no host synchronisation; the
+ * workspace counters record finished and step-limited events. */
 int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
                            const gaps_persistent_config* cfg, void* stream);
 
 /* Autotuner of the persistent form: times every block size in {128, 256,
- * 512} with compaction periods {1, 2, 4} on this batch (matrix element +
+ * 512} with compaction periods {2, 4, 8, 16} on this batch (matrix element +
  * shower each time, CUDA events on `stream`) and returns the fastest in
  * *best (and its time in *best_ms, may be NULL).  Overwrites the batch's
  * events.  Synchronous. */

@@ -304,7 +304,7 @@ int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch,
 
 namespace {
 
-constexpr gaps_persistent_config kDefaultPersistent = {256, 1, 0, 0};
+constexpr gaps_persistent_config kDefaultPersistent = {128, 8, 0, 0};
 
 bool config_ok(const gaps_persistent_config& c) {
   const bool threads_ok = c.block_threads == 64 || c.block_threads == 128 || c.block_threads == 256 ||
@@ -523,9 +523,9 @@ int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch,
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   double best_time = -1.0;
   const int threads[3] = {128, 256, 512};
-  const int periods[3] = {1, 2, 4};
+  const int periods[4] = {2, 4, 8, 16};
   for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
-    for (int pi = 0; pi < 3 && e == cudaSuccess; ++pi) {
+    for (int pi = 0; pi < 4 && e == cudaSuccess; ++pi) {
       const gaps_persistent_config c = {threads[ti], periods[pi], 0, 0};
       e = launch_me(P, E, s);
       if (e == cudaSuccess) e = clear_shower_counters(E, s);

@@ -38,8 +38,25 @@ __device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
   }
 }
 
+// Launch shape knobs: resident threads per SM the register budget is set for
+// (0: no bound), and the queued emissions that trigger a flush before the
+// end of a compaction period.
+#ifndef GAPS_PERSIST_THREADS_PER_SM
+#define GAPS_PERSIST_THREADS_PER_SM 1024
+#endif
+#ifndef GAPS_PERSIST_FLUSH
+#define GAPS_PERSIST_FLUSH 32
+#endif
+constexpr int persist_min_blocks(int t) {
+  return GAPS_PERSIST_THREADS_PER_SM > 0 && GAPS_PERSIST_THREADS_PER_SM / t > 0 ? GAPS_PERSIST_THREADS_PER_SM / t : 1;
+}
+
+// Slot states of a pool: dead, live, live with an emission waiting in the
+// block's queue.
+enum : uint8_t { kSlotDead = 0, kSlotLive = 1, kSlotPending = 2 };
+
 template <int T, bool kMulti>
-__global__ void __launch_bounds__(T) k_shower_persistent(DevParams P0, Events E, int period) {
+__global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(DevParams P0, Events E, int period) {
   __shared__ int32_t s_pool[T];
   __shared__ uint8_t s_alive[T];
   __shared__ EmitTask s_task[T];
@@ -75,19 +92,21 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P0, Events E,
     const int take = s_count[3];
     if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int32_t>(s_base + (tid - pool));
     pool += take;
-    s_alive[tid] = tid < pool ? 1 : 0;
+    s_alive[tid] = tid < pool ? kSlotLive : kSlotDead;
     __syncthreads();
     if (pool == 0) break;
     const int lanes = s_count[2];
     const int g = tid / lanes, sub = tid - g * lanes;
 
+    if (tid == 0) {
+      s_count[1] = 0;
+      s_count[4] = 0;
+    }
     for (int c = 0; c < period; ++c) {
-      if (tid == 0) {
-        s_count[1] = 0;
-        s_count[4] = 0;
-      }
       __syncthreads();
-      const bool live = g < pool && s_alive[g];
+      // An event whose emission waits in the queue skips its next selects
+      // until the queue is flushed (its draws are keyed by its own cycle).
+      const bool live = g < pool && s_alive[g] == kSlotLive;
       const int64_t ev = live ? s_pool[g] : -1;
       Screen sc;
       screen_none(sc);
@@ -111,23 +130,36 @@ __global__ void __launch_bounds__(T) k_shower_persistent(DevParams P0, Events E,
           r = cycle_decide(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
         }
         if (r == kCycleAccepted) {
+          task.pad0 = static_cast<uint8_t>(g & 255);  // pool slot, to release it after the emission
+          task.pad1 = static_cast<uint8_t>(g >> 8);
+          s_alive[g] = kSlotPending;
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
-          s_alive[g] = 0;
+          s_alive[g] = kSlotDead;
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
       __syncthreads();
-      if (tid < s_count[1]) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
+      // Flush the queued emissions once enough have gathered to fill warps,
+      // and always before the pool is compacted.
+      const int queued = s_count[1];
+      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && c + 1 < period)) continue;
+      if (tid < queued) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
       __syncthreads();
       for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
+      if (tid < queued) s_alive[s_task[tid].pad0 | (s_task[tid].pad1 << 8)] = kSlotLive;
       __syncthreads();
+      if (tid == 0) {
+        s_count[1] = 0;
+        s_count[4] = 0;
+      }
     }
+    __syncthreads();
 
     // Compact: the still-active events move to the front of the pool.
-    const bool alive = tid < pool && s_alive[tid];
+    const bool alive = tid < pool && s_alive[tid] == kSlotLive;
     const int32_t mine = alive ? s_pool[tid] : 0;
     if (tid == 0) s_count[0] = 0;
     __syncthreads();

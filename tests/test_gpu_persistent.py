@@ -59,7 +59,8 @@ def test_persistent_equals_plain(g):
     assert pers[4][0] == 20011 and pers[4][6] >= 20011
 
 
-@pytest.mark.parametrize("threads,period,per_sm", [(64, 1, 0), (128, 2, 0), (256, 4, 1), (512, 3, 0)])
+@pytest.mark.parametrize("threads,period,per_sm", [(64, 1, 0), (128, 2, 0), (256, 4, 1), (512, 3, 0), (128, 8, 0),
+                                                  (256, 16, 0), (512, 7, 1)])
 def test_persistent_launch_shapes(g, threads, period, per_sm):
     p = g.make_params(seed=6)
     plain = _run(g, p, 7001, persistent=False)
@@ -118,7 +119,7 @@ def test_autotuner_picks_a_valid_shape(g):
     p = g.make_params(seed=9)
     ws = g.Workspace(100000, 128)
     cfg, ms = g.autotune_persistent(p, ws)
-    assert cfg.block_threads in (128, 256, 512) and cfg.compact_period in (1, 2, 4) and ms > 0
+    assert cfg.block_threads in (128, 256, 512) and cfg.compact_period in (2, 4, 8, 16) and ms > 0
     # the tuned shape gives the same events as the plain form
     plain = _run(g, p, 20000, persistent=False)
     _assert_same(plain, _run(g, p, 20000, persistent=True, cfg=cfg.as_dict()))
