@@ -45,12 +45,13 @@ DFMA_PER_SM_PER_CLOCK = 2
 
 
 def step_kernel_traffic(event_cycles_per_launch):
-    """DRAM bytes per launch of the veto-cycle kernel: the per-event-cycle
-    traffic of the committed ncu capture times this run's event-cycles per
-    launch; None once the kernel sources differ from the captured ones."""
+    """DRAM bytes per launch of the plain-form step kernel: the per-event-cycle
+    traffic of the committed ncu capture (all step launches of one pass, the
+    deferred emissions included) times this run's event-cycles per launch;
+    None once the kernel sources differ from the captured ones."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "k_step_plain_500k.md")
+    path = os.path.join(ROOT, "profiles", "k_step_deferred_500k.md")
     try:
         text = open(path).read()
         per_unit = float(re.search(r"dram_bytes_per_event_cycle:\s*([0-9.]+)", text).group(1))
@@ -492,11 +493,11 @@ def main():
                 "d2h_bytes_per_step": 8 * g.HIST_DOUBLES + len(bytes(g.Stats())),
                 "api": "gaps_run (parameters from host, histograms and statistics back to host)"},
         "gpu_launches": int(args.steps * kernels_outside_shower(args.capacity) + launches_total),
-        "roofline": {"bound": "alu", "kernel": "k_step_plain (fused veto cycle)",
+        "roofline": {"bound": "alu", "kernel": "k_step_deferred (plain-form step: select/veto + deferred emissions)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak_tflops,
                      "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
-                     "traffic_source": "profiles/k_step_plain_500k.md: DRAM bytes per event-cycle from one ncu "
+                     "traffic_source": "profiles/k_step_deferred_500k.md: DRAM bytes per event-cycle from one ncu "
                                        "capture x this run's event-cycles per launch",
                      "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "
                                     f"x {clock_mhz:.0f} MHz (median SM clock under load) x 2 flops; "
@@ -513,7 +514,8 @@ def main():
         "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,
                                       "winners": st.sum_winners, "emissions": st.sum_emissions},
-                   "max_steps": st.max_steps, "mean_partons": st.sum_partons / max(1, st.n_events),
+                   "max_steps": st.max_steps, "event_cycles": st.sum_steps,
+                   "mean_partons": st.sum_partons / max(1, st.n_events),
                    "fp64_fallback_cycles": int(counters[2]), "fp64_vetoes": int(counters[3]),
                    "fp64_thrust_searches": int(counters[4]), "durham_multi_candidate_merges": int(counters[5])},
     }

@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
 // rho_H on [0, 0.5]; 100 bins plus underflow 0 and overflow 101), or -1 when
 // the value is undefined.  1-T and rho_H cannot be negative (Sec. 3.1): a
 // negative value is an exact zero after rounding and is binned as zero.
-__device__ __forceinline__ int hist_bin(int h, double o) {
+// The oracle's FP64 formula.
+__device__ __noinline__ int hist_bin_fp64(int h, double o) {
   double x, lo, hi;
   if (h < 4) {
     if (!(o > 0.0)) return -1;
@@ -115,48 +116,74 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
   return f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
 }
 
-// Single-job batch: block-private histograms in shared memory, then one
-// atomic merge per bin.
-__global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
-  __shared__ double sh[GAPS_HIST_DOUBLES];
-  for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x) sh[i] = 0.0;
-  __syncthreads();
-  const int64_t N = E.n;
-  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < N;
-       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
-    const double w = E.weight[ev];
-    for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const int bin = hist_bin(h, E.obs[h * E.stride + ev]);
-      if (bin < 0) continue;
-      double* cell = sh + (h * GAPS_HIST_ROW + bin) * 3;
-      atomicAdd(cell + 0, w);
-      atomicAdd(cell + 1, w * w);
-      atomicAdd(cell + 2, 1.0);
-    }
+// The same bin from an FP32 position: MUFU log2 and the FP32 conversion put
+// the position within 1e-4 bins of the FP64 one (|log10 y| <= 10 at 2e-6
+// absolute, times 25 bins per decade; 1-T and rho_H at 6e-8 relative, times
+// 200 bins per unit), so a position more than 1e-3 bins from every edge is
+// in the FP64 formula's bin; the others take the FP64 formula.
+__device__ __forceinline__ int hist_bin(int h, double o) {
+  float f;
+  if (h < 4) {
+    if (!(o > 0.0)) return -1;
+    f = (__log2f(static_cast<float>(o)) * 0.30102999566f + 4.3f) * 25.0f;
+  } else {
+    f = (o > 0.0 ? static_cast<float>(o) : 0.0f) * 200.0f;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < GAPS_HIST_DOUBLES; i += blockDim.x)
-    if (sh[i] != 0.0) atomicAdd(hist + i, sh[i]);
+  const float fr = f - floorf(f);
+  if (!(fr > 1e-3f && fr < 1.0f - 1e-3f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);
+  return f < 0.0f ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
 }
 
-// Multi-job batch: every event fills its own job's histograms (hist +
-// job * GAPS_HIST_DOUBLES) with global atomics.
-__global__ void __launch_bounds__(256) k_histograms_jobs(Events E, double* hist) {
+// Weighted fills (sum w, sum w^2, entries) of every finished valid event.
+// The lanes of a warp that fill the same cell are merged first (match on
+// the cell, the first lane sums its peers' weights from shared memory), so
+// a crowded bin costs one atomic per warp, not one per event.  Single-job
+// batch (kJobs false): block-private histograms in shared memory, merged
+// with one atomic per cell; multi-job batch: every event fills its own
+// job's histograms (hist + job * GAPS_HIST_DOUBLES) with global atomics.
+template <bool kJobs>
+__global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
+  __shared__ double sh[kJobs ? 1 : GAPS_HIST_DOUBLES];
+  __shared__ double s_w[256], s_w2[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
+  if (!kJobs) {
+    for (int i = tid; i < GAPS_HIST_DOUBLES; i += blockDim.x) sh[i] = 0.0;
+    __syncthreads();
+  }
   const int64_t N = E.n;
-  for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < N;
-       ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (E.status[ev] != GAPS_DONE || E.valid[ev] != 0) continue;
-    const double w = E.weight[ev];
-    double* base = hist + static_cast<size_t>(E.job_of[ev]) * GAPS_HIST_DOUBLES;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // every lane of a warp runs the same iterations (the match needs them all)
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + warp0; base < N; base += stride) {
+    const int64_t ev = base + lane;
+    const bool fill = ev < N && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
+    const double w = fill ? E.weight[ev] : 0.0;
+    s_w[tid] = w;
+    s_w2[tid] = w * w;
+    const int job = kJobs && fill ? static_cast<int>(E.job_of[ev]) : 0;
+    __syncwarp();
     for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const int bin = hist_bin(h, E.obs[h * E.stride + ev]);
-      if (bin < 0) continue;
-      double* cell = base + (h * GAPS_HIST_ROW + bin) * 3;
-      atomicAdd(cell + 0, w);
-      atomicAdd(cell + 1, w * w);
-      atomicAdd(cell + 2, 1.0);
+      const int bin = fill ? hist_bin(h, E.obs[h * E.stride + ev]) : -1;
+      const int cell = bin < 0 ? -1 : job * GAPS_HIST_ROW * GAPS_N_OBS + h * GAPS_HIST_ROW + bin;
+      const unsigned peers = __match_any_sync(0xffffffffu, cell);
+      if (cell >= 0 && lane == __ffs(peers) - 1) {
+        double sw = 0.0, sw2 = 0.0;
+        for (unsigned m = peers; m; m &= m - 1) {
+          const int l = __ffs(m) - 1;
+          sw += s_w[warp0 + l];
+          sw2 += s_w2[warp0 + l];
+        }
+        double* c = (kJobs ? hist : sh) + static_cast<size_t>(cell) * 3;
+        atomicAdd(c + 0, sw);
+        atomicAdd(c + 1, sw2);
+        atomicAdd(c + 2, static_cast<double>(__popc(peers)));
+      }
     }
+    __syncwarp();
+  }
+  if (!kJobs) {
+    __syncthreads();
+    for (int i = tid; i < GAPS_HIST_DOUBLES; i += blockDim.x)
+      if (sh[i] != 0.0) atomicAdd(hist + i, sh[i]);
   }
 }
 
@@ -254,9 +281,9 @@ cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s) {
   const int64_t want = (E.n + 255) / 256;
   const unsigned blocks = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
   if (E.jobs) {
-    k_histograms_jobs<<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(E, hist);
+    k_histograms<true><<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(E, hist);
   } else {
-    k_histograms<<<blocks, 256, 0, s>>>(E, hist);
+    k_histograms<false><<<blocks, 256, 0, s>>>(E, hist);
   }
   return cudaGetLastError();
 }
