@@ -283,7 +283,7 @@ def main():
 
     # FP32-screen fallbacks of the last pass (cycles redone in FP64, vetoes
     # decided in FP64)
-    counters = ws.view("counters", torch.int64, (16,)).cpu().numpy()
+    counters = ws.view("counters", torch.int64, (32,)).cpu().numpy()
     # per-event work units of one pass (identical every step)
     g.reduce_stats(ws, stats_dev, stream)
     st = g.Stats.from_buffer_copy(stats_dev.cpu().numpy().tobytes()[:len(bytes(g.Stats()))])
@@ -492,7 +492,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48,
                 "d2h_bytes_per_step": 8 * g.HIST_DOUBLES + len(bytes(g.Stats())),
                 "api": "gaps_run (parameters from host, histograms and statistics back to host)"},
-        "gpu_launches": int(args.steps * kernels_outside_shower(args.capacity) + launches_total),
+        "gpu_launches": int(args.steps * (kernels_outside_shower(args.capacity) + int(counters[27]))
+                            + launches_total),
         "roofline": {"bound": "alu", "kernel": "k_step_deferred (plain-form step: select/veto + deferred emissions)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak_tflops,

@@ -113,7 +113,8 @@ typedef struct gaps_layout {
                              merges with several FP64 candidates; 6 the persistent form's event cursor;
                              7 scratch of the plain form's list rebuild; 21..23 the plain form's
                              active-list lengths and 24..26 its deferred-emission counts, rotating
-                             over three launches; 10..12 and 18..20 the same for the serving pool */
+                             over three launches; 10..12 and 18..20 the same for the serving pool;
+                             27 the plain form's list rebuilds */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */

@@ -318,7 +318,7 @@ bool config_ok(const gaps_persistent_config& c) {
 cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
   // words 0..9 and the plain form's list and task counts
   cudaError_t e = cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainListWord, 0, 6 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainListWord, 0, 7 * sizeof(unsigned long long), s);
   return e;
 }
 

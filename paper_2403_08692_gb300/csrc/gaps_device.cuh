@@ -59,6 +59,7 @@ static_assert(sizeof(EmitTask) == kEmitTaskBytes, "EmitTask layout");
 constexpr int kCounterWords = 32;
 constexpr int kPlainListWord = 21;
 constexpr int kPlainTaskWord = 24;
+constexpr int kRebuildWord = 27;
 
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {

@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(256) k_list_active(Events E, int64_t n, int* l
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t ev = static_cast<int64_t>(blockIdx.x) * 256 + tid;
   const bool live = ev < n && E.status[ev] == GAPS_ACTIVE;
+  if (blockIdx.x == 0 && tid == 0) atomicAdd(&E.counters[kRebuildWord], 1ull);  // launches of this kernel
   const unsigned mask = __ballot_sync(0xffffffffu, live);
   if (lane == 0) s_warp[warp] = __popc(mask);
   __syncthreads();
