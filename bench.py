@@ -98,6 +98,7 @@ def parse():
                     help="length of the Poisson arrival schedule of the serving variant (0: skip it)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory of the serving pool")
     ap.add_argument("--serve-cycles-per-round", type=int, default=8)
+    ap.add_argument("--serve-mode", default="slice", choices=["slice", "steps"])
     return ap.parse_args()
 
 
@@ -414,7 +415,8 @@ def main():
         torch.cuda.empty_cache()
         arrivals = workloads.poisson_arrivals(rate_per_s=50.0, duration_s=args.serve_seconds, seed=5)
         server = g.Server(memory_budget=args.serve_budget_gb * 2**30, capacity=args.capacity,
-                          cycles_per_round=args.serve_cycles_per_round, clock="wall", device=dev)
+                          cycles_per_round=args.serve_cycles_per_round, clock="wall", device=dev,
+                          mode=args.serve_mode)
         warm = [g.ServeJob(g.make_params(seed=7), 20000, 0, 0.0)] * 4
         server.serve(warm)
         server.reset()
@@ -432,6 +434,8 @@ def main():
             "max_latency_ms": 1e3 * s["max_latency_s"], "jobs": s["jobs"], "events": s["events"], "wall_s": wall,
             "pool_events": server.pool_events, "memory_budget_gb": args.serve_budget_gb,
             "cycles_per_round": server.cycles_per_round, "peak_live_jobs": server.peak_live_jobs,
+            "mode": server.mode + (" (one persistent launch per round)" if server.mode == "slice"
+                                   else " (plain-form steps)"),
             "veto_cycles": server.launched_cycles}
         server.reset()
         sat_jobs = [g.ServeJob(j.params, j.n_events, 0, 0.0, tag=j.tag) for j in jobs

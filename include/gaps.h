@@ -114,7 +114,7 @@ typedef struct gaps_layout {
                              7 scratch of the plain form's list rebuild; 21..23 the plain form's
                              active-list lengths and 24..26 its deferred-emission counts, rotating
                              over three launches; 10..12 and 18..20 the same for the serving pool;
-                             27 the plain form's list rebuilds */
+                             27 the plain form's list rebuilds; 28 the pool slices' event cursor */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
@@ -228,6 +228,16 @@ int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begi
  * synchronisation. */
 int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
                      void* stream);
+
+/* The same advance by the persistent form (time-sliced): one launch runs
+ * every live event for up to `cycles` (1..255) more veto cycles in per-block
+ * pools (cfg as for gaps_shower_persistent, NULL for the default), and the
+ * events still active afterwards make up the next active list.  `round`
+ * numbers the slices (the `cycle` of gaps_pool_admit and
+ * gaps_pool_progress).  A pool is driven either by gaps_pool_cycles or by
+ * gaps_pool_slice.  No host synchronisation. */
+int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64_t max_active,
+                    const gaps_persistent_config* cfg, void* stream);
 
 /* Read the number of live events before step `cycle` and, if job_done_out
  * is not NULL, the finished-event count of every job slot

@@ -681,6 +681,28 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
   return GAPS_OK;
 }
 
+int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64_t max_active,
+                    const gaps_persistent_config* cfg, void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || round < 0 || cycles < 1 || cycles > 255 || max_active < 0 ||
+      max_active > pool->n_events)
+    return GAPS_ERR_INVALID;
+  const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
+  if (c.compact_period < 1 || c.reserved != 0 || c.blocks_per_sm < 0) return GAPS_ERR_INVALID;
+  if (c.block_threads != 64 && c.block_threads != 128 && c.block_threads != 256 && c.block_threads != 512)
+    return GAPS_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t in = static_cast<size_t>(round % 2) * E.stride, out = static_cast<size_t>((round + 1) % 2) * E.stride;
+  unsigned long long* out_count = &E.counters[10 + (round + 1) % 3];
+  cudaError_t e = cudaMemsetAsync(out_count, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&E.counters[kSliceCursorWord], 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess)
+    e = launch_shower_slice(P, E, c, E.active + in, max_active, &E.counters[10 + round % 3],
+                            &E.counters[kSliceCursorWord], cycles, E.active + out, out_count, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
 int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_out, uint64_t* job_done_out,
                        void* stream) {
   DevParams P;

@@ -60,6 +60,7 @@ constexpr int kCounterWords = 32;
 constexpr int kPlainListWord = 21;
 constexpr int kPlainTaskWord = 24;
 constexpr int kRebuildWord = 27;
+constexpr int kSliceCursorWord = 28;
 
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {

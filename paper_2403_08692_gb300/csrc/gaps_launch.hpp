@@ -41,6 +41,14 @@ cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, c
 // Persistent form; counters word 6 is the event cursor and must be zero.
 cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
                                      cudaStream_t s);
+// Persistent form over a list, time-sliced: every event of list_in (length
+// *n_in_dev when given, at most n_in) runs at most `cycles` (1..255) veto
+// cycles; the still-active ones go to list_out through *out_count.  *cursor
+// must be zero.
+cudaError_t launch_shower_slice(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
+                                const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
+                                unsigned long long* cursor, int cycles, int* list_out, unsigned long long* out_count,
+                                cudaStream_t s);
 cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s);
 // buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
 // scratch [n_events].

@@ -55,16 +55,34 @@ constexpr int persist_min_blocks(int t) {
 // block's queue.
 enum : uint8_t { kSlotDead = 0, kSlotLive = 1, kSlotPending = 2 };
 
-template <int T, bool kMulti>
-__global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(DevParams P0, Events E, int period) {
+// Where a launch takes its events from and how far it runs them.  Whole
+// batch (kSlice false): events 0 .. E.n - 1 to the cutoff, cursor in counter
+// word 6.  Slice (kSlice true): the events of list_in (length *n_in_dev, at
+// most n_in), each for at most `cycles` veto cycles; those still active then
+// go to list_out (one atomic per warp).
+struct SliceArgs {
+  const int* list_in;
+  const unsigned long long* n_in_dev;
+  int64_t n_in;
+  unsigned long long* cursor;
+  int cycles;
+  int* list_out;
+  unsigned long long* out_count;
+};
+
+template <int T, bool kMulti, bool kSlice>
+__global__ void __launch_bounds__(T, persist_min_blocks(T))
+    k_shower_persistent(DevParams P0, Events E, int period, SliceArgs sl) {
   __shared__ int32_t s_pool[T];
   __shared__ uint8_t s_alive[T];
+  __shared__ uint8_t s_cyc[kSlice ? T : 1];  // cycles run in this slice, per slot
   __shared__ EmitTask s_task[T];
   __shared__ uint32_t s_jobs[kMaxRefresh * T];
   __shared__ int s_count[6];  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
-  unsigned long long* cursor = &E.counters[6];
+  unsigned long long* cursor = kSlice ? sl.cursor : &E.counters[6];
+  const int64_t total = kSlice ? (sl.n_in_dev ? min(sl.n_in, static_cast<int64_t>(*sl.n_in_dev)) : sl.n_in) : E.n;
   int pool = 0;
   if (tid == 0) s_count[5] = 0;
   for (;;) {
@@ -77,7 +95,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
       int take = 0;
       if (want > 0 && s_count[5] == 0) {
         base = atomicAdd(cursor, static_cast<unsigned long long>(want));
-        const long long left = static_cast<long long>(E.n) - static_cast<long long>(base);
+        const long long left = static_cast<long long>(total) - static_cast<long long>(base);
         take = left <= 0 ? 0 : (left < want ? static_cast<int>(left) : want);
         if (take < want) s_count[5] = 1;
       }
@@ -90,7 +108,11 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
     }
     __syncthreads();
     const int take = s_count[3];
-    if (tid >= pool && tid < pool + take) s_pool[tid] = static_cast<int32_t>(s_base + (tid - pool));
+    if (tid >= pool && tid < pool + take) {
+      const int64_t k = static_cast<int64_t>(s_base) + (tid - pool);
+      s_pool[tid] = kSlice ? (sl.list_in ? sl.list_in[k] : static_cast<int32_t>(k)) : static_cast<int32_t>(k);
+      if constexpr (kSlice) s_cyc[tid] = 0;
+    }
     pool += take;
     s_alive[tid] = tid < pool ? kSlotLive : kSlotDead;
     __syncthreads();
@@ -106,7 +128,8 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
       __syncthreads();
       // An event whose emission waits in the queue skips its next selects
       // until the queue is flushed (its draws are keyed by its own cycle).
-      const bool live = g < pool && s_alive[g] == kSlotLive;
+      bool live = g < pool && s_alive[g] == kSlotLive;
+      if constexpr (kSlice) live = live && s_cyc[g] < sl.cycles;
       const int64_t ev = live ? s_pool[g] : -1;
       Screen sc;
       screen_none(sc);
@@ -121,6 +144,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
       }
       screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
       if (live && sub == 0) {
+        if constexpr (kSlice) s_cyc[g] = static_cast<uint8_t>(s_cyc[g] + 1);
         const DevParams& P = params_of<kMulti>(P0, E, ev);
         EmitTask task;
         int r = kCycleFinished;
@@ -158,9 +182,24 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
     }
     __syncthreads();
 
-    // Compact: the still-active events move to the front of the pool.
-    const bool alive = tid < pool && s_alive[tid] == kSlotLive;
+    // Compact: the still-active events move to the front of the pool; in a
+    // slice, those that have run their cycles leave for list_out.
+    bool alive = tid < pool && s_alive[tid] == kSlotLive;
     const int32_t mine = alive ? s_pool[tid] : 0;
+    uint8_t my_cyc = 0;
+    if constexpr (kSlice) {
+      my_cyc = tid < pool ? s_cyc[tid] : 0;
+      const bool done = alive && my_cyc >= sl.cycles;
+      const unsigned dmask = __ballot_sync(0xffffffffu, done);
+      if (dmask) {
+        const int lane = tid & 31, leader = __ffs(dmask) - 1;
+        unsigned long long at = 0;
+        if (lane == leader) at = atomicAdd(sl.out_count, static_cast<unsigned long long>(__popc(dmask)));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (done) sl.list_out[at + __popc(dmask & ((1u << lane) - 1u))] = mine;
+      }
+      alive = alive && !done;
+    }
     if (tid == 0) s_count[0] = 0;
     __syncthreads();
     const unsigned mask = __ballot_sync(0xffffffffu, alive);
@@ -168,26 +207,50 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T)) k_shower_persistent(
     if ((tid & 31) == 0 && mask) base = atomicAdd(&s_count[0], __popc(mask));
     base = __shfl_sync(0xffffffffu, base, 0);
     __syncthreads();
-    if (alive) s_pool[base + __popc(mask & ((1u << (tid & 31)) - 1u))] = mine;
+    if (alive) {
+      const int at = base + __popc(mask & ((1u << (tid & 31)) - 1u));
+      s_pool[at] = mine;
+      if constexpr (kSlice) s_cyc[at] = my_cyc;
+    }
     pool = s_count[0];
     __syncthreads();
   }
 }
 
-template <int T, bool kMulti>
-cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks_per_sm, cudaStream_t s) {
+template <int T, bool kMulti, bool kSlice>
+cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks_per_sm, const SliceArgs& sl,
+                     cudaStream_t s) {
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T, kMulti>, T, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T, kMulti, kSlice>, T, 0);
   if (e != cudaSuccess) return e;
   if (fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
   int64_t blocks = static_cast<int64_t>(sms) * per_sm;
-  const int64_t needed = (E.n + T - 1) / T;
+  const int64_t needed = ((kSlice ? sl.n_in : E.n) + T - 1) / T;
   if (blocks > needed) blocks = needed;
-  k_shower_persistent<T, kMulti><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period);
+  if (blocks == 0) return cudaSuccess;
+  k_shower_persistent<T, kMulti, kSlice><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period, sl);
   return cudaGetLastError();
+}
+
+template <bool kSlice>
+cudaError_t launch_shape(const DevParams& P, const Events& E, const gaps_persistent_config& cfg, const SliceArgs& sl,
+                         cudaStream_t s) {
+  const bool multi = E.jobs != nullptr;
+  const int k = cfg.compact_period, b = cfg.blocks_per_sm;
+  switch (cfg.block_threads) {
+    case 64: return multi ? launch_t<64, true, kSlice>(P, E, k, b, sl, s) : launch_t<64, false, kSlice>(P, E, k, b, sl, s);
+    case 128:
+      return multi ? launch_t<128, true, kSlice>(P, E, k, b, sl, s) : launch_t<128, false, kSlice>(P, E, k, b, sl, s);
+    case 256:
+      return multi ? launch_t<256, true, kSlice>(P, E, k, b, sl, s) : launch_t<256, false, kSlice>(P, E, k, b, sl, s);
+    case 512:
+      return multi ? launch_t<512, true, kSlice>(P, E, k, b, sl, s) : launch_t<512, false, kSlice>(P, E, k, b, sl, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -195,18 +258,18 @@ cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks
 cudaError_t launch_shower_persistent(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
                                      cudaStream_t s) {
   if (E.n == 0) return cudaSuccess;
-  const bool multi = E.jobs != nullptr;
-  switch (cfg.block_threads) {
-    case 64: return multi ? launch_t<64, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
-                          : launch_t<64, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 128: return multi ? launch_t<128, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
-                           : launch_t<128, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 256: return multi ? launch_t<256, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
-                           : launch_t<256, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    case 512: return multi ? launch_t<512, true>(P, E, cfg.compact_period, cfg.blocks_per_sm, s)
-                           : launch_t<512, false>(P, E, cfg.compact_period, cfg.blocks_per_sm, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_shape<false>(P, E, cfg, SliceArgs{}, s);
+}
+
+cudaError_t launch_shower_slice(const DevParams& P, const Events& E, const gaps_persistent_config& cfg,
+                                const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
+                                unsigned long long* cursor, int cycles, int* list_out, unsigned long long* out_count,
+                                cudaStream_t s) {
+  if (n_in == 0 || cycles < 1 || cycles > 255) return n_in == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  gaps_persistent_config c = cfg;
+  if (c.compact_period > cycles) c.compact_period = cycles;  // no slot idles past its last cycle
+  const SliceArgs sl{list_in, n_in_dev, n_in, cursor, cycles, list_out, out_count};
+  return launch_shape<true>(P, E, c, sl, s);
 }
 
 }  // namespace gaps

@@ -94,6 +94,7 @@ SIGNATURES = {
     "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
                                   C.c_void_p]),
     "gaps_pool_cycles": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, C.c_void_p]),
+    "gaps_pool_slice": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(PersistentConfig), C.c_void_p]),
     "gaps_pool_progress": (C.c_int, [_P(Batch), C.c_int64, _P(C.c_int64), C.c_void_p, C.c_void_p]),
     "gaps_pool_finish": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
@@ -283,6 +284,17 @@ def pool_admit(p, job_slot, ev_begin, n_events, first_event, ws, cycle, stream=N
 def pool_cycles(ws, first_cycle, n_cycles, max_active, stream=None):
     _check(load().gaps_pool_cycles(C.byref(_batch(ws)), int(first_cycle), int(n_cycles), int(max_active),
                                    _stream_handle(stream)), "gaps_pool_cycles")
+
+
+def pool_slice(ws, round_index, cycles, max_active, cfg=None, stream=None):
+    """gaps_pool_slice: every live event runs up to `cycles` more cycles in one
+    persistent launch.  cfg: PersistentConfig, a dict of its fields, or None."""
+    if isinstance(cfg, dict):
+        cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
+                               int(cfg.get("blocks_per_sm", 0)), 0)
+    ptr = C.byref(cfg) if cfg is not None else None
+    _check(load().gaps_pool_slice(C.byref(_batch(ws)), int(round_index), int(cycles), int(max_active), ptr,
+                                  _stream_handle(stream)), "gaps_pool_slice")
 
 
 def pool_progress(ws, cycle, job_done=None, stream=None):

@@ -5,9 +5,11 @@ event) arrive over time.  The server keeps one resident workspace, the pool,
 sized by a device-memory budget.  A job is admitted as soon as a free job
 slot and a free contiguous range of the pool can hold its events: its matrix
 elements are generated in place and its events join the live active list.
-Every veto cycle then advances the live events of all jobs at once (the
-plain event-parallel cycle of Sec. 2 over a compacted active list), so jobs
-that arrive while others shower share their launches.  A job whose events
+Each round then advances the live events of all jobs at once, so jobs that
+arrive while others shower share their launches: either one launch of the
+persistent form that runs every live event for a slice of veto cycles in
+per-block pools (mode "slice"), or a few launches of the plain form's step
+over the active list (mode "steps").  A job whose events
 have all reached the cutoff is finalised on its own range (validation,
 observables, its own histograms), its histograms go back to the host, and its
 range and slot are reused.
@@ -108,13 +110,14 @@ class Server:
     """Continuous-batching shower server over one resident pool.
 
     pool_events: pool size in events (None: from memory_budget bytes);
-    capacity: parton slots per event; cycles_per_round: veto cycles queued
-    between two progress reads; clock: "wall" (arrival times in seconds,
-    served in real time) or "rounds" (arrival times in rounds, for
-    deterministic tests)."""
+    capacity: parton slots per event; cycles_per_round: veto cycles per
+    event and round; clock: "wall" (arrival times in seconds, served in real
+    time) or "rounds" (arrival times in rounds, for deterministic tests);
+    mode: "slice" (one persistent launch per round, launch shape cfg) or
+    "steps" (cycles_per_round plain-form steps per round)."""
 
     def __init__(self, pool_events=None, capacity=128, memory_budget=None, cycles_per_round=8, clock="wall",
-                 device="cuda"):
+                 device="cuda", mode="slice", cfg=None):
         import torch
         if pool_events is None:
             if memory_budget is None:
@@ -126,7 +129,11 @@ class Server:
         self.cycles_per_round = int(cycles_per_round)
         if clock not in ("wall", "rounds"):
             raise ValueError("clock must be 'wall' or 'rounds'")
+        if mode not in ("slice", "steps"):
+            raise ValueError("mode must be 'slice' or 'steps'")
         self.clock = clock
+        self.mode = mode
+        self.cfg = cfg
         self.ws = gaps.Workspace(self.pool_events, self.capacity, device=device)
         self.stream = torch.cuda.Stream(device=device)
         self.hist = torch.zeros((gaps.MAX_JOBS, gaps.HIST_DOUBLES), dtype=torch.float64, device=device)
@@ -175,8 +182,14 @@ class Server:
     def _launch_round(self):
         torch = self._torch
         k = self.cycles_per_round
-        gaps.pool_cycles(self.ws, self.cycle, k, min(self.bound, self.pool_events), stream=self.stream)
-        self.cycle += k
+        bound = min(self.bound, self.pool_events)
+        if self.mode == "slice":
+            # self.cycle counts slices: the rotation index of the pool's lists
+            gaps.pool_slice(self.ws, self.cycle, k, bound, self.cfg, stream=self.stream)
+            self.cycle += 1
+        else:
+            gaps.pool_cycles(self.ws, self.cycle, k, bound, stream=self.stream)
+            self.cycle += k
         self.launched_cycles += k
         buf = self._progress_host[self.rounds % 2]
         with torch.cuda.stream(self.stream):

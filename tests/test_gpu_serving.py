@@ -54,10 +54,12 @@ def _assert_same_events(a, b, tag):
         assert np.array_equal(ma[c][live], mb[c][live]), (tag, c)
 
 
-def test_pool_allocator_and_slots_reuse(g):
-    """Jobs admitted at different cycles into a pool too small for all of
+@pytest.mark.parametrize("mode", ["slice", "steps"])
+def test_pool_allocator_and_slots_reuse(g, mode):
+    """Jobs admitted at different rounds into a pool too small for all of
     them at once: later jobs wait for room, ranges are reused, and each job
-    equals the same job run alone."""
+    equals the same job run alone, whether the pool advances by persistent
+    slices or by plain-form steps."""
     cap = 128
     specs = [  # (sqrt_s, t_cutoff, seed, n_events, first_event, arrival round)
         (91.2, 1.0, 11, 20000, 0, 0),
@@ -72,7 +74,7 @@ def test_pool_allocator_and_slots_reuse(g):
     for k, (rs, tc, seed, n, first, arr) in enumerate(specs):
         p = g.make_params(sqrt_s=rs, t_cutoff=tc, seed=seed)
         jobs.append(g.ServeJob(p, n, first, float(arr), tag=k))
-    srv = g.Server(pool_events=40000, capacity=cap, cycles_per_round=3, clock="rounds")
+    srv = g.Server(pool_events=40000, capacity=cap, cycles_per_round=3, clock="rounds", mode=mode)
     seen = {}
     tag_of = {}
 
@@ -99,13 +101,14 @@ def test_pool_allocator_and_slots_reuse(g):
         assert counts[4] == good and counts[5] == good
 
 
-def test_wall_clock_poisson(g):
+@pytest.mark.parametrize("mode", ["slice", "steps"])
+def test_wall_clock_poisson(g, mode):
     """Real-time Poisson arrivals: every job completes with its events all
     counted, latencies are positive, and the pool ends empty."""
     from paper_2403_08692_gb300 import workloads
     arrivals = workloads.poisson_arrivals(rate_per_s=100.0, duration_s=0.5, seed=9, n_min=1000, n_max=30000)
     jobs = [g.ServeJob(g.make_params(seed=s), n, 0, t, tag=k) for k, (t, n, s) in enumerate(arrivals)]
-    srv = g.Server(pool_events=60000, capacity=128, cycles_per_round=8, clock="wall")
+    srv = g.Server(pool_events=60000, capacity=128, cycles_per_round=8, clock="wall", mode=mode)
     results = srv.serve(jobs)
     assert len(results) == len(jobs)
     for r in results:
