@@ -91,6 +91,7 @@ int oracle_check_params(const oracle_params* p) {
   if (!(p->t_cutoff < 0.25 * p->sqrt_s * p->sqrt_s)) return -1;
   if (p->n_flavours < 1 || p->n_flavours > 5) return -1;
   if (p->capacity < 2 || p->capacity > 1024 || p->max_steps < 1) return -1;
+  if (p->trial_mode != 0 && p->trial_mode != 1) return -1;
   // The one-loop coupling must stay finite and positive down to the cutoff.
   if (!p->fixed_alphas) {
     const double b0 = (33.0 - 2.0 * p->n_flavours) / (12.0 * kPi);

@@ -27,6 +27,8 @@ MUT_KT_SIGN = 1 << 8
 MUT_Z_SWAP = 1 << 9
 MUT_HJM_LIGHT = 1 << 10
 MUT_TRIAL_RESTART = 1 << 11
+MUT_KERNEL_UNIFORM = 1 << 12
+TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE = 0, 1
 
 
 class Params(C.Structure):
@@ -41,6 +43,7 @@ class Params(C.Structure):
         ("max_steps", C.c_int32),
         ("max_emissions", C.c_int32),
         ("mutation", C.c_int32),
+        ("trial_mode", C.c_int32),
     ]
 
 
@@ -102,9 +105,10 @@ def _ip(a):
 
 
 def make_params(sqrt_s=91.2, alphas_mz=0.118, t_cutoff=1.0, seed=1, n_flavours=5, fixed_alphas=0,
-                capacity=128, max_steps=100000, max_emissions=0, mutation=0):
+                capacity=128, max_steps=100000, max_emissions=0, mutation=0, trial_mode=0):
     return Params(float(sqrt_s), float(alphas_mz), float(t_cutoff), int(seed), int(n_flavours),
-                  int(fixed_alphas), int(capacity), int(max_steps), int(max_emissions), int(mutation))
+                  int(fixed_alphas), int(capacity), int(max_steps), int(max_emissions), int(mutation),
+                  int(trial_mode))
 
 
 def check_params(p: Params) -> int:

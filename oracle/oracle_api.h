@@ -31,6 +31,9 @@ typedef struct oracle_params {
   int32_t max_steps;     /* veto cycles per event before the step-limit flag */
   int32_t max_emissions; /* stop after this many accepted emissions (0 = no limit; tests) */
   int32_t mutation;      /* planted mistakes for pin-sensitivity tests (0 = none) */
+  int32_t trial_mode;    /* 0: one trial per (dipole, kernel) (App. A listing); 1: one trial per
+                            dipole with the kernels' summed overestimate, the kernel drawn in
+                            proportion to its share (equivalent in distribution, Sec. 2) */
 } oracle_params;
 
 typedef struct oracle_event_out {
@@ -65,7 +68,8 @@ enum {
   ORACLE_MUT_KT_SIGN = 1 << 8,       /* +k_perp on both daughters */
   ORACLE_MUT_Z_SWAP = 1 << 9,        /* daughters' momentum fractions exchanged */
   ORACLE_MUT_HJM_LIGHT = 1 << 10,    /* lighter hemisphere mass */
-  ORACLE_MUT_TRIAL_RESTART = 1 << 11 /* a vetoed trial restarts from the old scale */
+  ORACLE_MUT_TRIAL_RESTART = 1 << 11,/* a vetoed trial restarts from the old scale */
+  ORACLE_MUT_KERNEL_UNIFORM = 1 << 12 /* per-dipole trials: kernel drawn uniformly, not by its share */
 };
 
 /* Histogram layout: 6 observables x (100 bins + underflow + overflow) x

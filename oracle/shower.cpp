@@ -1,5 +1,6 @@
 // Oracle: LO matrix element and the serial Sudakov veto-algorithm shower.
 // Test infrastructure only (see oracle_api.h).
+#include <algorithm>
 #include <cmath>
 
 #include "oracle_internal.hpp"
@@ -80,6 +81,11 @@ struct Winner {
   int i = -1, k = -1, side = 0, kappa = 0;
   KernelRef kernel{0, 0};
   double q2 = 0, zm = 0, zp = 0;
+  // per-dipole trials: the dipole's kernels and their overestimate integrals
+  int nk = 0;
+  KernelRef kernels[8];
+  double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double c_sum = 0;
 };
 
 }  // namespace
@@ -137,6 +143,37 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
         ++ev.n_dipoles;
         KernelRef kernels[8];
         const int nk = kernels_for(ev.partons[i].flav, p.n_flavours, kernels);
+        if (p.trial_mode == 1) {
+          // One trial for the dipole with c = sum of its kernels' c
+          // (competing exponentials: the first of independent trials is one
+          // trial with the summed rate, its kernel drawn by share).
+          double c[8], c_sum = 0.0;
+          for (int kappa = 0; kappa < nk; ++kappa) {
+            c[kappa] = as_over / (2.0 * kPi) * kernel_integral(kernels[kappa].kind, zm, zp);
+            c_sum += c[kappa];
+          }
+          const uint32_t slot = static_cast<uint32_t>((2 * i + side) * 4);
+          const double u = uniform_pair(p.seed, event_id, step, slot, kPurposeTrial).u0;
+          const double t_trial = ev.t * std::pow(u, 1.0 / c_sum);
+          ++ev.n_trials;
+          if (t_trial > t_win) {
+            t_win = t_trial;
+            w.found = true;
+            w.i = i;
+            w.k = k;
+            w.side = side;
+            w.q2 = q2;
+            w.zm = zm;
+            w.zp = zp;
+            w.nk = nk;
+            for (int kappa = 0; kappa < nk; ++kappa) {
+              w.kernels[kappa] = kernels[kappa];
+              w.c[kappa] = c[kappa];
+            }
+            w.c_sum = c_sum;
+          }
+          continue;
+        }
         for (int kappa = 0; kappa < nk; ++kappa) {
           const double c = as_over / (2.0 * kPi) * kernel_integral(kernels[kappa].kind, zm, zp);
           const uint32_t slot = static_cast<uint32_t>((2 * i + side) * 4 + kappa / 2);
@@ -171,6 +208,25 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
     const double t_old = ev.t;
     ev.t = t_win;
     ++ev.n_winners;
+    if (p.trial_mode == 1) {
+      // The winning dipole's kernel, with probability c_kappa / c_sum.
+      const double v = uniform_pair(p.seed, event_id, step, 1, kPurposeWinner).u1;
+      int kappa = w.nk - 1;
+      if (p.mutation & ORACLE_MUT_KERNEL_UNIFORM) {
+        kappa = std::min(static_cast<int>(v * w.nk), w.nk - 1);
+      } else {
+        double cum = 0.0;
+        for (int q = 0; q < w.nk; ++q) {
+          cum += w.c[q];
+          if (v * w.c_sum < cum) {
+            kappa = q;
+            break;
+          }
+        }
+      }
+      w.kappa = kappa;
+      w.kernel = w.kernels[kappa];
+    }
 
     // (4) AcceptOrVeto.
     const UniformPair rw = uniform_pair(p.seed, event_id, step, 0, kPurposeWinner);
