@@ -362,6 +362,43 @@ def main():
                                         "ms_per_step": sum(times) / args.steps}
         del graph
 
+    # The per-dipole trial mode (one trial per dipole with the summed
+    # overestimate; the same distribution, other events) on the same
+    # workload, plain and persistent forms.
+    if not args.no_variants:
+        pd = g.make_params(seed=args.seed, trial_mode=g.TRIALS_PER_DIPOLE)
+        cfg_pd, _ = g.autotune_persistent(pd, ws, stream)
+        for name, persistent in (("plain_per_dipole", False), ("persistent_per_dipole", True)):
+            def pass_pd():
+                hist_dev.zero_()
+                g.generate_me(pd, ws, stream)
+                if persistent:
+                    g.shower_persistent(pd, ws, cfg_pd, stream)
+                else:
+                    g.shower(pd, ws, g.SHOWER_PLAIN, stream)
+                g.validate(pd, ws, stream)
+                g.observables(pd, ws, stream)
+                g.histograms(pd, ws, hist_dev, stream)
+            for _ in range(3):
+                pass_pd()
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pass_pd()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            variants[name] = {"workload": f"{n} LEP events per GPU, seed {args.seed}, per-dipole trials",
+                              "value": world * n * args.steps / (sharding.job_time_ms(sum(times), dist, dev) / 1e3),
+                              "unit": UNIT, "ms_per_step": sum(times) / args.steps}
+            if persistent:
+                variants[name]["config"] = cfg_pd.as_dict()
+
     # The batched persistent form at its own paper-scale workload (10^7 LEP
     # events, seed 3): autotuned shape, the whole pass in one CUDA graph.
     if not args.no_variants and args.batched_events > 0:

@@ -60,8 +60,16 @@ typedef struct gaps_params {
   int32_t n_flavours;   /* 1..5 */
   int32_t fixed_alphas; /* 0: one-loop running alpha_s(t); 1: alpha_s fixed at alpha_s(m_Z) */
   int32_t max_steps;    /* veto cycles allowed per event (>= 1); more sets the step-limit status */
-  int32_t reserved;     /* must be 0 */
+  int32_t trial_mode;   /* GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE */
 } gaps_params;
+
+/* Trial generation (Sec. 2, App. A).  Per kernel: one trial scale for every
+ * (dipole, matching kernel), the App. A listing.  Per dipole: one trial per
+ * dipole with the sum of its kernels' overestimates, the kernel then drawn
+ * with probability proportional to its share; the same distribution with
+ * fewer trials (a gluon's six kernels need one trial, not six), but other
+ * random numbers, so other events. */
+enum { GAPS_TRIALS_PER_KERNEL = 0, GAPS_TRIALS_PER_DIPOLE = 1 };
 
 /* One batch of events inside a caller-owned device workspace.  Event j of
  * the batch has id first_event + j (the Philox counter's event word). */

@@ -96,6 +96,7 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   d.nf = p.n_flavours;
   d.fixed = p.fixed_alphas ? 1 : 0;
   d.max_steps = p.max_steps;
+  d.trial_mode = p.trial_mode;
   d.b0 = (33.0 - 2.0 * p.n_flavours) / (12.0 * kPi);
   d.as_over = d.fixed ? p.alphas_mz
                       : p.alphas_mz / (1.0 + p.alphas_mz * d.b0 * std::log(p.t_cutoff / (kMZ * kMZ)));
@@ -246,7 +247,8 @@ int gaps_check_params(const gaps_params* p) {
   if (!(p->alphas_mz > 0.0) || !std::isfinite(p->alphas_mz)) return GAPS_ERR_INVALID;
   if (!(p->t_cutoff > 0.0) || !(p->t_cutoff < 0.25 * p->sqrt_s * p->sqrt_s)) return GAPS_ERR_INVALID;
   if (p->n_flavours < 1 || p->n_flavours > 5) return GAPS_ERR_INVALID;
-  if (p->max_steps < 1 || p->reserved != 0) return GAPS_ERR_INVALID;
+  if (p->max_steps < 1) return GAPS_ERR_INVALID;
+  if (p->trial_mode != GAPS_TRIALS_PER_KERNEL && p->trial_mode != GAPS_TRIALS_PER_DIPOLE) return GAPS_ERR_INVALID;
   if (!p->fixed_alphas) {
     const double b0 = (33.0 - 2.0 * p->n_flavours) / (12.0 * kPi);
     if (!(1.0 + p->alphas_mz * b0 * std::log(p->t_cutoff / (kMZ * kMZ)) > 0.0)) return GAPS_ERR_INVALID;

@@ -27,6 +27,8 @@ constexpr uint8_t kNoLink = 255;
 
 enum : uint32_t { kDrawME = 1, kDrawTrial = 2, kDrawWinner = 3 };
 enum : int { kQtoQG = 0, kGtoGG = 1, kGtoQQ = 2 };
+// A gluon dipole's per-dipole trial won; its kernel is drawn afterwards.
+constexpr int kKindUnchosen = 7;
 
 // Parameters of one launch, derived once on the host from gaps_params.
 struct DevParams {
@@ -35,6 +37,7 @@ struct DevParams {
   double b0;                  // one-loop beta_0 = (33 - 2 n_f) / (12 pi)
   uint32_t seed_lo, seed_hi;
   int nf, fixed, max_steps;
+  int trial_mode;  // GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE
   double ln_tc;                       // ln t_C
   double ln_s;                        // ln s, the starting scale of the evolution variable
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg

@@ -121,6 +121,33 @@ __device__ __forceinline__ double inv_c_fp64(const DevParams& P, int kind, doubl
   return inv_ls * (kind == kQtoQG ? P.inv_as2pi_2cf : P.inv_as2pi_ca);
 }
 
+// 1/c of a gluon's kernels together (the per-dipole trial): c summed over
+// the kernels in their order, as the oracle sums it.
+__device__ __forceinline__ double inv_c_sum_fp64(const DevParams& P, double zp, double inv_ls) {
+  const double c_gg = 1.0 / (inv_ls * P.inv_as2pi_ca);
+  const double c_qq = (P.as_over / (2.0 * kPi)) * (0.5 * kTR) * (zp - (1.0 - zp));
+  double c = c_gg;
+  for (int f = 0; f < P.nf; ++f) c += c_qq;
+  return 1.0 / c;
+}
+
+// The kernel of a winning gluon dipole in the per-dipole mode: kappa with
+// probability c_kappa / c_sum, by the running sum against v c_sum.
+__device__ __forceinline__ int choose_kernel(const DevParams& P, double zp, double inv_ls, double v) {
+  const double c_gg = 1.0 / (inv_ls * P.inv_as2pi_ca);
+  const double c_qq = (P.as_over / (2.0 * kPi)) * (0.5 * kTR) * (zp - (1.0 - zp));
+  double c_sum = c_gg;
+  for (int f = 0; f < P.nf; ++f) c_sum += c_qq;
+  const double target = v * c_sum;
+  double cum = c_gg;
+  if (target < cum) return 0;
+  for (int q = 1; q <= P.nf; ++q) {
+    cum += c_qq;
+    if (target < cum) return q;
+  }
+  return P.nf;
+}
+
 // The full FP64 SelectWinnerEmission (every trial exact, recomputed from the
 // momenta); the fallback of the FP32 screen.  The log-space scale of trial
 // j is L + ln(r_j)/c_j; the highest above ln t_C wins, the first on ties.
@@ -131,7 +158,8 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
   bool found = false;
   for (int i = 0; i < n; ++i) {
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
-    const int nk = gluon ? 1 + P.nf : 1;
+    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const int nk = gluon && !combined ? 1 + P.nf : 1;
     const V4 pi = load_p(E, i, ev);
     for (int side = 0; side < 2; ++side) {
       const int k = E.link[E.link_at(side, i, ev)];
@@ -143,9 +171,10 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
                               kDrawTrial, P.seed_lo, P.seed_hi);
         for (int h = 0; h < 2 && kp + h < nk; ++h) {
           const int kappa = kp + h;
-          const int kind = gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG;
+          const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
           const double u = h ? to_unit(r.z, r.w) : to_unit(r.x, r.y);
-          const double lt = lnt + log(u) * inv_c_fp64(P, kind, d.zp, d.inv_ls);
+          const double inv_c = combined ? inv_c_sum_fp64(P, d.zp, d.inv_ls) : inv_c_fp64(P, kind, d.zp, d.inv_ls);
+          const double lt = lnt + log(u) * inv_c;
           if (lt > best) {
             best = lt;
             found = true;
@@ -245,12 +274,15 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
     PartonScreen nxt = cur;
     if (i + stride < n) nxt = load_parton_screen(E, ev, i + stride);
     const bool gluon = cur.flav == kGluon;
-    const int nk = gluon ? 1 + P.nf : 1;
+    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const int nk = gluon && !combined ? 1 + P.nf : 1;
     for (int side = 0; side < 2; ++side) {
       if ((side ? cur.link1 : cur.link0) == kNoLink) continue;
       const float2 d = side ? cur.d1 : cur.d0;
       if (d.x < 0.0f) continue;
       ++sc.dipoles;
+      // per-dipole trial of a gluon: 1/c of all its kernels (a few ulp)
+      const float inv_sum = combined ? 1.0f / (static_cast<float>(kCA) / d.x + static_cast<float>(P.nf) / d.y) : 0.0f;
       for (int kp = 0; kp < nk; kp += 2) {
         const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
                               kDrawTrial, P.seed_lo, P.seed_hi);
@@ -260,7 +292,7 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
           if (kappa >= nk) break;
           const uint32_t whi = h ? r.z : r.x, wlo = h ? r.w : r.y;
           const float lg2u = __log2f(unit_float(whi, wlo));
-          const float invc = !gluon ? d.x * kInvCF2 : (kappa == 0 ? d.x * kInvCA : d.y);
+          const float invc = combined ? inv_sum : (!gluon ? d.x * kInvCF2 : (kappa == 0 ? d.x * kInvCA : d.y));
           const float key = lg2u * invc;
           const float m = kKeyRelInvc * invc + kKeyRelKey * fabsf(key);
           ++sc.trials;
@@ -348,9 +380,11 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
     const int i = dcode >> 1, side = dcode & 1;
     const size_t a = dip_at(E, side, i, ev);
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
-    const int kind = gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG;
+    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
     const double zp = E.dzp[a], inv_ls = E.dinv[a];
-    const double lt = lnt + log(to_unit(best_hi, best_lo)) * inv_c_fp64(P, kind, zp, inv_ls);
+    const double inv_c = combined ? inv_c_sum_fp64(P, zp, inv_ls) : inv_c_fp64(P, kind, zp, inv_ls);
+    const double lt = lnt + log(to_unit(best_hi, best_lo)) * inv_c;
     if (lt > P.ln_tc) {
       task.lnt = lt;
       task.q2 = E.dq2[a];
@@ -376,6 +410,13 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   }
   E.lnt[ev] = task.lnt;
   E.n_winners[ev] += 1;
+  if (task.kind == kKindUnchosen) {
+    // per-dipole trial of a gluon: its kernel from the winner's second draw
+    const U4 rk = philox10(id, static_cast<uint32_t>(step), 1u, kDrawWinner, P.seed_lo, P.seed_hi);
+    const int kappa = choose_kernel(P, task.zp, task.inv_ls, to_unit(rk.z, rk.w));
+    task.kappa = static_cast<uint8_t>(kappa);
+    task.kind = static_cast<uint8_t>(kappa == 0 ? kGtoGG : kGtoQQ);
+  }
 
   // ---- AcceptOrVeto: FP32 screen of Eq. (A.8)-(A.9), FP64 near the edge.
   const U4 rw = philox10(id, static_cast<uint32_t>(step), 0u, kDrawWinner, P.seed_lo, P.seed_hi);

@@ -18,7 +18,7 @@ HIST_DOUBLES = N_OBS * HIST_ROW * 3
 class Params(C.Structure):
     _fields_ = [("sqrt_s", C.c_double), ("alphas_mz", C.c_double), ("t_cutoff", C.c_double),
                 ("seed", C.c_uint64), ("n_flavours", C.c_int32), ("fixed_alphas", C.c_int32),
-                ("max_steps", C.c_int32), ("reserved", C.c_int32)]
+                ("max_steps", C.c_int32), ("trial_mode", C.c_int32)]
 
 
 class PersistentConfig(C.Structure):
@@ -141,10 +141,13 @@ def _check(code, where, allow=()):
     return code
 
 
+TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE = 0, 1
+
+
 def make_params(sqrt_s=91.2, alphas_mz=0.118, t_cutoff=1.0, seed=1, n_flavours=5, fixed_alphas=0,
-                max_steps=100000):
+                max_steps=100000, trial_mode=TRIALS_PER_KERNEL):
     return Params(float(sqrt_s), float(alphas_mz), float(t_cutoff), int(seed), int(n_flavours),
-                  int(fixed_alphas), int(max_steps), 0)
+                  int(fixed_alphas), int(max_steps), int(trial_mode))
 
 
 def workspace_bytes(n_events, capacity):

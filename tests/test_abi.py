@@ -73,8 +73,9 @@ def test_param_checks(g):
     assert g.check_params(g.make_params(n_flavours=6)) == -1
     assert g.check_params(g.make_params(max_steps=0)) == -1
     assert g.check_params(g.make_params(t_cutoff=1e-4)) == -1
+    assert g.check_params(g.make_params(trial_mode=g.TRIALS_PER_DIPOLE)) == 0
     p = g.make_params()
-    p.reserved = 1
+    p.trial_mode = 2
     assert g.check_params(p) == -1
 
 
