@@ -300,7 +300,8 @@ int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
                            const gaps_persistent_config* cfg, void* stream);
 
 /* Autotuner of the persistent form: times every block size in {128, 256,
- * 512} with compaction periods {2, 4, 8, 16} on this batch (matrix element +
+ * 512} with compaction periods {2, 4, 8, 16} on this batch, the better of two
+ * timings each (matrix element +
  * shower each time, CUDA events on `stream`) and returns the fastest in
  * *best (and its time in *best_ms, may be NULL).  Overwrites the batch's
  * events.  Synchronous. */

@@ -529,16 +529,20 @@ int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch,
   for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
     for (int pi = 0; pi < 4 && e == cudaSuccess; ++pi) {
       const gaps_persistent_config c = {threads[ti], periods[pi], 0, 0};
-      e = launch_me(P, E, s);
-      if (e == cudaSuccess) e = clear_shower_counters(E, s);
-      if (e == cudaSuccess) e = cudaEventRecord(a, s);
-      if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
-      if (e == cudaSuccess) e = cudaEventRecord(b, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(b);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e == cudaSuccess && (best_time < 0.0 || ms < best_time)) {
-        best_time = ms;
+      float shape_ms = -1.0f;  // the better of two timings of the shape
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = launch_me(P, E, s);
+        if (e == cudaSuccess) e = clear_shower_counters(E, s);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && (shape_ms < 0.0f || ms < shape_ms)) shape_ms = ms;
+      }
+      if (e == cudaSuccess && (best_time < 0.0 || shape_ms < best_time)) {
+        best_time = shape_ms;
         *best = c;
       }
     }
