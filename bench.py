@@ -99,6 +99,9 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory of the serving pool")
     ap.add_argument("--serve-cycles-per-round", type=int, default=8)
     ap.add_argument("--serve-mode", default="slice", choices=["slice", "steps"])
+    ap.add_argument("--scan", action="store_true",
+                    help="instead of the benchmark line: events/s of the plain and persistent passes for "
+                         "1 .. 10^7 events (median and IQR of --steps passes), one JSON line per size")
     return ap.parse_args()
 
 
@@ -210,6 +213,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- size scan
+def run_scan(args, g, torch, np):
+    """Throughput against batch size (the paper's scan over N): the whole
+    pass, plain and persistent forms, median and IQR over args.steps passes
+    after args.warmup, one JSON line per size."""
+    stream = torch.cuda.current_stream()
+    p = g.make_params(seed=args.seed)
+    for n in (1, 10, 100, 1_000, 10_000, 100_000, 1_000_000, 10_000_000):
+        ws = g.Workspace(n, args.capacity)
+        hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
+        line = {"impl": "scan", "events": n, "unit": UNIT}
+        for form, mode in (("plain", g.SHOWER_PLAIN), ("persistent", g.SHOWER_PERSISTENT)):
+            def one():
+                hist.zero_()
+                g.generate_me(p, ws, stream)
+                if mode == g.SHOWER_PERSISTENT:
+                    g.shower_persistent(p, ws, None, stream)
+                else:
+                    g.shower(p, ws, mode, stream)
+                g.validate(p, ws, stream)
+                g.observables(p, ws, stream)
+                g.histograms(p, ws, hist, stream)
+            for _ in range(max(1, args.warmup)):
+                one()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            med = float(np.median(ms))
+            line[form] = {"ms_median": med, "ms_iqr": [float(np.percentile(ms, 25)), float(np.percentile(ms, 75))],
+                          "events_per_s": n / (med / 1e3)}
+        print(json.dumps(line), flush=True)
+        del ws
+        torch.cuda.empty_cache()
+
+
 # ------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -227,6 +272,10 @@ def main():
     from paper_2403_08692_gb300 import sharding
 
     torch.cuda.set_device(local_rank)
+    if args.scan:
+        g.load()
+        run_scan(args, g, torch, np)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -242,12 +291,25 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
+    STAGES = ("me", "shower", "validate", "observables", "histograms")
+
+    def step(marks=None):
+        # marks: CUDA events recorded after each stage (per-stage times)
         g.generate_me(p, ws, stream)
+        if marks:
+            marks[0].record(stream)
         rc, launches, kms = g.shower_timed(p, ws, g.SHOWER_PLAIN, stream)
+        if marks:
+            marks[1].record(stream)
         g.validate(p, ws, stream)
+        if marks:
+            marks[2].record(stream)
         g.observables(p, ws, stream)
+        if marks:
+            marks[3].record(stream)
         g.histograms(p, ws, hist_dev, stream)
+        if marks:
+            marks[4].record(stream)
         return launches, kms
 
     def barrier():
@@ -262,6 +324,7 @@ def main():
     sampler = ClockSampler(local_rank)
     sampler.start()
     step_ms, launches_total, kernel_ms_total = [], 0, 0.0
+    stage_ms = {k: [] for k in STAGES}
     barrier()
     torch.cuda.synchronize()
     for _ in range(args.steps):
@@ -269,12 +332,15 @@ def main():
         hist_dev.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in STAGES]
         e0.record(stream)
-        launches, kms = step()
-        e1.record(stream)
+        launches, kms = step(marks)
         torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        step_ms.append(e0.elapsed_time(marks[-1]))
+        prev = e0
+        for name, m in zip(STAGES, marks):
+            stage_ms[name].append(prev.elapsed_time(m))
+            prev = m
         launches_total += launches
         kernel_ms_total += kms
     torch.cuda.synchronize()
@@ -552,6 +618,9 @@ def main():
                      "fp64_probe_per_s": {k: float(f"{v:.4g}") for k, v in rates.items()},
                      "probe_dfma_tflops": 2.0 * rates["dfma"] / 1e12},
         "clocks": clocks,
+        "stages_ms": {k: {"median": float(np.median(v)), "iqr": [float(np.percentile(v, 25)),
+                                                                 float(np.percentile(v, 75))]}
+                      for k, v in stage_ms.items()},
         "variants": variants,
         "shower": {"kernel_ms_per_pass": kernel_ms_total / args.steps, "launches_per_pass": launches_per_pass,
                    "units_per_pass": {"dipoles": st.sum_dipoles, "trials": st.sum_trials,

@@ -28,7 +28,7 @@ void run_range(const oracle_params& p, uint32_t first_event, int64_t begin, int6
     generate_me(p, id, ev);
     shower(p, id, ev);
     const int valid = validate(ev.partons, p.sqrt_s);
-    double o[6] = {-1, -1, -1, -1, -1, -1};
+    double o[kNObs] = {-1, -1, -1, -1, -1, -1, -1, -1};
     if (ev.status == ORACLE_DONE) event_shapes(momenta_of(ev), s, p.mutation, o);
     if (out) {
       oracle_event_out& r = out[j];
@@ -63,7 +63,7 @@ void run_range(const oracle_params& p, uint32_t first_event, int64_t begin, int6
         dst[3 * i + 2] = ev.partons[i].acol;
       }
     }
-    if (obs) std::memcpy(obs + j * 6, o, sizeof(o));
+    if (obs) std::memcpy(obs + j * kNObs, o, sizeof(o));
     if (hist && ev.status == ORACLE_DONE) histogram_fill(hist, o, ev.weight);
   }
 }
@@ -187,7 +187,7 @@ int oracle_thrust(int n, const double* mom, int mutation, double out[4]) {
   return 0;
 }
 
-int oracle_event_shapes(int n, const double* mom, double s, int mutation, double out[6]) {
+int oracle_event_shapes(int n, const double* mom, double s, int mutation, double out[8]) {
   if (n < 2 || !mom) return -1;
   event_shapes(unpack(n, mom), s, mutation, out);
   return 0;

@@ -106,10 +106,13 @@ double thrust(const std::vector<Vec4>& moms, int mutation, Vec4* axis) {
   return len / sum_abs;
 }
 
-// out = (y23, y34, y45, y56, 1 - T, rho_H).  The heavy-jet mass splits the
-// event into hemispheres by the sign of p_i . n_T (zero goes to the "+" side)
-// and takes rho_H = max(M+^2, M-^2) / s.
-void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double out[6]) {
+// out = (y23, y34, y45, y56, 1 - T, rho_H, B_T, B_W).  The hemispheres
+// split the event by the sign of p_i . n_T (zero goes to the "+" side).  The
+// heavy-jet mass is rho_H = max(M+^2, M-^2) / s.  The jet broadenings
+// (Table 1's observable list) sum the momenta transverse to the thrust axis:
+// B_+- = sum over the hemisphere of |p_i x n_T| / (2 sum_i |p_i|),
+// B_T = B_+ + B_-, B_W = max(B_+, B_-).
+void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double out[8]) {
   durham(moms, s, mutation, out);
   Vec4 axis{};
   const double t = thrust(moms, mutation, &axis);
@@ -123,6 +126,21 @@ void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double 
   const double mp = dot(hp, hp), mm = dot(hm, hm);
   const double heavy = (mutation & ORACLE_MUT_HJM_LIGHT) ? std::min(mp, mm) : std::max(mp, mm);
   out[5] = heavy / s;
+  double sum_abs = 0.0, bp = 0.0, bm = 0.0;
+  for (const Vec4& m : moms) {
+    sum_abs += p3abs(m);
+    const double d = m.x * axis.x + m.y * axis.y + m.z * axis.z;
+    const double cx = m.y * axis.z - m.z * axis.y;
+    const double cy = m.z * axis.x - m.x * axis.z;
+    const double cz = m.x * axis.y - m.y * axis.x;
+    const double pt = (mutation & ORACLE_MUT_BROAD_DOT) ? std::fabs(d) : std::sqrt(cx * cx + cy * cy + cz * cz);
+    if (d >= 0.0) bp += pt;
+    else bm += pt;
+  }
+  bp /= 2.0 * sum_abs;
+  bm /= 2.0 * sum_abs;
+  out[6] = bp + bm;
+  out[7] = std::max(bp, bm);
 }
 
 // Validation bits: 1 momentum not conserved to 1e-10 GeV, 2 a parton off
@@ -196,8 +214,8 @@ int validate(const std::vector<Parton>& ps, double sqrt_s) {
 // (y <= 0) are not filled.  1-T and rho_H are non-negative by definition
 // (Sec. 3.1); a negative value is the rounding of an exact zero (a two-parton
 // event) and is binned as zero, so that it never depends on the sign of an
-// ulp.
-void histogram_fill(double* hist, const double obs[6], double w) {
+// ulp.  B_T and B_W are binned on [0, 0.4].
+void histogram_fill(double* hist, const double obs[8], double w) {
   for (int h = 0; h < kNObs; ++h) {
     double x, lo, hi;
     if (h < 4) {
@@ -208,7 +226,7 @@ void histogram_fill(double* hist, const double obs[6], double w) {
     } else {
       x = obs[h] > 0.0 ? obs[h] : 0.0;
       lo = 0.0;
-      hi = 0.5;
+      hi = h < 6 ? 0.5 : 0.4;
     }
     const double f = (x - lo) / (hi - lo) * kNBins;
     int bin;

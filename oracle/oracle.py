@@ -11,7 +11,7 @@ import numpy as np
 
 from . import build_oracle
 
-N_OBS = 6
+N_OBS = 8
 HIST_ROW = 102
 DONE, OVERFLOW, STEP_LIMIT = 1, 2, 3
 
@@ -28,6 +28,7 @@ MUT_Z_SWAP = 1 << 9
 MUT_HJM_LIGHT = 1 << 10
 MUT_TRIAL_RESTART = 1 << 11
 MUT_KERNEL_UNIFORM = 1 << 12
+MUT_BROAD_DOT = 1 << 13
 TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE = 0, 1
 
 
@@ -119,8 +120,8 @@ def run(p: Params, first_event: int, n_events: int, threads: int = 1, want_momen
         want_obs=True, want_hist=True):
     """Shower events first_event .. first_event+n_events-1.  Returns a dict with
     'events' (structured array), and optionally 'mom' [n, cap, 4] (E, px, py,
-    pz), 'info' [n, cap, 3] (flavour, colour, anticolour), 'obs' [n, 6] and
-    'hist' [6, 102, 3]."""
+    pz), 'info' [n, cap, 3] (flavour, colour, anticolour), 'obs' [n, 8] and
+    'hist' [8, 102, 3]."""
     n = int(n_events)
     ev = np.zeros(n, dtype=EVENT_DTYPE)
     mom = np.zeros((n, p.capacity, 4)) if want_momenta else None
@@ -210,7 +211,7 @@ def thrust(mom, mutation=0):
 
 def event_shapes(mom, s, mutation=0):
     m = np.ascontiguousarray(mom, dtype=np.float64)
-    o = np.zeros(6)
+    o = np.zeros(N_OBS)
     if lib().oracle_event_shapes(len(m), _dp(m), s, mutation, _dp(o)) != 0:
         raise ValueError("bad event-shape input")
     return o

@@ -69,19 +69,20 @@ enum {
   ORACLE_MUT_Z_SWAP = 1 << 9,        /* daughters' momentum fractions exchanged */
   ORACLE_MUT_HJM_LIGHT = 1 << 10,    /* lighter hemisphere mass */
   ORACLE_MUT_TRIAL_RESTART = 1 << 11,/* a vetoed trial restarts from the old scale */
-  ORACLE_MUT_KERNEL_UNIFORM = 1 << 12 /* per-dipole trials: kernel drawn uniformly, not by its share */
+  ORACLE_MUT_KERNEL_UNIFORM = 1 << 12,/* per-dipole trials: kernel drawn uniformly, not by its share */
+  ORACLE_MUT_BROAD_DOT = 1 << 13     /* broadening from |p . n_T| instead of |p x n_T| */
 };
 
 /* Histogram layout: 6 observables x (100 bins + underflow + overflow) x
  * (sum w, sum w^2, entries). */
-enum { ORACLE_N_OBS = 6, ORACLE_N_BINS = 100, ORACLE_HIST_ROW = 102 };
+enum { ORACLE_N_OBS = 8, ORACLE_N_BINS = 100, ORACLE_HIST_ROW = 102 };
 
 int oracle_check_params(const oracle_params* p);
 
 /* Generate, shower and analyse events first_event .. first_event+n_events-1.
  * Outputs may be NULL.  mom: [n_events][capacity][4]; info: [n_events][capacity][3]
- * (flavour, colour, anticolour); obs: [n_events][6] (y23, y34, y45, y56, 1-T,
- * rho_H; -1 where undefined); hist: [6][102][3], accumulated over the events
+ * (flavour, colour, anticolour); obs: [n_events][8] (y23, y34, y45, y56, 1-T,
+ * rho_H, B_T, B_W; -1 where undefined); hist: [8][102][3], accumulated over the events
  * that ended at the cutoff.  n_threads <= 1 runs serially. */
 int oracle_run(const oracle_params* p, uint32_t first_event, int64_t n_events, int n_threads,
                oracle_event_out* out, double* mom, int32_t* info, double* obs, double* hist);
@@ -102,7 +103,7 @@ int oracle_splitting_map(const double pij[4], const double pk[4], double z, doub
                          int mutation, double pi_out[4], double pj_out[4], double pk_out[4]);
 int oracle_durham(int n, const double* mom, double s, int mutation, double y_out[4]);
 int oracle_thrust(int n, const double* mom, int mutation, double out[4]);
-int oracle_event_shapes(int n, const double* mom, double s, int mutation, double out[6]);
+int oracle_event_shapes(int n, const double* mom, double s, int mutation, double out[8]);
 int oracle_validate(int n, const double* mom, const int32_t* info, double sqrt_s);
 
 #ifdef __cplusplus

@@ -39,7 +39,7 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev);
 // Stage 3: observables (Sec. 3.1).
 void durham(const std::vector<Vec4>& moms, double s, int mutation, double y_out[4]);
 double thrust(const std::vector<Vec4>& moms, int mutation, Vec4* axis);
-void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double out[6]);
+void event_shapes(const std::vector<Vec4>& moms, double s, int mutation, double out[8]);
 // Per-event validation bits (momentum, on-shell, colour, flavour).
 int validate(const std::vector<Parton>& partons, double sqrt_s);
 
@@ -47,6 +47,6 @@ int validate(const std::vector<Parton>& partons, double sqrt_s);
 constexpr int kNObs = ORACLE_N_OBS;
 constexpr int kNBins = ORACLE_N_BINS;
 constexpr int kRow = ORACLE_HIST_ROW;
-void histogram_fill(double* hist, const double obs[6], double w);
+void histogram_fill(double* hist, const double obs[8], double w);
 
 }  // namespace oracle

@@ -125,9 +125,52 @@ def test_three_parton_closed_forms(oracle_mod):
     assert light[5] != pytest.approx(1 - x.max(), rel=1e-6)
 
 
+def test_three_parton_broadening(oracle_mod):
+    """Three massless partons: the thrust axis lies along the hardest one, so
+    its hemisphere has no transverse momentum and the other holds two equal
+    and opposite p_T; B_T = B_W = p_T / sqrt s = sqrt((1-x1)(1-x2)(1-x3)) / x1
+    with x1 the largest x = 2E/sqrt s.  Broadening from |p . n_T| instead of
+    |p x n_T| (planted) fails."""
+    rng = np.random.default_rng(8)
+    s = 91.2 ** 2
+    for _ in range(200):
+        p = _random_event(rng, 3)
+        x = np.sort(2 * p[:, 0] / 91.2)[::-1]
+        b = math.sqrt((1 - x[0]) * (1 - x[1]) * (1 - x[2])) / x[0]
+        out = oracle_mod.event_shapes(p, s)
+        assert out[6] == pytest.approx(b, rel=1e-9, abs=1e-13)
+        assert out[7] == pytest.approx(b, rel=1e-9, abs=1e-13)
+        bad = oracle_mod.event_shapes(p, s, oracle_mod.MUT_BROAD_DOT)
+        assert bad[6] != pytest.approx(b, rel=1e-6)
+
+
+@pytest.mark.parametrize("n", [4, 6, 9])
+def test_broadening_against_enumerated_axis(oracle_mod, n):
+    """B_T and B_W from the definition about the axis of the exhaustive
+    thrust enumeration: sum |p_i x n| over each hemisphere / (2 sum |p_i|)."""
+    rng = np.random.default_rng(20 + n)
+    s = 91.2 ** 2
+    for _ in range(20):
+        p = _random_event(rng, n)
+        best, axis = -1.0, None
+        for mask in range(1 << (n - 1)):
+            sel = np.array([(mask >> i) & 1 for i in range(n)], dtype=bool)
+            v = p[sel, 1:].sum(axis=0) - p[~sel, 1:].sum(axis=0)
+            if np.linalg.norm(v) > best:
+                best, axis = np.linalg.norm(v), v / np.linalg.norm(v)
+        pt = np.linalg.norm(np.cross(p[:, 1:], axis), axis=1)
+        side = p[:, 1:] @ axis >= 0
+        denom = 2 * np.linalg.norm(p[:, 1:], axis=1).sum()
+        bp, bm = pt[side].sum() / denom, pt[~side].sum() / denom
+        out = oracle_mod.event_shapes(p, s)
+        assert out[6] == pytest.approx(bp + bm, rel=1e-9)
+        assert out[7] == pytest.approx(max(bp, bm), rel=1e-9)
+
+
 def test_two_partons(oracle_mod):
     p = np.array([[45.6, 0, 0, 45.6], [45.6, 0, 0, -45.6]])
     out = oracle_mod.event_shapes(p, 91.2 ** 2)
+    assert out[6] == 0.0 and out[7] == 0.0
     assert out[4] == 0.0 and out[5] == 0.0
     assert np.all(out[:4] == -1.0)
 
@@ -146,19 +189,20 @@ def test_rotation_invariance(oracle_mod):
 
 def test_histograms_are_the_binned_observables(oracle_mod):
     """The run's histogram equals re-binning the per-event observables with
-    the stated edges (log10 y on [-4.3, -0.3], 1-T and rho_H on [0, 0.5])."""
+    the stated edges (log10 y on [-4.3, -0.3], 1-T and rho_H on [0, 0.5],
+    B_T and B_W on [0, 0.4])."""
     p = oracle_mod.make_params(seed=6)
     r = oracle_mod.run(p, 0, 3000, threads=oracle_mod.threads_available())
     obs, ev, hist = r["obs"], r["events"], r["hist"]
     w = ev["weight"]
-    for h in range(6):
+    for h in range(oracle_mod.N_OBS):
         x = obs[:, h]
         ok = (ev["status"] == oracle_mod.DONE)
         if h < 4:
             ok &= x > 0
             v, lo, hi = np.log10(np.where(ok, x, 1.0)), -4.3, -0.3
         else:
-            v, lo, hi = np.maximum(x, 0.0), 0.0, 0.5   # non-negative by definition
+            v, lo, hi = np.maximum(x, 0.0), 0.0, (0.5 if h < 6 else 0.4)   # non-negative by definition
         f = (v - lo) / (hi - lo) * 100
         b = np.where(f < 0, 0, np.where(f >= 100, 101, 1 + np.floor(np.clip(f, 0, 99.999999)).astype(int)))
         sw = np.bincount(b[ok], weights=w[ok], minlength=102)
