@@ -109,7 +109,8 @@ typedef struct gaps_layout {
   int64_t next_colour;    /* int32  [n_events] */
   int64_t me_flavour;     /* int32  [n_events] */
   int64_t valid;          /* int32  [n_events]: validation bits, 0 = valid */
-  int64_t obs;            /* double [6][n_events]: y23, y34, y45, y56, 1-T, rho_H (-1 = undefined) */
+  int64_t obs;            /* double [GAPS_N_OBS][n_events]: y23, y34, y45, y56, 1-T, rho_H, B_T, B_W
+                             (-1 = undefined) */
   int64_t buckets;        /* int32 [769]: scratch of gaps_observables (multiplicity buckets) */
   int64_t order;          /* int32 [n_events]: scratch of gaps_observables (events by multiplicity) */
   int64_t active;         /* int32 [2][n_events]: scratch of the plain shower (active-event lists) */
@@ -151,8 +152,9 @@ enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3, G
 
 /* Histograms: GAPS_N_OBS observables x GAPS_HIST_ROW bins (underflow, 100
  * bins, overflow) x (sum w, sum w^2, entries), double.  Binning: log10 y23,
- * y34, y45, y56 on [-4.3, -0.3]; 1-T and rho_H on [0, 0.5]. */
-enum { GAPS_N_OBS = 6, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102 };
+ * y34, y45, y56 on [-4.3, -0.3]; 1-T and rho_H on [0, 0.5]; B_T and B_W on
+ * [0, 0.4]. */
+enum { GAPS_N_OBS = 8, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102 };
 #define GAPS_HIST_DOUBLES (GAPS_N_OBS * GAPS_HIST_ROW * 3)
 
 /* Totals over a batch, reduced on the device. */
@@ -317,9 +319,11 @@ int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* s
  * 16 flavour imbalance, 32 non-finite momentum.  Asynchronous. */
 int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream);
 
-/* Sec. 3.1: Durham y23..y56 (E-scheme), thrust 1-T (exact) and heavy-jet
- * mass rho_H for every event that reached the cutoff; -1 where undefined.
- * Asynchronous. */
+/* Sec. 3.1: Durham y23..y56 (E-scheme), thrust 1-T (exact), heavy-jet mass
+ * rho_H, and the total and wide jet broadenings B_T, B_W (Table 1's
+ * observable list: sum |p x n_T| / (2 sum |p|) per thrust hemisphere; B_T
+ * their sum, B_W the larger) for every event that reached the cutoff; -1
+ * where undefined.  Asynchronous. */
 int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* stream);
 
 /* Sec. 3.2 (atomic histogramming): add the batch's observables, weighted by
@@ -346,14 +350,15 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
 /* Largest batch gaps_event_shapes_noalloc accepts. */
 #define GAPS_NOALLOC_MAX_EVENTS (1 << 20)
 
-/* The observables stage of gaps_observables (Durham y23..y56, 1-T, rho_H)
+/* The observables stage of gaps_observables (Durham y23..y56, 1-T, rho_H,
+ * B_T, B_W)
  * for callers that cannot allocate device memory -- code that must stay
  * inside another framework's memory pool, plug-ins whose host forbids
  * allocation calls, or processes that hand out all device memory up front.
  * The paper has no counterpart; it is a deployment variant.  The caller
  * passes only inputs and outputs: momenta px, py, pz, e as slot-major
  * [capacity][n_events] doubles (the workspace layout), n_partons and status
- * (int32 [n_events]), and obs (double [6][n_events], written: -1 for events
+ * (int32 [n_events]), and obs (double [GAPS_N_OBS][n_events], written: -1 for events
  * whose status is not GAPS_DONE and for undefined y values).  The working
  * arrays live in one fixed device array inside the library (about 4.2 MB,
  * held by every GPU that loads the library until the process exits), so the

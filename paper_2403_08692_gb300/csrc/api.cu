@@ -59,7 +59,7 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->next_colour = take(4 * n);
   L->me_flavour = take(4 * n);
   L->valid = take(4 * n);
-  L->obs = take(8 * 6 * n);
+  L->obs = take(8 * GAPS_N_OBS * n);
   L->buckets = take(4 * 769);
   L->order = take(4 * n);
   L->active = take(8 * n);

@@ -192,19 +192,34 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     atomicAdd(&E.counters[4], 1ull);  // thrust decided by the exact FP64 search
     thrust = thrust_fp64<MAXJ>(n, jx, jy, jz, sum_abs, ax, ay, az);
   }
-  // Heavy-jet mass: hemispheres by the sign of p . n_T.
+  // Hemispheres by the sign of p . n_T: heavy-jet mass, and the jet
+  // broadenings B_+- = sum |p x n_T| / (2 sum |p|), B_T = B_+ + B_-,
+  // B_W = max(B_+, B_-).
   double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+  double bp = 0.0, bm = 0.0;
   for (int i = 0; i < n; ++i) {
-    double* h = (jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0) ? hp : hm;
+    const bool plus = jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0;
+    double* h = plus ? hp : hm;
     h[0] += je[i];
     h[1] += jx[i];
     h[2] += jy[i];
     h[3] += jz[i];
+    const double cx = jy[i] * az - jz[i] * ay, cy = jz[i] * ax - jx[i] * az, cz = jx[i] * ay - jy[i] * ax;
+    const double pt = sqrt(cx * cx + cy * cy + cz * cz);
+    if (plus) {
+      bp += pt;
+    } else {
+      bm += pt;
+    }
   }
   const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
   const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
   E.obs[4 * E.stride + ev] = 1.0 - thrust;
   E.obs[5 * E.stride + ev] = fmax(mp, mm) / P.s;
+  bp /= 2.0 * sum_abs;
+  bm /= 2.0 * sum_abs;
+  E.obs[6 * E.stride + ev] = bp + bm;
+  E.obs[7 * E.stride + ev] = fmax(bp, bm);
 
   // ---- Durham (E-scheme)
   float fe2[MAXJ];

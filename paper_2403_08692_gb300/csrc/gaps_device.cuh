@@ -78,7 +78,7 @@ struct Events {
   unsigned long long* hash;
   int32_t *n_partons, *status, *n_steps, *n_emissions, *n_winners, *n_trials, *n_dipoles, *next_colour,
       *me_flavour, *valid;
-  double* obs;  // [6][n]
+  double* obs;  // [GAPS_N_OBS][n]
   int* buckets;  // [769] scratch of the observables' multiplicity buckets
   int* order;    // [n] scratch: finished events ordered by multiplicity
   int* active;   // [2][n] scratch: the plain form's active-event lists

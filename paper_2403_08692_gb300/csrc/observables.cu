@@ -110,7 +110,7 @@ __device__ __noinline__ int hist_bin_fp64(int h, double o) {
   } else {
     x = o > 0.0 ? o : 0.0;
     lo = 0.0;
-    hi = 0.5;
+    hi = h < 6 ? 0.5 : 0.4;
   }
   const double f = (x - lo) / (hi - lo) * GAPS_N_BINS;
   return f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
@@ -127,7 +127,7 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
     if (!(o > 0.0)) return -1;
     f = (__log2f(static_cast<float>(o)) * 0.30102999566f + 4.3f) * 25.0f;
   } else {
-    f = (o > 0.0 ? static_cast<float>(o) : 0.0f) * 200.0f;
+    f = (o > 0.0 ? static_cast<float>(o) : 0.0f) * (h < 6 ? 200.0f : 250.0f);
   }
   const float fr = f - floorf(f);
   if (!(fr > 1e-3f && fr < 1.0f - 1e-3f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);

@@ -11,7 +11,7 @@ from . import build as _build
 GAPS_OK, GAPS_ERR_INVALID, GAPS_ERR_CUDA, GAPS_ERR_STEP_LIMIT, GAPS_ERR_NO_DEVICE = 0, -1, -2, -3, -4
 ACTIVE, DONE, OVERFLOW, STEP_LIMIT, PENDING = 0, 1, 2, 3, 4
 SHOWER_PLAIN, SHOWER_PERSISTENT = 0, 1
-N_OBS, N_BINS, HIST_ROW = 6, 100, 102
+N_OBS, N_BINS, HIST_ROW = 8, 100, 102
 HIST_DOUBLES = N_OBS * HIST_ROW * 3
 
 
@@ -268,7 +268,7 @@ NOALLOC_MAX_EVENTS = 1 << 20
 def event_shapes_noalloc(px, py, pz, e, n_partons, status, n_events, capacity, sqrt_s, obs, stream=None):
     """gaps_event_shapes_noalloc on caller-owned device tensors (no workspace,
     no allocation): momenta [capacity][n_events] float64, n_partons and
-    status int32 [n_events]; writes obs [6][n_events] float64."""
+    status int32 [n_events]; writes obs [N_OBS][n_events] float64."""
     ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)
     _check(load().gaps_event_shapes_noalloc(ptr(px), ptr(py), ptr(pz), ptr(e), ptr(n_partons), ptr(status),
                                             int(n_events), int(capacity), float(sqrt_s), ptr(obs),

@@ -70,7 +70,7 @@ def test_config3_persistent_graph_1e7(g, oracle_mod):
     assert same / len(ids) >= H.AGREE_MIN
     del e, obs
     orc = oracle_mod.run(op, 0, n, threads=oracle_mod.threads_available(), want_obs=False)
-    chi2, ndf = H.hist_chi2(hist.cpu().numpy().reshape(6, 102, 3), orc["hist"])
+    chi2, ndf = H.hist_chi2(hist.cpu().numpy().reshape(g.N_OBS, g.HIST_ROW, 3), orc["hist"])
     assert chi2 < 1.5, (chi2, ndf)
     # the same events on both sides: only bin-edge rounding could still differ
     assert chi2 < 0.05, (chi2, ndf)

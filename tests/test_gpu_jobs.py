@@ -41,7 +41,7 @@ def _multi(g, jobs, persistent, capacity=128):
     hist = torch.zeros(len(jobs) * g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
     g.histograms(None, ws, hist)
     torch.cuda.synchronize()
-    return ws, hist.cpu().numpy().reshape(len(jobs), 6, 102, 3)
+    return ws, hist.cpu().numpy().reshape(len(jobs), g.N_OBS, g.HIST_ROW, 3)
 
 
 def _single(g, job, capacity=128):
@@ -55,7 +55,7 @@ def _single(g, job, capacity=128):
     hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
     g.histograms(p, ws, hist)
     torch.cuda.synchronize()
-    return ws, hist.cpu().numpy().reshape(6, 102, 3)
+    return ws, hist.cpu().numpy().reshape(g.N_OBS, g.HIST_ROW, 3)
 
 
 def _slice(ws, lo, hi):

@@ -96,5 +96,5 @@ def test_per_dipole_paper_scale(g, oracle_mod):
                == sc["hash"][j])
     assert same / len(ids) >= H.AGREE_MIN
     orc = oracle_mod.run(op, 0, n, threads=oracle_mod.threads_available(), want_obs=False)
-    chi2, ndf = H.hist_chi2(host.numpy().reshape(6, 102, 3), orc["hist"])
+    chi2, ndf = H.hist_chi2(host.numpy().reshape(g.N_OBS, g.HIST_ROW, 3), orc["hist"])
     assert chi2 < 0.05, (chi2, ndf)

@@ -224,5 +224,5 @@ def test_two_parton_shapes_bin_as_zero(oracle_mod):
     assert np.all(r["events"]["n_partons"] == 2)
     obs, hist = r["obs"], r["hist"]
     assert np.all(np.abs(obs[:, 4:6]) < 1e-12)
-    for h in (4, 5):
+    for h in (4, 5, 6, 7):
         assert hist[h, 0, 2] == 0.0 and hist[h, 1, 2] == 2000.0

@@ -48,7 +48,7 @@ def test_modes_agree_in_distribution(oracle_mod, samples):
     numbers)."""
     h0, h1 = samples[0]["hist"], samples[1]["hist"]
     assert _two_sample_chi2(_multiplicity(samples[0]["events"]), _multiplicity(samples[1]["events"])) < 1.6
-    for h in range(6):
+    for h in range(oracle_mod.N_OBS):
         assert _two_sample_chi2(h0[h, :, 2], h1[h, :, 2]) < 1.6, h
     # mean emissions per event within 4 sigma
     e0 = samples[0]["events"]["n_emissions"].astype(float)
