@@ -63,12 +63,14 @@ typedef struct gaps_params {
   int32_t trial_mode;   /* GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE */
 } gaps_params;
 
-/* Trial generation (Sec. 2, App. A).  Per kernel: one trial scale for every
- * (dipole, matching kernel), the App. A listing.  Per dipole: one trial per
- * dipole with the sum of its kernels' overestimates, the kernel then drawn
- * with probability proportional to its share; the same distribution with
- * fewer trials (a gluon's six kernels need one trial, not six), but other
- * random numbers, so other events. */
+/* Trial generation (App. A).  Per kernel: one trial scale for every
+ * (dipole, matching kernel), as App. A generates them.  Per dipole: one
+ * trial per dipole with the sum of its kernels' overestimates, the kernel
+ * then drawn with probability proportional to its share.  The first of
+ * independent exponential trials is distributed as one trial with the
+ * summed rate whose kind has probability rate / sum, so this is the same
+ * distribution with fewer trials (a gluon's six kernels need one trial, not
+ * six), but other random numbers, so other events. */
 enum { GAPS_TRIALS_PER_KERNEL = 0, GAPS_TRIALS_PER_DIPOLE = 1 };
 
 /* One batch of events inside a caller-owned device workspace.  Event j of

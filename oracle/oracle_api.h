@@ -33,7 +33,9 @@ typedef struct oracle_params {
   int32_t mutation;      /* planted mistakes for pin-sensitivity tests (0 = none) */
   int32_t trial_mode;    /* 0: one trial per (dipole, kernel) (App. A listing); 1: one trial per
                             dipole with the kernels' summed overestimate, the kernel drawn in
-                            proportion to its share (equivalent in distribution, Sec. 2) */
+                            proportion to its share: the same distribution, since the first of
+                            independent exponential trials is one trial with the summed rate whose
+                            kind has probability rate / sum (App. A generates one per kind) */
 } oracle_params;
 
 typedef struct oracle_event_out {

@@ -1,9 +1,11 @@
 """Pins of the oracle's per-dipole trial mode (trial_mode 1): one trial per
 dipole with the summed overestimate of its kernels, the kernel drawn in
-proportion to its share.  Sec. 2 states that this is equivalent in
-distribution to one trial per (dipole, kernel); these tests check that
-equivalence on the full shower, the exact Sudakov factor of the first
-emission, and that a planted uniform kernel choice is caught."""
+proportion to its share.  App. A generates one trial per (dipole, kernel);
+the first of independent exponential trials is distributed as one trial
+with the summed rate whose kind has probability rate / sum, so both modes
+give the same distribution.  These tests check that equivalence on the full
+shower, the exact Sudakov factor of the first emission, and that a planted
+uniform kernel choice is caught."""
 import numpy as np
 import pytest
 
