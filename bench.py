@@ -99,6 +99,9 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory of the serving pool")
     ap.add_argument("--serve-cycles-per-round", type=int, default=8)
     ap.add_argument("--serve-mode", default="slice", choices=["slice", "steps"])
+    ap.add_argument("--early-stop", action="store_true",
+                    help="instead of the benchmark line: the early-termination trade-off, pass time against "
+                         "the bias of the histograms when the shower stops after k veto cycles")
     ap.add_argument("--scan", action="store_true",
                     help="instead of the benchmark line: events/s of the plain and persistent passes for "
                          "1 .. 10^7 events (median and IQR of --steps passes), one JSON line per size")
@@ -255,6 +258,65 @@ def run_scan(args, g, torch, np):
         torch.cuda.empty_cache()
 
 
+# ------------------------------------------------------------ early stop
+def hist_chi2(h1, h2):
+    """chi^2/ndf between two weighted histograms [obs][bin][3] (summed
+    variances, bins empty in both skipped)."""
+    import numpy as np
+    w1, v1, w2, v2 = h1[:, :, 0], h1[:, :, 1], h2[:, :, 0], h2[:, :, 1]
+    m = (v1 + v2) > 0
+    return float(np.sum((w1[m] - w2[m]) ** 2 / (v1[m] + v2[m])) / max(1, m.sum())), int(m.sum())
+
+
+def run_early_stop(args, g, torch, np):
+    """Early termination (a measured trade-off, never the default): the plain
+    form with the veto cycles capped at k, so events still showering after k
+    cycles stop with the step-limit status and are left out of the
+    histograms.  Per k: the pass time, the events left out, and the bias of
+    the histograms against the full run's, as chi^2/ndf and per observable
+    as the relative change of the mean."""
+    stream = torch.cuda.current_stream()
+    n = args.events
+    ws = g.Workspace(n, args.capacity)
+    hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
+    centres = np.zeros((g.N_OBS, g.HIST_ROW))
+
+    def one(p):
+        hist.zero_()
+        g.generate_me(p, ws, stream)
+        g.shower(p, ws, g.SHOWER_PLAIN, stream)
+        g.validate(p, ws, stream)
+        g.observables(p, ws, stream)
+        g.histograms(p, ws, hist, stream)
+
+    def timed(p):
+        for _ in range(2):
+            one(p)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one(p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)), hist.cpu().numpy().reshape(g.N_OBS, g.HIST_ROW, 3).copy()
+
+    full_ms, full = timed(g.make_params(seed=args.seed))
+    means_full = (full[:, :, 0] * np.arange(g.HIST_ROW)).sum(axis=1) / np.maximum(full[:, :, 0].sum(axis=1), 1e-300)
+    for k in (100000, 80, 60, 50, 40, 35, 30, 25):
+        ms, h = timed(g.make_params(seed=args.seed, max_steps=k))
+        status = ws.scalars()["status"].cpu().numpy()
+        chi2, ndf = hist_chi2(h, full)
+        means = (h[:, :, 0] * np.arange(g.HIST_ROW)).sum(axis=1) / np.maximum(h[:, :, 0].sum(axis=1), 1e-300)
+        print(json.dumps({"impl": "early_stop", "events": n, "max_cycles": k, "ms_median": ms,
+                          "time_saved": 1.0 - ms / full_ms, "events_stopped": int((status == g.STEP_LIMIT).sum()),
+                          "chi2_per_ndf_vs_full": chi2, "ndf": ndf,
+                          "mean_bin_shift": [float(x) for x in (means - means_full)]}), flush=True)
+
+
 # ------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -275,6 +337,10 @@ def main():
     if args.scan:
         g.load()
         run_scan(args, g, torch, np)
+        return
+    if args.early_stop:
+        g.load()
+        run_early_stop(args, g, torch, np)
         return
     dist = None
     if world > 1:
