@@ -47,6 +47,11 @@ __device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
 #ifndef GAPS_PERSIST_FLUSH
 #define GAPS_PERSIST_FLUSH 32
 #endif
+// A pool is compacted early once 1/GAPS_PERSIST_DEAD_DIV of it has finished
+// (0: only every compaction period).
+#ifndef GAPS_PERSIST_DEAD_DIV
+#define GAPS_PERSIST_DEAD_DIV 8
+#endif
 constexpr int persist_min_blocks(int t) {
   return GAPS_PERSIST_THREADS_PER_SM > 0 && GAPS_PERSIST_THREADS_PER_SM / t > 0 ? GAPS_PERSIST_THREADS_PER_SM / t : 1;
 }
@@ -78,7 +83,8 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
   __shared__ uint8_t s_cyc[kSlice ? T : 1];  // cycles run in this slice, per slot
   __shared__ EmitTask s_task[T];
   __shared__ uint32_t s_jobs[kMaxRefresh * T];
-  __shared__ int s_count[6];  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail
+  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail, finished since compaction
+  __shared__ int s_count[7];
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   unsigned long long* cursor = kSlice ? sl.cursor : &E.counters[6];
@@ -123,6 +129,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     if (tid == 0) {
       s_count[1] = 0;
       s_count[4] = 0;
+      s_count[6] = 0;
     }
     for (int c = 0; c < period; ++c) {
       __syncthreads();
@@ -160,16 +167,24 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
           s_alive[g] = kSlotDead;
+          atomicAdd(&s_count[6], 1);
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
       __syncthreads();
-      // Flush the queued emissions once enough have gathered to fill warps,
-      // and always before the pool is compacted.
+      // Compact at the end of the period, or earlier once enough of the pool
+      // has finished (its lanes idle until then).  Flush the queued
+      // emissions once enough have gathered to fill warps, and always before
+      // the pool is compacted.
+      const bool compact_now =
+          c + 1 == period || (GAPS_PERSIST_DEAD_DIV > 0 && s_count[6] * GAPS_PERSIST_DEAD_DIV >= pool);
       const int queued = s_count[1];
-      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && c + 1 < period)) continue;
+      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && !compact_now)) {
+        if (compact_now) break;
+        continue;
+      }
       if (tid < queued) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
       __syncthreads();
       for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
@@ -179,6 +194,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
         s_count[1] = 0;
         s_count[4] = 0;
       }
+      if (compact_now) break;
     }
     __syncthreads();
 
