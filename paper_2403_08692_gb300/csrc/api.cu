@@ -329,7 +329,7 @@ cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
 // events of gaps_shower_timed, created once and reused by every call the
 // thread makes (a few hundred bytes of page-locked host memory).
 struct HostCounters {
-  static constexpr int kSlots = 3;
+  static constexpr int kSlots = 8;
   unsigned long long* words = nullptr;
   cudaEvent_t done[kSlots] = {};
   std::vector<cudaEvent_t> timing;
@@ -349,6 +349,13 @@ HostCounters& host_counters() {
   }
   return hc;
 }
+
+// Launches the plain form's host loop queues ahead of the one it reads back.
+#ifndef GAPS_PLAIN_LOOKAHEAD
+#define GAPS_PLAIN_LOOKAHEAD 1
+#endif
+constexpr int64_t kLookahead = GAPS_PLAIN_LOOKAHEAD;
+static_assert(kLookahead >= 1 && kLookahead + 2 <= 8, "lookahead and readback slots");
 
 int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                 double* kernel_ms_out, void* stream) {
@@ -459,8 +466,10 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
   const unsigned long long* words = nullptr;
   if ((e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
   for (int64_t c = 0;; ++c) {
-    // c: the oldest launch not yet read back; keep one more queued behind it
-    if (queued < max_launches && (e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
+    // c: the oldest launch not yet read back; keep kLookahead more queued
+    // behind it, so the GPU has work while the host reads counts back
+    while (queued < max_launches && queued <= c + kLookahead)
+      if ((e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
     if ((e = live_after(c, &words)) != cudaSuccess) return cuda_fail(e);
     worked = c + 1;
     if (bound == 0 || queued >= max_launches) break;
