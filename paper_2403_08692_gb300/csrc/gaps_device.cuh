@@ -116,6 +116,24 @@ __device__ __forceinline__ const DevParams& params_of(const DevParams& launch, c
   }
 }
 
+// Compile-time policy of the shower kernels: a single job with one trial per
+// (dipole, kernel), a single job with one trial per dipole, or a multi-job
+// batch (parameters and trial mode read per event).  Single-job kernels then
+// carry no code of the mode they do not run.
+enum : int { kModeSingleKernel = 0, kModeSingleDipole = 1, kModeMulti = 2 };
+template <int kMode>
+__device__ __forceinline__ bool per_dipole(const DevParams& P) {
+  if constexpr (kMode == kModeMulti) {
+    return P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+  } else {
+    return kMode == kModeSingleDipole;
+  }
+}
+// The mode of a launch.
+inline int launch_mode(const DevParams& P, const Events& E) {
+  return E.jobs ? kModeMulti : (P.trial_mode == GAPS_TRIALS_PER_DIPOLE ? kModeSingleDipole : kModeSingleKernel);
+}
+
 // The same choice at run time, for kernels that read the parameters once per
 // event.
 __device__ __forceinline__ const DevParams& params_of_event(const DevParams& launch, const Events& E, int64_t ev) {

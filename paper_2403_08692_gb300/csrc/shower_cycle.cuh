@@ -152,13 +152,14 @@ __device__ __forceinline__ int choose_kernel(const DevParams& P, double zp, doub
 // momenta); the fallback of the FP32 screen.  The log-space scale of trial
 // j is L + ln(r_j)/c_j; the highest above ln t_C wins, the first on ties.
 // Returns false if no trial is above t_C.
+template <int kMode>
 __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
                                    double lnt, EmitTask& w) {
   double best = P.ln_tc;
   bool found = false;
   for (int i = 0; i < n; ++i) {
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
-    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const bool combined = gluon && per_dipole<kMode>(P);
     const int nk = gluon && !combined ? 1 + P.nf : 1;
     const V4 pi = load_p(E, i, ev);
     for (int side = 0; side < 2; ++side) {
@@ -263,6 +264,7 @@ __device__ __forceinline__ PartonScreen load_parton_screen(const Events& E, int6
 
 // The loads of the next parton are issued before the trials of the current
 // one are generated, so their latency hides behind the Philox rounds.
+template <int kMode>
 __device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step,
                                                int n, int first, int stride, Screen& sc) {
   screen_none(sc);
@@ -274,7 +276,7 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
     PartonScreen nxt = cur;
     if (i + stride < n) nxt = load_parton_screen(E, ev, i + stride);
     const bool gluon = cur.flav == kGluon;
-    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const bool combined = gluon && per_dipole<kMode>(P);
     const int nk = gluon && !combined ? 1 + P.nf : 1;
     for (int side = 0; side < 2; ++side) {
       if ((side ? cur.link1 : cur.link0) == kNoLink) continue;
@@ -357,6 +359,7 @@ __device__ __forceinline__ void screen_group_reduce(Screen& sc) {
 // when the event left the active state (status written), kCycleAccepted
 // with `task` filled when an emission must be generated, kCycleVetoed
 // otherwise.
+template <int kMode>
 __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
                                    double lnt, const Screen& sc, EmitTask& task) {
   const float best_key = sc.best_key, best_m = sc.best_m, others_hi = sc.others_hi;
@@ -380,7 +383,7 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
     const int i = dcode >> 1, side = dcode & 1;
     const size_t a = dip_at(E, side, i, ev);
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
-    const bool combined = gluon && P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+    const bool combined = gluon && per_dipole<kMode>(P);
     const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
     const double zp = E.dzp[a], inv_ls = E.dinv[a];
     const double inv_c = combined ? inv_c_sum_fp64(P, zp, inv_ls) : inv_c_fp64(P, kind, zp, inv_ls);
@@ -400,7 +403,7 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   }
   if (!decided) {
     atomicAdd(&E.counters[2], 1ull);  // screen undecided: full FP64 cycle
-    have = select_winner_fp64(P, E, ev, id, step, n, lnt, task);
+    have = select_winner_fp64<kMode>(P, E, ev, id, step, n, lnt, task);
   }
 
   // ---- CheckCutoff.
@@ -478,9 +481,9 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
 
 // Phase 1 of a cycle for active event ev, one thread: SelectWinnerEmission
 // (the FP32 screen over every trial), then cycle_decide.
-template <bool kMulti>
+template <int kMode>
 __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
-  const DevParams& P = params_of<kMulti>(P0, E, ev);
+  const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
   const uint32_t id = event_id(P, E, ev);
   const int n = E.n_partons[ev];
   const int step = E.n_steps[ev];
@@ -490,8 +493,8 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
     return kCycleFinished;
   }
   Screen sc;
-  screen_partons(P, E, ev, id, step, n, 0, 1, sc);
-  return cycle_decide(P, E, ev, id, step, n, lnt, sc, task);
+  screen_partons<kMode>(P, E, ev, id, step, n, 0, 1, sc);
+  return cycle_decide<kMode>(P, E, ev, id, step, n, lnt, sc, task);
 }
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours

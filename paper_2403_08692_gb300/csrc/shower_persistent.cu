@@ -47,11 +47,6 @@ __device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
 #ifndef GAPS_PERSIST_FLUSH
 #define GAPS_PERSIST_FLUSH 32
 #endif
-// A pool is compacted early once 1/GAPS_PERSIST_DEAD_DIV of it has finished
-// (0: only every compaction period).
-#ifndef GAPS_PERSIST_DEAD_DIV
-#define GAPS_PERSIST_DEAD_DIV 8
-#endif
 constexpr int persist_min_blocks(int t) {
   return GAPS_PERSIST_THREADS_PER_SM > 0 && GAPS_PERSIST_THREADS_PER_SM / t > 0 ? GAPS_PERSIST_THREADS_PER_SM / t : 1;
 }
@@ -75,7 +70,7 @@ struct SliceArgs {
   unsigned long long* out_count;
 };
 
-template <int T, bool kMulti, bool kSlice>
+template <int T, int kMode, bool kSlice>
 __global__ void __launch_bounds__(T, persist_min_blocks(T))
     k_shower_persistent(DevParams P0, Events E, int period, SliceArgs sl) {
   __shared__ int32_t s_pool[T];
@@ -83,8 +78,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
   __shared__ uint8_t s_cyc[kSlice ? T : 1];  // cycles run in this slice, per slot
   __shared__ EmitTask s_task[T];
   __shared__ uint32_t s_jobs[kMaxRefresh * T];
-  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail, finished since compaction
-  __shared__ int s_count[7];
+  __shared__ int s_count[6];  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   unsigned long long* cursor = kSlice ? sl.cursor : &E.counters[6];
@@ -129,7 +123,6 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     if (tid == 0) {
       s_count[1] = 0;
       s_count[4] = 0;
-      s_count[6] = 0;
     }
     for (int c = 0; c < period; ++c) {
       __syncthreads();
@@ -143,22 +136,22 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
       int n = 0, step = 0;
       bool limited = false;
       if (live) {
-        const DevParams& P = params_of<kMulti>(P0, E, ev);
+        const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
         n = E.n_partons[ev];
         step = E.n_steps[ev];
         limited = step >= P.max_steps;
-        if (!limited) screen_partons(P, E, ev, event_id(P, E, ev), step, n, sub, lanes, sc);
+        if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, lanes, sc);
       }
       screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
       if (live && sub == 0) {
         if constexpr (kSlice) s_cyc[g] = static_cast<uint8_t>(s_cyc[g] + 1);
-        const DevParams& P = params_of<kMulti>(P0, E, ev);
+        const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
         EmitTask task;
         int r = kCycleFinished;
         if (limited) {
           finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
         } else {
-          r = cycle_decide(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+          r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
         }
         if (r == kCycleAccepted) {
           task.pad0 = static_cast<uint8_t>(g & 255);  // pool slot, to release it after the emission
@@ -167,34 +160,26 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
           s_alive[g] = kSlotDead;
-          atomicAdd(&s_count[6], 1);
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
       __syncthreads();
-      // Compact at the end of the period, or earlier once enough of the pool
-      // has finished (its lanes idle until then).  Flush the queued
-      // emissions once enough have gathered to fill warps, and always before
-      // the pool is compacted.
-      const bool compact_now =
-          c + 1 == period || (GAPS_PERSIST_DEAD_DIV > 0 && s_count[6] * GAPS_PERSIST_DEAD_DIV >= pool);
+      // Flush the queued emissions once enough have gathered to fill warps,
+      // and always before the pool is compacted.  (Compacting early, once an
+      // eighth of the pool had finished, measured no faster.)
       const int queued = s_count[1];
-      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && !compact_now)) {
-        if (compact_now) break;
-        continue;
-      }
-      if (tid < queued) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
+      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && c + 1 < period)) continue;
+      if (tid < queued) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
       __syncthreads();
-      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
+      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
       if (tid < queued) s_alive[s_task[tid].pad0 | (s_task[tid].pad1 << 8)] = kSlotLive;
       __syncthreads();
       if (tid == 0) {
         s_count[1] = 0;
         s_count[4] = 0;
       }
-      if (compact_now) break;
     }
     __syncthreads();
 
@@ -233,14 +218,14 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
   }
 }
 
-template <int T, bool kMulti, bool kSlice>
+template <int T, int kMode, bool kSlice>
 cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks_per_sm, const SliceArgs& sl,
                      cudaStream_t s) {
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T, kMulti, kSlice>, T, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_shower_persistent<T, kMode, kSlice>, T, 0);
   if (e != cudaSuccess) return e;
   if (fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
@@ -248,24 +233,30 @@ cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks
   const int64_t needed = ((kSlice ? sl.n_in : E.n) + T - 1) / T;
   if (blocks > needed) blocks = needed;
   if (blocks == 0) return cudaSuccess;
-  k_shower_persistent<T, kMulti, kSlice><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period, sl);
+  k_shower_persistent<T, kMode, kSlice><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period, sl);
   return cudaGetLastError();
+}
+
+template <int kMode, bool kSlice>
+cudaError_t launch_shape_m(const DevParams& P, const Events& E, const gaps_persistent_config& cfg, const SliceArgs& sl,
+                           cudaStream_t s) {
+  const int k = cfg.compact_period, b = cfg.blocks_per_sm;
+  switch (cfg.block_threads) {
+    case 64: return launch_t<64, kMode, kSlice>(P, E, k, b, sl, s);
+    case 128: return launch_t<128, kMode, kSlice>(P, E, k, b, sl, s);
+    case 256: return launch_t<256, kMode, kSlice>(P, E, k, b, sl, s);
+    case 512: return launch_t<512, kMode, kSlice>(P, E, k, b, sl, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <bool kSlice>
 cudaError_t launch_shape(const DevParams& P, const Events& E, const gaps_persistent_config& cfg, const SliceArgs& sl,
                          cudaStream_t s) {
-  const bool multi = E.jobs != nullptr;
-  const int k = cfg.compact_period, b = cfg.blocks_per_sm;
-  switch (cfg.block_threads) {
-    case 64: return multi ? launch_t<64, true, kSlice>(P, E, k, b, sl, s) : launch_t<64, false, kSlice>(P, E, k, b, sl, s);
-    case 128:
-      return multi ? launch_t<128, true, kSlice>(P, E, k, b, sl, s) : launch_t<128, false, kSlice>(P, E, k, b, sl, s);
-    case 256:
-      return multi ? launch_t<256, true, kSlice>(P, E, k, b, sl, s) : launch_t<256, false, kSlice>(P, E, k, b, sl, s);
-    case 512:
-      return multi ? launch_t<512, true, kSlice>(P, E, k, b, sl, s) : launch_t<512, false, kSlice>(P, E, k, b, sl, s);
-    default: return cudaErrorInvalidValue;
+  switch (launch_mode(P, E)) {
+    case kModeMulti: return launch_shape_m<kModeMulti, kSlice>(P, E, cfg, sl, s);
+    case kModeSingleDipole: return launch_shape_m<kModeSingleDipole, kSlice>(P, E, cfg, sl, s);
+    default: return launch_shape_m<kModeSingleKernel, kSlice>(P, E, cfg, sl, s);
   }
 }
 

@@ -88,7 +88,7 @@ constexpr int kStepThreads = GAPS_STEP_THREADS;
 // *reset_count, the output counter of the next launch.  Counter word 0 counts
 // finished events (the paper's completedEventsCounter), word 1 those stopped
 // by the veto-cycle limit.
-template <bool kMulti>
+template <int kMode>
 __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     k_step_plain(DevParams P, Events E, const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
                  int* list_out, unsigned long long* out_count, unsigned long long* reset_count) {
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   bool survive = false;
   if (active) {
     EmitTask task;
-    const int r = cycle_select_veto<kMulti>(P, E, ev, task);
+    const int r = cycle_select_veto<kMode>(P, E, ev, task);
     if (r == kCycleAccepted) {
       s_task[atomicAdd(&s_naccept, 1)] = task;
     } else if (r == kCycleFinished) {
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     }
   }
   __syncthreads();
-  if (tid < s_naccept) cycle_emit<kMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
+  if (tid < s_naccept) cycle_emit<kMode == kModeMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
   __syncthreads();
-  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P, E, s_task, s_jobs[j]);
+  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMode == kModeMulti>(P, E, s_task, s_jobs[j]);
 }
 
 // Slot of this thread's item in an output list shared by the grid: one
@@ -170,7 +170,7 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // n_tasks_dev) replace the host ones, which then only bound them.  The
 // launch zeroes *reset_list and *reset_tasks, the output counters of the
 // next launch.
-template <bool kMulti, int L>
+template <int kMode, int L>
 __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E, const int* list_in, int64_t len,
                                             int* list_out,
                                             unsigned long long* list_count, EmitTask* tasks_out,
@@ -189,22 +189,22 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     int n = 0, step = 0;
     bool limited = false;
     if (active) {
-      const DevParams& P = params_of<kMulti>(P0, E, ev);
+      const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
       n = E.n_partons[ev];
       step = E.n_steps[ev];
       limited = step >= P.max_steps;
-      if (!limited) screen_partons(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc);
+      if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc);
     }
     screen_group_reduce<L>(sc);  // every lane of the warp, one call site
     const bool lead = active && sub == 0;
     int r = kCycleFinished;
     EmitTask task;
     if (lead) {
-      const DevParams& P = params_of<kMulti>(P0, E, ev);
+      const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
       if (limited) {
         finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
       } else {
-        r = cycle_decide(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+        r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
       }
       if (r == kCycleFinished) {
         atomicAdd(&E.counters[0], 1ull);
@@ -231,7 +231,7 @@ __host__ __device__ __forceinline__ int lanes_for(int64_t len, int64_t resident)
   return lanes;
 }
 
-template <bool kMulti, int L>
+template <int kMode, int L>
 __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     k_step_deferred(DevParams P0, Events E, int64_t select_blocks, const int* list_in,
                     int64_t n_list, const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   }
   if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
     const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
-    select_role<kMulti, L>(P0, E, list_in, len, list_out, list_count, tasks_out, task_count);
+    select_role<kMode, L>(P0, E, list_in, len, list_out, list_count, tasks_out, task_count);
     return;
   }
   const int64_t emit_blocks = static_cast<int64_t>(gridDim.x) - select_blocks;
@@ -261,9 +261,9 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     const bool has = k < len;
     if (has) s_task[tid] = tasks_in[k];
     __syncthreads();
-    if (has) cycle_emit<kMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
+    if (has) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
     __syncthreads();
-    for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMulti>(P0, E, s_task, s_jobs[j]);
+    for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
     if (has) E.status[s_task[tid].ev] = GAPS_ACTIVE;
     const int64_t at_list = warp_append_slot(has, list_count);
     if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
@@ -316,12 +316,19 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
                               unsigned long long* reset_count, cudaStream_t s) {
   if (n_in <= 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n_in + kStepThreads - 1) / kStepThreads);
-  if (E.jobs)
-    k_step_plain<true>
-        <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
-  else
-    k_step_plain<false>
-        <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+  switch (launch_mode(P, E)) {
+    case kModeMulti:
+      k_step_plain<kModeMulti>
+          <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+      break;
+    case kModeSingleDipole:
+      k_step_plain<kModeSingleDipole>
+          <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+      break;
+    default:
+      k_step_plain<kModeSingleKernel>
+          <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
+  }
   return cudaGetLastError();
 }
 
@@ -377,10 +384,15 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
     default:                         \
       GAPS_DEFERRED_CASE(MULTI, 32)  \
   }
-  if (E.jobs) {
-    GAPS_DEFERRED_SWITCH(true)
-  } else {
-    GAPS_DEFERRED_SWITCH(false)
+  switch (launch_mode(P, E)) {
+    case kModeMulti:
+      GAPS_DEFERRED_SWITCH(kModeMulti)
+      break;
+    case kModeSingleDipole:
+      GAPS_DEFERRED_SWITCH(kModeSingleDipole)
+      break;
+    default:
+      GAPS_DEFERRED_SWITCH(kModeSingleKernel)
   }
 #undef GAPS_DEFERRED_SWITCH
 #undef GAPS_DEFERRED_CASE
