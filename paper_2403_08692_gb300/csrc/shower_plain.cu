@@ -72,6 +72,10 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
 #ifndef GAPS_STEP_MIN_BLOCKS
 #define GAPS_STEP_MIN_BLOCKS 4
 #endif
+// Emission blocks of a deferred step launch per SM, at most.
+#ifndef GAPS_EMIT_BLOCKS_PER_SM
+#define GAPS_EMIT_BLOCKS_PER_SM 1
+#endif
 constexpr int kStepThreads = GAPS_STEP_THREADS;
 
 // One veto cycle over the events list_in[0 .. n_in): the list holds the
@@ -152,7 +156,7 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 }
 
 // One step of the plain form with the emissions deferred by one launch.
-// Blocks [0, select_blocks) run SelectWinnerEmission, CheckCutoff and
+// The last select_blocks blocks run SelectWinnerEmission, CheckCutoff and
 // AcceptOrVeto for the events list_in[0 .. n_list) (no list: events
 // 0 .. n_list), one event per group of L lanes and without a block barrier:
 // the group's lanes screen every L-th parton's trials and merge their
@@ -160,10 +164,12 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // first lane decides.  A vetoed event goes back to list_out, an accepted
 // one leaves its emission in tasks_out, a finished one leaves.  The host
 // widens L as the batch thins out, so the last, longest showers do not run
-// their whole trial loop in one thread.  The remaining blocks run
+// their whole trial loop in one thread.  The first blocks run
 // GenerateEmission for the accepted emissions of the previous launch,
-// tasks_in[0 .. n_tasks), 256 per block in full warps, refresh the dipoles
-// they moved block-wide, and put their events back in list_out.  An event
+// tasks_in[0 .. n_tasks), an even share of at most 256 per block in full
+// warps, refresh the dipoles they moved block-wide, and put their events back
+// in list_out.  They come first so that their long FP64 work starts with the
+// launch, beside the select blocks, instead of forming its tail.  An event
 // with a pending emission is in no list, so it never runs two phases in one
 // launch, and its history is the one the fused cycle gives (every draw is
 // keyed by event and cycle).  Lengths given on the device (n_list_dev,
@@ -171,8 +177,8 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // launch zeroes *reset_list and *reset_tasks, the output counters of the
 // next launch.
 template <int kMode, int L>
-__device__ __forceinline__ void select_role(const DevParams& P0, const Events& E, const int* list_in, int64_t len,
-                                            int* list_out,
+__device__ __forceinline__ void select_role(const DevParams& P0, const Events& E, int64_t block,
+                                            const int* list_in, int64_t len, int* list_out,
                                             unsigned long long* list_count, EmitTask* tasks_out,
                                             unsigned long long* task_count) {
   const int tid = threadIdx.x;
@@ -180,7 +186,7 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
   const int sub = tid & (L - 1);
   // the host sizes the grid for any lanes choice: one pass
   {
-    const int64_t idx = static_cast<int64_t>(blockIdx.x) * kGroups + tid / L;
+    const int64_t idx = block * kGroups + tid / L;
     int64_t ev = -1;
     if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
     const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
@@ -246,19 +252,21 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     if (reset_list) *reset_list = 0ull;
     if (reset_tasks) *reset_tasks = 0ull;
   }
-  if (static_cast<int64_t>(blockIdx.x) < select_blocks) {
+  const int64_t emit_blocks = static_cast<int64_t>(gridDim.x) - select_blocks;
+  if (static_cast<int64_t>(blockIdx.x) >= emit_blocks) {
     const int64_t len = n_list_dev ? min(n_list, static_cast<int64_t>(*n_list_dev)) : n_list;
-    select_role<kMode, L>(P0, E, list_in, len, list_out, list_count, tasks_out, task_count);
+    select_role<kMode, L>(P0, E, static_cast<int64_t>(blockIdx.x) - emit_blocks, list_in, len, list_out, list_count,
+                          tasks_out, task_count);
     return;
   }
-  const int64_t emit_blocks = static_cast<int64_t>(gridDim.x) - select_blocks;
   const int64_t len = n_tasks_dev ? min(n_tasks, static_cast<int64_t>(*n_tasks_dev)) : n_tasks;
-  for (int64_t base = (static_cast<int64_t>(blockIdx.x) - select_blocks) * kStepThreads; base < len;
-       base += emit_blocks * kStepThreads) {
+  // each block's share: a whole number of warps, at most one block's worth
+  const int64_t share = min(static_cast<int64_t>(kStepThreads), ((len + emit_blocks - 1) / emit_blocks + 31) / 32 * 32);
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * share; base < len; base += emit_blocks * share) {
     __syncthreads();  // the previous round is done with s_task and s_jobs
     if (tid == 0) s_njobs = 0;
     const int64_t k = base + tid;
-    const bool has = k < len;
+    const bool has = tid < share && k < len;
     if (has) s_task[tid] = tasks_in[k];
     __syncthreads();
     if (has) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
@@ -359,12 +367,13 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
   // the lanes per event follow from the bound (at most one step narrower
   // than the exact length would give, since the bound is one or two launches
   // old).  The select grid covers n_list x lanes threads in one pass; the
-  // emission blocks stride over the tasks, one wave at most.
+  // emission blocks share the tasks, at least a warp's worth each and at
+  // most GAPS_EMIT_BLOCKS_PER_SM blocks per SM, so that every SM starts with
+  // about the same FP64 load.
   const int64_t resident = resident_threads();
-  const int64_t resident_blocks = resident / kStepThreads;
   const int lanes = lanes_for(n_list, resident);
   const int64_t select_blocks = (n_list * lanes + kStepThreads - 1) / kStepThreads;
-  const int64_t emit_blocks = std::min((n_tasks + kStepThreads - 1) / kStepThreads, resident_blocks);
+  const int64_t emit_blocks = std::min((n_tasks + 31) / 32, resident / 1024 * GAPS_EMIT_BLOCKS_PER_SM);
   if (select_blocks + emit_blocks == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>(select_blocks + emit_blocks);
 #define GAPS_DEFERRED_CASE(MULTI, LN)                                                                     \
