@@ -32,7 +32,8 @@ UNIT = "events/s"
 # Trial ranking and veto decisions give the same outcome in FP32 and are not
 # counted.  "simple" = +, -, x or a fused a*b+c; the other operations are
 # converted to DFMA-equivalents with their throughput measured on the device
-# in the same run (gaps_probe_fp64_rates).
+# in the same run (gaps_probe_fp64_rates; a log at the rate of the faster of
+# the library's and the shower's own table-driven log).
 #   per winner:   ln r and the scaled update of ln t
 #   per emission: t = exp(ln t), z (expm1), y, the azimuth (sincospi), the
 #                 dipole map (transverse frame, k_perp, three momenta) and
@@ -68,7 +69,11 @@ def step_kernel_traffic(event_cycles_per_launch):
 
 
 def dfma_equivalents(counts, rates):
-    return sum(n * (1.0 if op == "simple" else rates["dfma"] / rates[op]) for op, n in counts.items())
+    """DFMA-equivalents of an operation count; a logarithm costs what the
+    faster of the library's log and the shower's table-driven one costs."""
+    def rate(op):
+        return max(rates["log"], rates.get("log_fp64", 0.0)) if op == "log" else rates[op]
+    return sum(n * (1.0 if op == "simple" else rates["dfma"] / rate(op)) for op, n in counts.items())
 
 
 def kernels_outside_shower(capacity):
@@ -678,7 +683,8 @@ def main():
                                     f"MEASURED_PEAKS.json has no FP64 entry",
                      "work_model": f"required FP64 work: {dfma_per_winner:.1f} DFMA-equivalents per winner, "
                                    f"{dfma_per_emission:.1f} per accepted emission (oracle formulas; "
-                                   f"transcendentals at their measured cost), x2 flops",
+                                   f"transcendentals at their measured cost, a log at the faster of "
+                                   f"the library's and the table-driven one), x2 flops",
                      "launches_per_pass": launches_per_pass,
                      "avg_launch_ms": kernel_s_per_launch * 1e3,
                      "fp64_probe_per_s": {k: float(f"{v:.4g}") for k, v in rates.items()},

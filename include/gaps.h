@@ -384,10 +384,22 @@ int gaps_event_shapes_noalloc(const double* px, const double* py, const double* 
 /* --------------------------------------------------------------- misc */
 
 /* Measurement helper (no counterpart in the paper): FP64 results per second
- * of this GPU with every SM busy, for DFMA, log, exp, division, sqrt and
- * sincospi, in host_rates[0..5].  device_sink: one device double, never
- * written in practice.  Synchronous; about 50 ms. */
+ * of this GPU with every SM busy, for DFMA, log, exp, division, sqrt,
+ * sincospi and the shower's own logarithm (gaps_log_fp64_*), in
+ * host_rates[0..6] (caller-owned, 7 doubles).  device_sink: one device
+ * double, never written in practice.  Synchronous; about 60 ms. */
 int gaps_probe_fp64_rates(double* device_sink, double* host_rates, void* stream);
+
+/* The FP64 natural logarithm the shower kernels use for the winning trial's
+ * scale, ln t' = ln t + ln(r)/c (Eq. (A.5) in log form), and for the dipole
+ * cache's ln(z+/z-) (Eq. (A.4)): P. T. P. Tang's table-driven method (ACM
+ * TOMS 16 (1990) 378), error below one ulp for positive normal x; other
+ * inputs take the CUDA library's log.  y[i] = ln x[i] for 0 <= i < n.
+ * _host: host arrays, computed on the calling thread.  _device: device
+ * arrays, asynchronous on `stream`.  Both return GAPS_ERR_INVALID for n < 0
+ * or a null array with n > 0.  Exported for the accuracy tests. */
+int gaps_log_fp64_host(const double* x, double* y, int64_t n);
+int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream);
 const char* gaps_strerror(int status);
 const char* gaps_last_cuda_error(void);
 /* Library version as major * 10000 + minor * 100 + patch. */

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "gaps.h"
+#include "log_fp64.cuh"
 
 namespace gaps {
 
@@ -202,7 +203,7 @@ constexpr unsigned long long kFnvBasis = 14695981039346656037ull;
 // One-loop running coupling alpha_s(t); the fixed mode returns alpha_s(m_Z).
 __device__ __forceinline__ double alpha_s(const DevParams& P, double t) {
   if (P.fixed) return P.alphas_mz;
-  return P.alphas_mz / (1.0 + P.alphas_mz * P.b0 * log(t / (kMZ * kMZ)));
+  return P.alphas_mz / (1.0 + P.alphas_mz * P.b0 * log_fp64(t / (kMZ * kMZ)));
 }
 
 // Splitting kernel P(z, y) and its overestimate P^over(z).

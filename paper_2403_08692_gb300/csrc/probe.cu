@@ -1,8 +1,11 @@
-// FP64 throughput probe: how many DFMA, log, exp, division, square root and
-// sincospi results per second this GPU delivers, with every SM busy.  The
-// benchmark uses it to express the shower's required FP64 work in
-// DFMA-equivalents measured on the same device in the same run.
+// FP64 throughput probe: how many DFMA, log, exp, division, square root,
+// sincospi and table-driven log (log_fp64) results per second this GPU
+// delivers, with every SM busy.  The benchmark uses it to express the
+// shower's required FP64 work in DFMA-equivalents measured on the same device
+// in the same run.  Also the exported log_fp64, host and device, for the
+// accuracy tests.
 #include "gaps_launch.hpp"
+#include "log_fp64.cuh"
 
 namespace gaps {
 
@@ -10,8 +13,9 @@ namespace {
 
 constexpr int kProbeThreads = 256;
 constexpr int kChains = 4;
+constexpr int kProbeOps = 7;
 
-// One of six operations, iterated on independent chains; the result is
+// One of seven operations, iterated on independent chains; the result is
 // stored only under a condition no input meets, so nothing is written and
 // nothing can be optimised away.
 template <int OP>
@@ -41,10 +45,13 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* sink, int iters
       } else if (OP == 4) {
         acc[c] += sqrt(x[c]);
         x[c] += 0.25;
-      } else {
+      } else if (OP == 5) {
         double s, co;
         sincospi(x[c], &s, &co);
         acc[c] += s + co;
+        x[c] += 0.25;
+      } else {
+        acc[c] += log_fp64(x[c]);
         x[c] += 0.25;
       }
     }
@@ -88,18 +95,44 @@ extern "C" int gaps_probe_fp64_rates(double* device_sink, double* host_rates, vo
   const int blocks = sms * 8;
   const double threads = static_cast<double>(blocks) * kProbeThreads;
   // iterations per thread, sized for a few milliseconds per operation
-  const int iters[6] = {2048, 256, 256, 512, 512, 256};
+  const int iters[kProbeOps] = {2048, 256, 256, 512, 512, 256, 512};
   // results per iteration and chain: the FMA loop issues two DFMA
-  const double per_iter[6] = {2.0, 1.0, 1.0, 1.0, 1.0, 1.0};
-  float ms[6] = {0, 0, 0, 0, 0, 0};
+  const double per_iter[kProbeOps] = {2.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+  float ms[kProbeOps] = {0, 0, 0, 0, 0, 0, 0};
   e = time_op<0>(device_sink, blocks, iters[0], s, &ms[0]);
   if (e == cudaSuccess) e = time_op<1>(device_sink, blocks, iters[1], s, &ms[1]);
   if (e == cudaSuccess) e = time_op<2>(device_sink, blocks, iters[2], s, &ms[2]);
   if (e == cudaSuccess) e = time_op<3>(device_sink, blocks, iters[3], s, &ms[3]);
   if (e == cudaSuccess) e = time_op<4>(device_sink, blocks, iters[4], s, &ms[4]);
   if (e == cudaSuccess) e = time_op<5>(device_sink, blocks, iters[5], s, &ms[5]);
+  if (e == cudaSuccess) e = time_op<6>(device_sink, blocks, iters[6], s, &ms[6]);
   if (e != cudaSuccess) return record_cuda_error(e);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < kProbeOps; ++i)
     host_rates[i] = ms[i] > 0.0f ? threads * kChains * iters[i] * per_iter[i] / (ms[i] * 1e-3) : 0.0;
   return GAPS_OK;
+}
+
+namespace gaps {
+namespace {
+
+__global__ void __launch_bounds__(256) k_log_fp64(const double* x, double* y, int64_t n) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = log_fp64(x[k]);
+}
+
+}  // namespace
+}  // namespace gaps
+
+extern "C" int gaps_log_fp64_host(const double* x, double* y, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return GAPS_ERR_INVALID;
+  for (int64_t k = 0; k < n; ++k) y[k] = log_fp64(x[k]);
+  return GAPS_OK;
+}
+
+extern "C" int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return GAPS_ERR_INVALID;
+  if (n == 0) return GAPS_OK;
+  k_log_fp64<<<static_cast<unsigned>((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GAPS_OK : record_cuda_error(e);
 }

@@ -79,7 +79,7 @@ __device__ __forceinline__ DipoleEntry make_dipole(const DevParams& P, double q2
     return d;
   }
   d.zp = 0.5 * (1.0 + sqrt(1.0 - 4.0 * P.tc / q2));
-  const double ls = log(d.zp / (1.0 - d.zp));
+  const double ls = log_fp64(d.zp / (1.0 - d.zp));
   d.inv_ls = 1.0 / ls;
   d.screen = make_float2(1.0f / (P.as2pi_f * static_cast<float>(ls)),
                          1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * static_cast<float>(2.0 * d.zp - 1.0)));
@@ -175,7 +175,7 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
           const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
           const double u = h ? to_unit(r.z, r.w) : to_unit(r.x, r.y);
           const double inv_c = combined ? inv_c_sum_fp64(P, d.zp, d.inv_ls) : inv_c_fp64(P, kind, d.zp, d.inv_ls);
-          const double lt = lnt + log(u) * inv_c;
+          const double lt = lnt + log_fp64(u) * inv_c;
           if (lt > best) {
             best = lt;
             found = true;
@@ -387,7 +387,7 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
     const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
     const double zp = E.dzp[a], inv_ls = E.dinv[a];
     const double inv_c = combined ? inv_c_sum_fp64(P, zp, inv_ls) : inv_c_fp64(P, kind, zp, inv_ls);
-    const double lt = lnt + log(to_unit(best_hi, best_lo)) * inv_c;
+    const double lt = lnt + log_fp64(to_unit(best_hi, best_lo)) * inv_c;
     if (lt > P.ln_tc) {
       task.lnt = lt;
       task.q2 = E.dq2[a];

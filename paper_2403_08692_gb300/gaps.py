@@ -90,6 +90,8 @@ SIGNATURES = {
                                             C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
                                             C.c_void_p]),
     "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
+    "gaps_log_fp64_host": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64]),
+    "gaps_log_fp64_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "gaps_pool_reset": (C.c_int, [_P(Batch), C.c_void_p]),
     "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
                                   C.c_void_p]),
@@ -253,13 +255,33 @@ def reduce_stats(ws, stats_device, stream=None):
 
 def probe_fp64_rates(stream=None):
     """FP64 results per second of this GPU: dict of dfma, log, exp, div, sqrt,
-    sincospi."""
+    sincospi and log_fp64 (the shower's table-driven log)."""
     import torch
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
-    rates = (C.c_double * 6)()
+    rates = (C.c_double * 7)()
     _check(load().gaps_probe_fp64_rates(C.c_void_p(sink.data_ptr()), rates, _stream_handle(stream)),
            "gaps_probe_fp64_rates")
-    return dict(zip(("dfma", "log", "exp", "div", "sqrt", "sincospi"), list(rates)))
+    return dict(zip(("dfma", "log", "exp", "div", "sqrt", "sincospi", "log_fp64"), list(rates)))
+
+
+def log_fp64_host(x):
+    """The shower's FP64 logarithm on a float64 numpy array (host code)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _check(load().gaps_log_fp64_host(x.ctypes.data_as(_P(C.c_double)), y.ctypes.data_as(_P(C.c_double)),
+                                     int(x.size)), "gaps_log_fp64_host")
+    return y
+
+
+def log_fp64_device(x, stream=None):
+    """The shower's FP64 logarithm on a contiguous float64 CUDA tensor."""
+    import torch
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(load().gaps_log_fp64_device(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.numel()),
+                                       _stream_handle(stream)), "gaps_log_fp64_device")
+    return y
 
 
 NOALLOC_MAX_EVENTS = 1 << 20
