@@ -1,5 +1,6 @@
 // C ABI entry points (include/gaps.h): argument checks, workspace layout,
 // launch sequencing and the host all-done loop of the plain shower form.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -328,23 +329,38 @@ cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
 // workspace counters, the events that mark each slot's copy, and the timing
 // events of gaps_shower_timed, created once and reused by every call the
 // thread makes (a few hundred bytes of page-locked host memory).
+// Host memory of the plain form's host loop, per host thread: the final
+// counters, the host-mapped slots the step launches publish their input
+// lengths to ({list, tasks, sequence number}, kSlots of them in rotation),
+// and the timing events.  Sequence numbers grow across calls (`next_seq`),
+// so a slot never shows a value of an earlier call as current.
 struct HostCounters {
   static constexpr int kSlots = 8;
+  static constexpr int kSlotWords = 4;
   unsigned long long* words = nullptr;
-  cudaEvent_t done[kSlots] = {};
+  unsigned long long* pub = nullptr;      // host view
+  unsigned long long* pub_dev = nullptr;  // device view of the same memory
+  unsigned long long next_seq = 1;
   std::vector<cudaEvent_t> timing;
   bool ok = false;
   cudaError_t err = cudaSuccess;
-  unsigned long long* slot(int k) { return words + static_cast<size_t>(k) * kCounterWords; }
 };
 
 HostCounters& host_counters() {
   thread_local HostCounters hc;
   if (!hc.ok) {
     hc.err = cudaSuccess;
-    if (!hc.words) hc.err = cudaMallocHost(&hc.words, HostCounters::kSlots * kCounterWords * sizeof(unsigned long long));
-    for (int k = 0; k < HostCounters::kSlots && hc.err == cudaSuccess; ++k)
-      if (!hc.done[k]) hc.err = cudaEventCreateWithFlags(&hc.done[k], cudaEventDisableTiming);
+    if (!hc.words) hc.err = cudaMallocHost(&hc.words, kCounterWords * sizeof(unsigned long long));
+    if (hc.err == cudaSuccess && !hc.pub) {
+      hc.err = cudaHostAlloc(&hc.pub, HostCounters::kSlots * HostCounters::kSlotWords * sizeof(unsigned long long),
+                             cudaHostAllocMapped);
+      if (hc.err == cudaSuccess) {
+        std::memset(hc.pub, 0, HostCounters::kSlots * HostCounters::kSlotWords * sizeof(unsigned long long));
+        void* d = nullptr;
+        hc.err = cudaHostGetDevicePointer(&d, hc.pub, 0);
+        hc.pub_dev = static_cast<unsigned long long*>(d);
+      }
+    }
     hc.ok = hc.err == cudaSuccess;
   }
   return hc;
@@ -409,9 +425,11 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
   // lengths on the device.  The host therefore never waits for a launch
   // before queueing the next: it sizes the grids from a count one or two
   // launches old (the number of live events only falls, so that count
-  // bounds them), and reads the counters back asynchronously.  An event
-  // stops after max_steps cycles and each cycle takes at most two launches,
-  // so at most 2 max_steps + 1 launches have work.
+  // bounds them).  It learns the counts without a copy on the stream: each
+  // launch writes the lengths the previous one left to host-mapped memory
+  // as it starts.  An event stops after max_steps cycles and each cycle
+  // takes at most two launches, so at most 2 max_steps + 1 launches have
+  // work.
   HostCounters& hc = host_counters();
   if (!hc.ok) return cuda_fail(hc.err);
   std::vector<cudaEvent_t>& tev = hc.timing;
@@ -419,6 +437,12 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
   int64_t queued = 0;   // launches queued
   int64_t worked = 0;   // launches whose input held events
   const int64_t max_launches = 2 * static_cast<int64_t>(P.max_steps) + 2;
+  const unsigned long long seq0 = hc.next_seq;  // launch c publishes launch c - 1's lengths as seq0 + c
+  hc.next_seq += static_cast<unsigned long long>(max_launches) + 1;
+  auto pub_slot = [&](int64_t c, bool device) {
+    const size_t at = static_cast<size_t>(c % HostCounters::kSlots) * HostCounters::kSlotWords;
+    return (device ? hc.pub_dev : hc.pub) + at;
+  };
   auto enqueue = [&](int64_t c) -> cudaError_t {
     const int in_half = static_cast<int>(c & 1), out_half = 1 - in_half;
     const int* list_in = c == 0 ? nullptr : E.active + static_cast<size_t>(in_half) * E.n;
@@ -440,47 +464,58 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     unsigned long long* lw = &E.counters[kPlainListWord];
     unsigned long long* tw = &E.counters[kPlainTaskWord];
     const int r0 = static_cast<int>(c % 3), r1 = static_cast<int>((c + 1) % 3), r2 = static_cast<int>((c + 2) % 3);
+    const StepPublish pub{c == 0 ? nullptr : pub_slot(c - 1, true), seq0 + static_cast<unsigned long long>(c)};
     err = launch_step_deferred(P, E, list_in, c == 0 ? E.n : bound, c == 0 ? nullptr : lw + r0, tasks_in,
                                c == 0 ? 0 : bound, c == 0 ? nullptr : tw + r0, list_out, lw + r1, tasks_out, tw + r1,
-                               lw + r2, tw + r2, s);
+                               lw + r2, tw + r2, pub, s);
     if (err != cudaSuccess) return err;
     if (kernel_ms_out && (err = cudaEventRecord(tev[2 * c + 1], s)) != cudaSuccess) return err;
     // While the list is long, put it back in event order (appends scatter
     // it); the same events, so its length stands.
     if (bound * 16 >= E.n && (err = launch_list_active(E, list_out, &E.counters[7], s)) != cudaSuccess) return err;
-    const int slot = static_cast<int>(c % HostCounters::kSlots);
-    err = cudaMemcpyAsync(hc.slot(slot), E.counters, kCounterWords * sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, s);
-    if (err == cudaSuccess) err = cudaEventRecord(hc.done[slot], s);
-    return err;
+    return cudaSuccess;
   };
-  // Counters of launch c once it has finished: the live events it leaves.
-  auto live_after = [&](int64_t c, const unsigned long long** words) -> cudaError_t {
-    const int slot = static_cast<int>(c % HostCounters::kSlots);
-    const cudaError_t err = cudaEventSynchronize(hc.done[slot]);
-    const int r1 = static_cast<int>((c + 1) % 3);
-    *words = hc.slot(slot);
-    bound = static_cast<int64_t>((*words)[kPlainListWord + r1] + (*words)[kPlainTaskWord + r1]);
-    return err;
+  // The live events launch c leaves, once launch c + 1 has published them
+  // (or, for the last queued launch, once the stream has drained).
+  auto live_after = [&](int64_t c) -> cudaError_t {
+    if (c + 1 >= queued) {
+      cudaError_t err = cudaMemcpyAsync(hc.words, E.counters, kCounterWords * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      const int r1 = static_cast<int>((c + 1) % 3);
+      bound = static_cast<int64_t>(hc.words[kPlainListWord + r1] + hc.words[kPlainTaskWord + r1]);
+      return err;
+    }
+    volatile unsigned long long* w = pub_slot(c, false);
+    const unsigned long long want = seq0 + static_cast<unsigned long long>(c) + 1;
+    for (uint64_t spin = 1; w[2] != want; ++spin) {
+      if ((spin & 1023) != 0) continue;
+      // every 1024 polls: has the stream failed, or drained without it?
+      const cudaError_t q = cudaStreamQuery(s);
+      if (q == cudaSuccess && w[2] != want) return cudaErrorUnknown;
+      if (q != cudaSuccess && q != cudaErrorNotReady) return q;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    bound = static_cast<int64_t>(w[0] + w[1]);
+    return cudaSuccess;
   };
-  const unsigned long long* words = nullptr;
   if ((e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
   for (int64_t c = 0;; ++c) {
     // c: the oldest launch not yet read back; keep kLookahead more queued
-    // behind it, so the GPU has work while the host reads counts back
+    // behind it, so the GPU has work while the host waits for the counts
     while (queued < max_launches && queued <= c + kLookahead)
       if ((e = enqueue(queued++)) != cudaSuccess) return cuda_fail(e);
-    if ((e = live_after(c, &words)) != cudaSuccess) return cuda_fail(e);
+    if ((e = live_after(c)) != cudaSuccess) return cuda_fail(e);
     worked = c + 1;
     if (bound == 0 || queued >= max_launches) break;
   }
   // The launches queued after the last one with work have empty inputs; the
   // counters after the last queued launch are final.
-  e = cudaStreamSynchronize(s);
+  e = cudaMemcpyAsync(hc.words, E.counters, kCounterWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e);
-  words = hc.slot(static_cast<int>((queued - 1) % HostCounters::kSlots));
-  cnt[0] = words[0];
-  cnt[1] = words[1];
+  cnt[0] = hc.words[0];
+  cnt[1] = hc.words[1];
   double total_ms = 0.0;
   if (kernel_ms_out) {
     for (int64_t c = 0; c < worked; ++c) {
@@ -690,7 +725,8 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
     const cudaError_t e = launch_step_deferred(
         P, E, E.active + in, max_active, &E.counters[10 + c % 3], E.tasks + in, max_active,
         &E.counters[18 + c % 3], E.active + out, &E.counters[10 + (c + 1) % 3], E.tasks + out,
-        &E.counters[18 + (c + 1) % 3], &E.counters[10 + (c + 2) % 3], &E.counters[18 + (c + 2) % 3], s);
+        &E.counters[18 + (c + 1) % 3], &E.counters[10 + (c + 2) % 3], &E.counters[18 + (c + 2) % 3],
+        StepPublish{nullptr, 0ull}, s);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return GAPS_OK;

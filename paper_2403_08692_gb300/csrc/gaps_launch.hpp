@@ -27,12 +27,20 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
 // emissions tasks_in[0 .. n_tasks) accepted by the previous step.  Vetoed and
 // emitted events go to list_out, accepted ones to tasks_out; *reset_list and
 // *reset_tasks are zeroed.  n_list_dev / n_tasks_dev (may be NULL): the
-// lengths on the device, the host ones then only bound them.
+// lengths on the device, the host ones then only bound them.  With
+// pub.slot set (host-mapped memory), the launch writes its input lengths --
+// the previous launch's output lengths -- to pub.slot[0..1] as it starts,
+// then pub.seq to pub.slot[2], so that the host learns them without a copy
+// on the stream.
+struct StepPublish {
+  unsigned long long* slot;
+  unsigned long long seq;
+};
 cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int* list_in, int64_t n_list,
                                  const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                                 unsigned long long* reset_tasks, cudaStream_t s);
+                                 unsigned long long* reset_tasks, StepPublish pub, cudaStream_t s);
 // The active list of a batch rebuilt in event order (events with status
 // GAPS_ACTIVE); *count is a scratch counter.
 cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s);
