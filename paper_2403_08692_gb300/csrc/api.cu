@@ -93,6 +93,7 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   d.sqrt_s = p.sqrt_s;
   d.s = p.sqrt_s * p.sqrt_s;
   d.tc = p.t_cutoff;
+  d.inv_4tc = 1.0 / (4.0 * p.t_cutoff);
   d.alphas_mz = p.alphas_mz;
   d.nf = p.n_flavours;
   d.fixed = p.fixed_alphas ? 1 : 0;

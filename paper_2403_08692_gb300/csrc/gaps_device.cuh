@@ -41,6 +41,7 @@ struct DevParams {
   int trial_mode;  // GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE
   double ln_tc;                       // ln t_C
   double ln_s;                        // ln s, the starting scale of the evolution variable
+  double inv_4tc;                     // 1 / (4 t_C)
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
   // FP32 copies used by the screens
   float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;
@@ -246,28 +247,31 @@ __device__ __forceinline__ double det3(double a1, double a2, double a3, double b
 // spacelike vectors orthogonal to a, b and each other: n1 projects the
 // first of the references (1,1,0,0), (1,0,1,0), (1,0,0,1) whose projection
 // has |n1^2| >= 1e-4, n2 is the Minkowski-orthogonal complement of (a, b,
-// n1) (cofactor expansion of det[X; a; b; n1]).
+// n1) (cofactor expansion of det[X; a; b; n1]).  The projections share one
+// reciprocal of a.b and both normalisations take the library's rsqrt (one
+// ulp), the oracle's 1/sqrt up to rounding.
 __device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, double y, double cphi,
                                            double sphi, V4& pi, V4& pj, V4& pb) {
   const double ab = mdot(a, b);
   const double q2 = 2.0 * ab;
+  const double inv_ab = 1.0 / ab;
   V4 n1{0, 0, 0, 0};
   for (int r = 0; r < 3; ++r) {
     const V4 ref{1.0, r == 0 ? 1.0 : 0.0, r == 1 ? 1.0 : 0.0, r == 2 ? 1.0 : 0.0};
-    const double cb = mdot(ref, b) / ab;
-    const double ca = mdot(ref, a) / ab;
+    const double cb = mdot(ref, b) * inv_ab;
+    const double ca = mdot(ref, a) * inv_ab;
     n1 = V4{ref.e - cb * a.e - ca * b.e, ref.x - cb * a.x - ca * b.x, ref.y - cb * a.y - ca * b.y,
             ref.z - cb * a.z - ca * b.z};
     if (fabs(mdot(n1, n1)) >= 1e-4) break;
   }
-  const double s1 = 1.0 / sqrt(-mdot(n1, n1));
+  const double s1 = rsqrt(-mdot(n1, n1));
   n1 = V4{n1.e * s1, n1.x * s1, n1.y * s1, n1.z * s1};
   const double c0 = det3(a.x, a.y, a.z, b.x, b.y, b.z, n1.x, n1.y, n1.z);
   const double c1 = -det3(a.e, a.y, a.z, b.e, b.y, b.z, n1.e, n1.y, n1.z);
   const double c2 = det3(a.e, a.x, a.z, b.e, b.x, b.z, n1.e, n1.x, n1.z);
   const double c3 = -det3(a.e, a.x, a.y, b.e, b.x, b.y, n1.e, n1.x, n1.y);
   V4 n2{c0, -c1, -c2, -c3};
-  const double s2 = 1.0 / sqrt(-mdot(n2, n2));
+  const double s2 = rsqrt(-mdot(n2, n2));
   n2 = V4{n2.e * s2, n2.x * s2, n2.y * s2, n2.z * s2};
   const double kt = sqrt(z * (1.0 - z) * y * q2);
   const double kc = kt * cphi, ks = kt * sphi;
