@@ -356,13 +356,37 @@ __global__ void __launch_bounds__(256) k_bucket_scan(const int* counts, int* off
 }
 
 // Finished events go to their bucket; the others get undefined observables.
+// A warp's lanes of one bucket take their places with one shared-memory
+// atomic, a block's with one global atomic per bucket and round, so the
+// few hot buckets (a handful of multiplicities hold most events) see a
+// thousand times fewer global atomics than with one per event.
 __global__ void __launch_bounds__(256) k_bucket_scatter(Events E, int* cursor, int* order) {
-  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (ev >= E.n) return;
-  if (E.status[ev] == GAPS_DONE) {
-    order[atomicAdd(&cursor[E.n_partons[ev]], 1)] = static_cast<int>(ev);
-  } else {
-    for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.stride + ev] = -1.0;
+  __shared__ int s_cnt[256];
+  __shared__ int s_base[256];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int64_t first = static_cast<int64_t>(blockIdx.x) * 256; first < E.n;
+       first += static_cast<int64_t>(gridDim.x) * 256) {
+    s_cnt[tid] = 0;
+    __syncthreads();
+    const int64_t ev = first + tid;
+    int n = -1;
+    if (ev < E.n) {
+      if (E.status[ev] == GAPS_DONE) {
+        n = E.n_partons[ev];
+      } else {
+        for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.stride + ev] = -1.0;
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, n);
+    const int leader = __ffs(peers) - 1;
+    int at = 0;
+    if (n >= 0 && lane == leader) at = atomicAdd(&s_cnt[n], __popc(peers));
+    at = __shfl_sync(0xffffffffu, at, leader) + __popc(peers & ((1u << lane) - 1u));
+    __syncthreads();
+    if (s_cnt[tid]) s_base[tid] = atomicAdd(&cursor[tid], s_cnt[tid]);
+    __syncthreads();
+    if (n >= 0) order[s_base[n] + at] = static_cast<int>(ev);
+    __syncthreads();  // s_cnt and s_base are reused by the next round
   }
 }
 
@@ -394,7 +418,7 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
   const unsigned grid_count = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);
   k_bucket_count<<<grid_count, 256, 0, s>>>(E, counts);
   k_bucket_scan<<<1, 256, 0, s>>>(counts, offsets, cursor);
-  k_bucket_scatter<<<static_cast<unsigned>(want), 256, 0, s>>>(E, cursor, order);
+  k_bucket_scatter<<<grid_count, 256, 0, s>>>(E, cursor, order);
   // One launch per multiplicity class; grids cover the largest possible
   // class and stride over the actual one.
   const int64_t all = (E.n + kShapeThreads - 1) / kShapeThreads;
