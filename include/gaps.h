@@ -125,7 +125,9 @@ typedef struct gaps_layout {
                              7 scratch of the plain form's list rebuild; 21..23 the plain form's
                              active-list lengths and 24..26 its deferred-emission counts, rotating
                              over three launches; 10..12 and 18..20 the same for the serving pool;
-                             27 the plain form's list rebuilds; 28 the pool slices' event cursor */
+                             27 the plain form's list rebuilds; 28 the pool slices' event cursor;
+                             29..31 and 13..15 the emission-task cursors of the plain form's and the
+                             pool's step launches */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */

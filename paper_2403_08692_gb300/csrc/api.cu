@@ -320,16 +320,13 @@ bool config_ok(const gaps_persistent_config& c) {
 // Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
 // persistent form's event cursor).
 cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
-  // words 0..9 and the plain form's list and task counts
+  // words 0..9 and the plain form's list and task counts and emission cursors
   cudaError_t e = cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainListWord, 0, 7 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainEmitCursorWord, 0, 3 * sizeof(unsigned long long), s);
   return e;
 }
 
-// Per host thread: pinned slots for the asynchronous readback of the
-// workspace counters, the events that mark each slot's copy, and the timing
-// events of gaps_shower_timed, created once and reused by every call the
-// thread makes (a few hundred bytes of page-locked host memory).
 // Host memory of the plain form's host loop, per host thread: the final
 // counters, the host-mapped slots the step launches publish their input
 // lengths to ({list, tasks, sequence number}, kSlots of them in rotation),
@@ -464,11 +461,12 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     // (c+2)%3 for launch c+1 (never a word that it or a neighbour reads).
     unsigned long long* lw = &E.counters[kPlainListWord];
     unsigned long long* tw = &E.counters[kPlainTaskWord];
+    unsigned long long* cw = &E.counters[kPlainEmitCursorWord];
     const int r0 = static_cast<int>(c % 3), r1 = static_cast<int>((c + 1) % 3), r2 = static_cast<int>((c + 2) % 3);
     const StepPublish pub{c == 0 ? nullptr : pub_slot(c - 1, true), seq0 + static_cast<unsigned long long>(c)};
     err = launch_step_deferred(P, E, list_in, c == 0 ? E.n : bound, c == 0 ? nullptr : lw + r0, tasks_in,
                                c == 0 ? 0 : bound, c == 0 ? nullptr : tw + r0, list_out, lw + r1, tasks_out, tw + r1,
-                               lw + r2, tw + r2, pub, s);
+                               lw + r2, tw + r2, cw + r0, cw + r2, pub, s);
     if (err != cudaSuccess) return err;
     if (kernel_ms_out && (err = cudaEventRecord(tev[2 * c + 1], s)) != cudaSuccess) return err;
     // While the list is long, put it back in event order (appends scatter
@@ -727,6 +725,7 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
         P, E, E.active + in, max_active, &E.counters[10 + c % 3], E.tasks + in, max_active,
         &E.counters[18 + c % 3], E.active + out, &E.counters[10 + (c + 1) % 3], E.tasks + out,
         &E.counters[18 + (c + 1) % 3], &E.counters[10 + (c + 2) % 3], &E.counters[18 + (c + 2) % 3],
+        &E.counters[kPoolEmitCursorWord + c % 3], &E.counters[kPoolEmitCursorWord + (c + 2) % 3],
         StepPublish{nullptr, 0ull}, s);
     if (e != cudaSuccess) return cuda_fail(e);
   }

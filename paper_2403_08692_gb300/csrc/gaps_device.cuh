@@ -66,6 +66,10 @@ constexpr int kPlainListWord = 21;
 constexpr int kPlainTaskWord = 24;
 constexpr int kRebuildWord = 27;
 constexpr int kSliceCursorWord = 28;
+// The deferred step's emission-task cursor, rotating like the lengths:
+// plain form words 29..31, serving pool words 13..15.
+constexpr int kPlainEmitCursorWord = 29;
+constexpr int kPoolEmitCursorWord = 13;
 
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {

@@ -28,6 +28,8 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
 // emitted events go to list_out, accepted ones to tasks_out; *reset_list and
 // *reset_tasks are zeroed.  n_list_dev / n_tasks_dev (may be NULL): the
 // lengths on the device, the host ones then only bound them.  With
+// *emit_cursor hands out the emission tasks in chunks (zero before the
+// launch); *reset_cursor, the next launch's cursor, is zeroed.  With
 // pub.slot set (host-mapped memory), the launch writes its input lengths --
 // the previous launch's output lengths -- to pub.slot[0..1] as it starts,
 // then pub.seq to pub.slot[2], so that the host learns them without a copy
@@ -40,7 +42,8 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
                                  const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                                 unsigned long long* reset_tasks, StepPublish pub, cudaStream_t s);
+                                 unsigned long long* reset_tasks, unsigned long long* emit_cursor,
+                                 unsigned long long* reset_cursor, StepPublish pub, cudaStream_t s);
 // The active list of a batch rebuilt in event order (events with status
 // GAPS_ACTIVE); *count is a scratch counter.
 cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s);

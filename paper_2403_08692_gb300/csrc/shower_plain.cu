@@ -74,10 +74,9 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
 #ifndef GAPS_STEP_MIN_BLOCKS
 #define GAPS_STEP_MIN_BLOCKS (1024 / GAPS_STEP_THREADS)
 #endif
-// Emission threads of a deferred step launch per SM, at most, in units of
-// 256.
-#ifndef GAPS_EMIT_BLOCKS_PER_SM
-#define GAPS_EMIT_BLOCKS_PER_SM 1
+// Emission warps of a deferred step launch per SM, at most.
+#ifndef GAPS_EMIT_WARPS_PER_SM
+#define GAPS_EMIT_WARPS_PER_SM 4
 #endif
 constexpr int kStepThreads = GAPS_STEP_THREADS;
 
@@ -169,11 +168,11 @@ __device__ __forceinline__ int64_t warp_append_slot(bool flag, unsigned long lon
 // widens L as the batch thins out, so the last, longest showers do not run
 // their whole trial loop in one thread.  The first blocks run
 // GenerateEmission for the accepted emissions of the previous launch,
-// tasks_in[0 .. n_tasks), an even share of at most one per thread per round
-// in full warps, refresh the dipoles they moved block-wide, and put their
-// events back in list_out.  They come first so that their long FP64 work
-// starts with the launch, beside the select blocks, instead of forming its
-// tail.  Blocks are small (GAPS_STEP_THREADS = 64): a block holds its slot on
+// tasks_in[0 .. n_tasks), one per thread in rounds of a block's worth taken
+// from a shared cursor (an SM whose other blocks run slower takes fewer
+// rounds), refresh the dipoles they moved block-wide, and put their events
+// back in list_out.  They come first so that their long FP64 work starts
+// with the launch, beside the select blocks, instead of forming its tail.  Blocks are small (GAPS_STEP_THREADS = 64): a block holds its slot on
 // the SM until its slowest warp is done, and the select warps' lengths vary
 // with their events' parton counts.  An event
 // with a pending emission is in no list, so it never runs two phases in one
@@ -249,14 +248,17 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
                     int64_t n_list, const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                     const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                     EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                    unsigned long long* reset_tasks, StepPublish pub) {
+                    unsigned long long* reset_tasks, unsigned long long* emit_cursor,
+                    unsigned long long* reset_cursor, StepPublish pub) {
   __shared__ EmitTask s_task[kStepThreads];
   __shared__ uint32_t s_jobs[kMaxRefresh * kStepThreads];
   __shared__ int s_njobs;
+  __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid == 0) {
     if (reset_list) *reset_list = 0ull;
     if (reset_tasks) *reset_tasks = 0ull;
+    if (reset_cursor) *reset_cursor = 0ull;
     if (pub.slot) {
       // the lengths are final: the launch that wrote them has finished
       volatile unsigned long long* w = pub.slot;
@@ -274,13 +276,17 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     return;
   }
   const int64_t len = n_tasks_dev ? min(n_tasks, static_cast<int64_t>(*n_tasks_dev)) : n_tasks;
-  // each block's share: a whole number of warps, at most one block's worth
-  const int64_t share = min(static_cast<int64_t>(kStepThreads), ((len + emit_blocks - 1) / emit_blocks + 31) / 32 * 32);
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * share; base < len; base += emit_blocks * share) {
-    __syncthreads();  // the previous round is done with s_task and s_jobs
-    if (tid == 0) s_njobs = 0;
+  for (;;) {
+    __syncthreads();  // the previous round is done with s_task, s_jobs and s_base
+    if (tid == 0) {
+      s_njobs = 0;
+      s_base = atomicAdd(emit_cursor, static_cast<unsigned long long>(kStepThreads));
+    }
+    __syncthreads();
+    const int64_t base = static_cast<int64_t>(s_base);
+    if (base >= len) break;
     const int64_t k = base + tid;
-    const bool has = tid < share && k < len;
+    const bool has = k < len;
     if (has) s_task[tid] = tasks_in[k];
     __syncthreads();
     if (has) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
@@ -376,19 +382,20 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
                                  const unsigned long long* n_list_dev, const EmitTask* tasks_in, int64_t n_tasks,
                                  const unsigned long long* n_tasks_dev, int* list_out, unsigned long long* list_count,
                                  EmitTask* tasks_out, unsigned long long* task_count, unsigned long long* reset_list,
-                                 unsigned long long* reset_tasks, StepPublish pub, cudaStream_t s) {
+                                 unsigned long long* reset_tasks, unsigned long long* emit_cursor,
+                                 unsigned long long* reset_cursor, StepPublish pub, cudaStream_t s) {
   // The list length may be read on the device; n_list then bounds it, and
   // the lanes per event follow from the bound (at most one step narrower
   // than the exact length would give, since the bound is one or two launches
   // old).  The select grid covers n_list x lanes threads in one pass; the
-  // emission blocks share the tasks, at least a warp's worth each and at
-  // most GAPS_EMIT_BLOCKS_PER_SM blocks per SM, so that every SM starts with
-  // about the same FP64 load.
+  // emission blocks take the tasks in rounds from a cursor, at most
+  // GAPS_EMIT_WARPS_PER_SM warps per SM, so that every SM starts with about
+  // the same FP64 load and the rest goes to the SMs that free up first.
   const int64_t resident = resident_threads();
   const int lanes = lanes_for(n_list, resident);
   const int64_t select_blocks = (n_list * lanes + kStepThreads - 1) / kStepThreads;
-  const int64_t emit_per_sm = std::max(1, 256 * GAPS_EMIT_BLOCKS_PER_SM / kStepThreads);
-  const int64_t emit_blocks = std::min((n_tasks + 31) / 32, resident / 1024 * emit_per_sm);
+  const int64_t emit_per_sm = std::max(1, 32 * GAPS_EMIT_WARPS_PER_SM / kStepThreads);
+  const int64_t emit_blocks = std::min((n_tasks + kStepThreads - 1) / kStepThreads, resident / 1024 * emit_per_sm);
   if (select_blocks + emit_blocks == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>(select_blocks + emit_blocks);
 #define GAPS_DEFERRED_CASE(MULTI, LN)                                                                     \
@@ -396,7 +403,7 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
     k_step_deferred<MULTI, LN><<<grid, kStepThreads, 0, s>>>(P, E, select_blocks, list_in, n_list, n_list_dev, \
                                                              tasks_in, n_tasks, n_tasks_dev, list_out,         \
                                                              list_count, tasks_out, task_count, reset_list,    \
-                                                             reset_tasks, pub);                                \
+                                                             reset_tasks, emit_cursor, reset_cursor, pub);     \
     break;
 #define GAPS_DEFERRED_SWITCH(MULTI)  \
   switch (lanes) {                   \
