@@ -42,6 +42,8 @@ struct DevParams {
   double ln_tc;                       // ln t_C
   double ln_s;                        // ln s, the starting scale of the evolution variable
   double inv_4tc;                     // 1 / (4 t_C)
+  // event weight n_f 2 dsigma/dcos of flavour f: me_a[f-1] (1 + cos^2) + me_b[f-1] cos
+  double me_a[5], me_b[5];
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
   // FP32 copies used by the screens
   float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;
@@ -291,8 +293,10 @@ __device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, d
 
 // d sigma / d cos(theta) for e+e- -> q qbar (flavour f, PDG 1..5) at LO with
 // photon and Z exchange and their interference, in pb; theta is the quark's
-// angle to the electron beam.
-__device__ __forceinline__ double dsigma_dcos(double s, int f, double cth) {
+// angle to the electron beam.  It is a (1 + cos^2) + b cos: dsigma_parts gives
+// a and b (the host tabulates them per job and flavour, the matrix-element
+// kernel evaluates the quadratic).
+__host__ __device__ inline void dsigma_parts(double s, int f, double* a, double* b) {
   const bool up = (f == 2 || f == 4);
   const double qf = up ? 2.0 / 3.0 : -1.0 / 3.0;
   const double af = up ? 0.5 : -0.5;
@@ -305,7 +309,9 @@ __device__ __forceinline__ double dsigma_dcos(double s, int f, double cth) {
   const double chi2 = kappa * kappa * s * s / den;
   const double even = qe * qe * qf * qf + 2.0 * qe * qf * ve * vf * chi1 + (ae * ae + ve * ve) * (af * af + vf * vf) * chi2;
   const double odd = 2.0 * qe * qf * ae * af * chi1 + 4.0 * ae * ve * af * vf * chi2;
-  return kPi * kAlphaQED * kAlphaQED / (2.0 * s) * kNc * ((1.0 + cth * cth) * even + 2.0 * cth * odd) * kGeV2ToPb;
+  const double pref = kPi * kAlphaQED * kAlphaQED / (2.0 * s) * kNc * kGeV2ToPb;
+  *a = pref * even;
+  *b = pref * 2.0 * odd;
 }
 
 }  // namespace gaps

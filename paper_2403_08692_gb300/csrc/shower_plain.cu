@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
   const DipoleEntry d = make_dipole(P, 2.0 * mdot(q, qbar));
   store_dipole(E, ev, 0, 0, d);
   store_dipole(E, ev, 1, 1, d);
-  E.weight[ev] = P.nf * 2.0 * dsigma_dcos(P.s, fl, cth);
+  E.weight[ev] = fma(P.me_a[fl - 1], fma(cth, cth, 1.0), P.me_b[fl - 1] * cth);
   E.me_flavour[ev] = fl;
   E.t[ev] = P.s;  // starting scale t0 = s
   E.lnt[ev] = P.ln_s;
