@@ -1,10 +1,11 @@
 // Persistent shower form: one launch runs every event to the cutoff.
 //
 // Each block keeps a pool of events, one per thread.  It runs `period` veto
-// cycles on the pool (select/veto for every live event, then the accepted
-// emissions by packed threads), then compacts the still-active events to the
-// front of the pool with a warp ballot and refills the freed threads from a
-// global event cursor (one atomic per block per round).  Events therefore
+// cycles on the pool (select/veto for every live event, each warp on its own
+// events with no block barrier), generates the period's accepted emissions
+// in packed threads, then compacts the still-active events to the front of
+// the pool with a warp ballot and refills the freed threads from a global
+// event cursor (one atomic per block per round).  Events therefore
 // leave as soon as they finish -- the paper's cutoff inefficiency (Sec. 2,
 // Fig. 3: finished events wait for the last one) disappears -- and no
 // lane is spent on a finished event for more than `period` cycles.
@@ -38,14 +39,10 @@ __device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
   }
 }
 
-// Launch shape knobs: resident threads per SM the register budget is set for
-// (0: no bound), and the queued emissions that trigger a flush before the
-// end of a compaction period.
+// Launch shape knob: resident threads per SM the register budget is set for
+// (0: no bound).
 #ifndef GAPS_PERSIST_THREADS_PER_SM
 #define GAPS_PERSIST_THREADS_PER_SM 1024
-#endif
-#ifndef GAPS_PERSIST_FLUSH
-#define GAPS_PERSIST_FLUSH 32
 #endif
 constexpr int persist_min_blocks(int t) {
   return GAPS_PERSIST_THREADS_PER_SM > 0 && GAPS_PERSIST_THREADS_PER_SM / t > 0 ? GAPS_PERSIST_THREADS_PER_SM / t : 1;
@@ -124,10 +121,13 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
       s_count[1] = 0;
       s_count[4] = 0;
     }
+    __syncthreads();
+    // `period` veto cycles with no block barrier: each warp runs its own
+    // events, and a cycle's cost is the warp's, not the slowest warp's.  An
+    // event whose emission waits in the queue skips its remaining selects of
+    // the period (its draws are keyed by its own cycle).
     for (int c = 0; c < period; ++c) {
-      __syncthreads();
-      // An event whose emission waits in the queue skips its next selects
-      // until the queue is flushed (its draws are keyed by its own cycle).
+      __syncwarp();  // the group's first lane wrote s_alive / s_cyc last cycle
       bool live = g < pool && s_alive[g] == kSlotLive;
       if constexpr (kSlice) live = live && s_cyc[g] < sl.cycles;
       const int64_t ev = live ? s_pool[g] : -1;
@@ -165,23 +165,18 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
         }
       }
-      __syncthreads();
-      // Flush the queued emissions once enough have gathered to fill warps,
-      // and always before the pool is compacted.  (Compacting early, once an
-      // eighth of the pool had finished, measured no faster.)
-      const int queued = s_count[1];
-      if (queued == 0 || (queued < GAPS_PERSIST_FLUSH && c + 1 < period)) continue;
+    }
+    __syncthreads();
+    // GenerateEmission for the period's accepted emissions, in full warps,
+    // before the pool is compacted (at most one per event: queued <= T).
+    const int queued = s_count[1];
+    if (queued > 0) {
       if (tid < queued) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
       __syncthreads();
       for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
       if (tid < queued) s_alive[s_task[tid].pad0 | (s_task[tid].pad1 << 8)] = kSlotLive;
       __syncthreads();
-      if (tid == 0) {
-        s_count[1] = 0;
-        s_count[4] = 0;
-      }
     }
-    __syncthreads();
 
     // Compact: the still-active events move to the front of the pool; in a
     // slice, those that have run their cycles leave for list_out.
