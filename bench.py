@@ -45,17 +45,16 @@ WORK_PER_EMISSION = {"simple": 164, "div": 18, "sqrt": 7, "log": 4, "exp": 2, "s
 DFMA_PER_SM_PER_CLOCK = 2
 
 
-def step_kernel_traffic(event_cycles_per_launch):
-    """DRAM bytes per launch of the plain-form step kernel: the per-event-cycle
-    traffic of the committed ncu capture (all step launches of one pass, the
-    deferred emissions included) times this run's event-cycles per launch;
-    None once the kernel sources differ from the captured ones."""
+def step_kernel_profile():
+    """Figures of the committed ncu captures of the plain-form step kernel
+    (profiles/k_step_deferred_500k.md): DRAM bytes per event-cycle of a whole
+    pass and the FP64-pipe, issue-slot and SM-active fractions of mid-shower
+    launches; None once the kernel sources differ from the captured ones."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", "k_step_deferred_500k.md")
     try:
         text = open(path).read()
-        per_unit = float(re.search(r"dram_bytes_per_event_cycle:\s*([0-9.]+)", text).group(1))
         want = re.search(r"source_sha256:\s*([0-9a-f]+)", text).group(1)
         files = re.search(r"sources:\s*(.+)", text).group(1).split()
         h = hashlib.sha256()
@@ -63,9 +62,31 @@ def step_kernel_traffic(event_cycles_per_launch):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if h.hexdigest() != want:
             return None
-        return per_unit * event_cycles_per_launch
+        keys = ("dram_bytes_per_event_cycle", "fp64_pipe_active_frac", "issue_active_frac", "sm_active_frac")
+        return {k: float(re.search(k + r":\s*([0-9.]+)", text).group(1)) for k in keys}
     except (OSError, AttributeError, ValueError):
         return None
+
+
+def step_kernel_traffic(event_cycles_per_launch):
+    """DRAM bytes per launch of the plain-form step kernel: the per-event-cycle
+    traffic of the committed ncu capture (all step launches of one pass, the
+    deferred emissions included) times this run's event-cycles per launch;
+    None once the kernel sources differ from the captured ones."""
+    prof = step_kernel_profile()
+    return None if prof is None else prof["dram_bytes_per_event_cycle"] * event_cycles_per_launch
+
+
+def pipe_fractions():
+    """The FP64-pipe and issue-slot fractions of the step kernel (ncu, two
+    mid-shower launches at 5x10^5 events), as the profile records them."""
+    prof = step_kernel_profile()
+    if prof is None:
+        return None
+    return {"fp64_pipe_of_active_cycles": prof["fp64_pipe_active_frac"],
+            "issue_slots_of_active_cycles": prof["issue_active_frac"],
+            "sm_active_of_elapsed_cycles": prof["sm_active_frac"],
+            "source": "profiles/k_step_deferred_500k.md (ncu --set full, launches 21-22 of a 5x10^5-event pass)"}
 
 
 def dfma_equivalents(counts, rates):
@@ -678,6 +699,7 @@ def main():
                      "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
                      "traffic_source": "profiles/k_step_deferred_500k.md: DRAM bytes per event-cycle from one ncu "
                                        "capture x this run's event-cycles per launch",
+                     "pipes": pipe_fractions(),
                      "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "
                                     f"x {clock_mhz:.0f} MHz (median SM clock under load) x 2 flops; "
                                     f"MEASURED_PEAKS.json has no FP64 entry",
