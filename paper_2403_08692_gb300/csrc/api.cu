@@ -94,6 +94,7 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   d.s = p.sqrt_s * p.sqrt_s;
   d.tc = p.t_cutoff;
   d.inv_4tc = 1.0 / (4.0 * p.t_cutoff);
+  d.inv_s = 1.0 / d.s;
   for (int f = 1; f <= 5; ++f) {
     double a = 0.0, b = 0.0;
     dsigma_parts(d.s, f, &a, &b);

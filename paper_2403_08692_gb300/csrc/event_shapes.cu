@@ -21,6 +21,9 @@
 //    per-pair error bound; every pair that could be the minimum is evaluated
 //    with the FP64 formula 2 min(E_i^2, E_j^2)(1 - cos theta_ij)/s, and the
 //    smallest of those is merged, ties to the first pair as in the oracle.
+//  * Final scalings take reciprocals (1/s, 1/|P|, 1/(2 sum |p|)): the
+//    oracle's divisions up to an ulp.  The cosine inside Durham's 1 - cos
+//    keeps the oracle's division, since 1 - cos magnifies its rounding.
 #include "gaps_launch.hpp"
 
 namespace gaps {
@@ -73,10 +76,10 @@ __device__ double thrust_fp64(int n, const double* jx, const double* jy, const d
     az = jz[0] / l;
     return 1.0;
   }
-  const double l = sqrt(best2);
-  ax = bx / l;
-  ay = by / l;
-  az = bz / l;
+  const double l = sqrt(best2), inv_l = 1.0 / l;
+  ax = bx * inv_l;
+  ay = by * inv_l;
+  az = bz * inv_l;
   return l / sum_abs;
 }
 
@@ -180,11 +183,11 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
         py += sg * jy[i];
         pz += sg * jz[i];
       }
-      const double l = sqrt(px * px + py * py + pz * pz);
+      const double l = sqrt(px * px + py * py + pz * pz), inv_l = 1.0 / l;
       thrust = l / sum_abs;
-      ax = px / l;
-      ay = py / l;
-      az = pz / l;
+      ax = px * inv_l;
+      ay = py * inv_l;
+      az = pz * inv_l;
       decided = true;
     }
   }
@@ -215,9 +218,10 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
   const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
   E.obs[4 * E.stride + ev] = 1.0 - thrust;
-  E.obs[5 * E.stride + ev] = fmax(mp, mm) / P.s;
-  bp /= 2.0 * sum_abs;
-  bm /= 2.0 * sum_abs;
+  E.obs[5 * E.stride + ev] = fmax(mp, mm) * P.inv_s;
+  const double inv_2sum = 0.5 / sum_abs;
+  bp *= inv_2sum;
+  bm *= inv_2sum;
   E.obs[6 * E.stride + ev] = bp + bm;
   E.obs[7 * E.stride + ev] = fmax(bp, bm);
 
@@ -235,7 +239,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   // y of jets i, j with the oracle's FP64 formula (|p| cached per jet).
   auto y_exact = [&](int i, int j) {
     const double cosij = (jx[i] * jx[j] + jy[i] * jy[j] + jz[i] * jz[j]) / (ja[i] * ja[j]);
-    return 2.0 * fmin(je[i] * je[i], je[j] * je[j]) * (1.0 - cosij) / P.s;
+    return 2.0 * fmin(je[i] * je[i], je[j] * je[j]) * (1.0 - cosij) * P.inv_s;
   };
   for (int m = n; m > 1; --m) {
     // pass 1: the smallest upper bound of the FP32 distances, and its pair

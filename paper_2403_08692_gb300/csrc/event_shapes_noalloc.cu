@@ -89,6 +89,7 @@ extern "C" int gaps_event_shapes_noalloc(const double* px, const double* py, con
   DevParams P{};
   P.sqrt_s = sqrt_s;
   P.s = sqrt_s * sqrt_s;
+  P.inv_s = 1.0 / P.s;
   err = launch_observables(P, E, scratch->buckets, scratch->order, static_cast<cudaStream_t>(stream));
   return err == cudaSuccess ? GAPS_OK : record_cuda_error(err);
 }

@@ -42,6 +42,7 @@ struct DevParams {
   double ln_tc;                       // ln t_C
   double ln_s;                        // ln s, the starting scale of the evolution variable
   double inv_4tc;                     // 1 / (4 t_C)
+  double inv_s;                       // 1 / s
   // event weight n_f 2 dsigma/dcos of flavour f: me_a[f-1] (1 + cos^2) + me_b[f-1] cos
   double me_a[5], me_b[5];
   double inv_as2pi_2cf, inv_as2pi_ca;  // 1 / (alpha_s^over/(2 pi) K) of q->qg and g->gg
