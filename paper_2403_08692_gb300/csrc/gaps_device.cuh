@@ -180,10 +180,16 @@ __device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, ui
 }
 
 // 52-bit uniform strictly inside (0, 1): the top 26 bits of each word, plus
-// one half, times 2^-52 (exact in binary64).
+// one half, times 2^-52, i.e. (2m + 1) 2^-53 -- exact in binary64, so its
+// bits are assembled with integer instructions (the FP64 pipe's conversions
+// and adds cost as much as its FMAs on this part).
 __device__ __forceinline__ double to_unit(uint32_t hi, uint32_t lo) {
   const unsigned long long m = (static_cast<unsigned long long>(hi >> 6) << 26) | (lo >> 6);
-  return (static_cast<double>(m) + 0.5) * 0x1p-52;
+  const unsigned long long odd = (m << 1) | 1ull;  // < 2^53
+  const int top = 63 - __clzll(static_cast<long long>(odd));
+  const unsigned long long bits = (static_cast<unsigned long long>(top - 53 + 1023) << 52) |
+                                  ((odd << (52 - top)) & ((1ull << 52) - 1ull));
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 struct Uniforms {
