@@ -401,6 +401,10 @@ int gaps_probe_fp64_rates(double* device_sink, double* host_rates, void* stream)
  * arrays, asynchronous on `stream`.  Both return GAPS_ERR_INVALID for n < 0
  * or a null array with n > 0.  Exported for the accuracy tests. */
 int gaps_log_fp64_host(const double* x, double* y, int64_t n);
+/* The double -> float conversion (round to nearest even) the kernels do with
+ * integer instructions, host build, for the tests: y[i] = (float) x[i].
+ * GAPS_ERR_INVALID for n < 0 or a null array with n > 0. */
+int gaps_f32_from_f64_host(const double* x, float* y, int64_t n);
 int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream);
 const char* gaps_strerror(int status);
 const char* gaps_last_cuda_error(void);

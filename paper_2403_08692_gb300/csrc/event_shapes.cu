@@ -117,13 +117,13 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     jx[i] = E.px[a];
     jy[i] = E.py[a];
     jz[i] = E.pz[a];
-    fx[i] = static_cast<float>(jx[i]);
-    fy[i] = static_cast<float>(jy[i]);
-    fz[i] = static_cast<float>(jz[i]);
+    fx[i] = f32_from_f64(jx[i]);
+    fy[i] = f32_from_f64(jy[i]);
+    fz[i] = f32_from_f64(jz[i]);
     ja[i] = sqrt(jx[i] * jx[i] + jy[i] * jy[i] + jz[i] * jz[i]);
     sum_abs += ja[i];
   }
-  sum_absf = static_cast<float>(sum_abs);
+  sum_absf = f32_from_f64(sum_abs);
 
   // ---- thrust
   double thrust = 1.0, ax = 0.0, ay = 0.0, az = 0.0;
@@ -228,7 +228,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   // ---- Durham (E-scheme)
   float fe2[MAXJ];
   for (int i = 0; i < n; ++i) {
-    const float e = static_cast<float>(je[i]);
+    const float e = f32_from_f64(je[i]);
     fe2[i] = e * e;
     const float r = rsqrtf(fx[i] * fx[i] + fy[i] * fy[i] + fz[i] * fz[i]);
     fx[i] *= r;  // from here on fx, fy, fz hold unit directions
@@ -314,9 +314,9 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     fy[bj] = fy[m - 1];
     fz[bj] = fz[m - 1];
     {
-      const float e = static_cast<float>(je[bi]);
+      const float e = f32_from_f64(je[bi]);
       fe2[bi] = e * e;
-      const float x = static_cast<float>(jx[bi]), y = static_cast<float>(jy[bi]), z = static_cast<float>(jz[bi]);
+      const float x = f32_from_f64(jx[bi]), y = f32_from_f64(jy[bi]), z = f32_from_f64(jz[bi]);
       const float r = rsqrtf(x * x + y * y + z * z);
       fx[bi] = x * r;
       fy[bi] = y * r;

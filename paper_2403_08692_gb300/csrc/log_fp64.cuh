@@ -31,6 +31,39 @@
 
 namespace gaps {
 
+// double -> float, round to nearest even, with integer instructions for
+// every result in the normal float range (the FP64 pipe's conversion costs
+// as much as an FMA on this part; the ALU's instructions a small fraction of
+// that); zeros, tiny, huge and non-finite values take the hardware
+// conversion.  Bitwise the hardware result (tested against numpy's).
+__host__ __device__ __forceinline__ float f32_from_f64(double x) {
+#ifdef __CUDA_ARCH__
+  const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(x));
+#else
+  uint64_t bits;
+  std::memcpy(&bits, &x, sizeof bits);
+#endif
+  const uint64_t mag = bits & 0x7fffffffffffffffull;
+  // exponent field 897 .. 1150: normal floats, before rounding
+  if (mag - 0x3810000000000000ull >= 0x0fe0000000000000ull) {
+#ifdef __CUDA_ARCH__
+    return __double2float_rn(x);
+#else
+    return static_cast<float>(x);
+#endif
+  }
+  const uint64_t rounded = mag + 0x0fffffffull + ((mag >> 29) & 1ull);  // ties to even at bit 29
+  const uint32_t out = static_cast<uint32_t>((rounded >> 29) - (uint64_t{896} << 23)) |
+                       static_cast<uint32_t>((bits >> 32) & 0x80000000u);
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(out);
+#else
+  float f;
+  std::memcpy(&f, &out, sizeof f);
+  return f;
+#endif
+}
+
 struct alignas(32) LogEntry {
   double f, inv_f, ln_hi, ln_lo;  // 32 bytes: one sector
 };
@@ -83,7 +116,22 @@ __host__ __device__ __forceinline__ double log_fp64(double x) {
   q = fma(q, r, 1.0 / 3.0);
   q = fma(q, r, -0.5);
   const double r2 = r * r;
-  const double ed = static_cast<double>(e);
+  double ed = 0.0;  // (double) e, from its bits (|e| < 2^11, exact)
+  if (e != 0) {
+    const uint32_t a = static_cast<uint32_t>(e < 0 ? -e : e);
+#ifdef __CUDA_ARCH__
+    const int top = 31 - __clz(static_cast<int>(a));
+#else
+    const int top = 31 - __builtin_clz(a);
+#endif
+    const uint64_t ebits = (static_cast<uint64_t>(e < 0) << 63) | (static_cast<uint64_t>(top + 1023) << 52) |
+                           ((static_cast<uint64_t>(a) << (52 - top)) & ((uint64_t{1} << 52) - 1));
+#ifdef __CUDA_ARCH__
+    ed = __longlong_as_double(static_cast<long long>(ebits));
+#else
+    std::memcpy(&ed, &ebits, sizeof ed);
+#endif
+  }
   const double hi = fma(ed, GAPS_LOG_LN2_HI, ln_hi);  // exact
   // the small parts first, r (the largest of them, unrounded) next, hi last
   const double small = fma(r2, q, fma(ed, GAPS_LOG_LN2_LO, ln_lo));

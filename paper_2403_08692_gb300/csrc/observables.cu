@@ -125,9 +125,9 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
   float f;
   if (h < 4) {
     if (!(o > 0.0)) return -1;
-    f = (__log2f(static_cast<float>(o)) * 0.30102999566f + 4.3f) * 25.0f;
+    f = (__log2f(f32_from_f64(o)) * 0.30102999566f + 4.3f) * 25.0f;
   } else {
-    f = (o > 0.0 ? static_cast<float>(o) : 0.0f) * (h < 6 ? 200.0f : 250.0f);
+    f = (o > 0.0 ? f32_from_f64(o) : 0.0f) * (h < 6 ? 200.0f : 250.0f);
   }
   const float fr = f - floorf(f);
   if (!(fr > 1e-3f && fr < 1.0f - 1e-3f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);

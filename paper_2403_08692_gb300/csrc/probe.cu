@@ -129,6 +129,12 @@ extern "C" int gaps_log_fp64_host(const double* x, double* y, int64_t n) {
   return GAPS_OK;
 }
 
+extern "C" int gaps_f32_from_f64_host(const double* x, float* y, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return GAPS_ERR_INVALID;
+  for (int64_t k = 0; k < n; ++k) y[k] = f32_from_f64(x[k]);
+  return GAPS_OK;
+}
+
 extern "C" int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return GAPS_ERR_INVALID;
   if (n == 0) return GAPS_OK;

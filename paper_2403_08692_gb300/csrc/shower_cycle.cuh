@@ -85,8 +85,8 @@ __device__ __forceinline__ DipoleEntry make_dipole(const DevParams& P, double q2
   d.zp = 0.5 * b1;
   const double ls = log_fp64((b1 * b1) * (q2 * P.inv_4tc));
   d.inv_ls = 1.0 / ls;
-  d.screen = make_float2(1.0f / (P.as2pi_f * static_cast<float>(ls)),
-                         1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * static_cast<float>(2.0 * d.zp - 1.0)));
+  d.screen = make_float2(1.0f / (P.as2pi_f * f32_from_f64(ls)),
+                         1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * f32_from_f64(2.0 * d.zp - 1.0)));
   return d;
 }
 
@@ -374,7 +374,7 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   E.n_dipoles[ev] += sc.dipoles;
 
   // Cutoff threshold in key units: t' > t_C  <=>  key > log2(t_C / t).
-  const float lt2 = static_cast<float>(lnt) * 1.44269504f;
+  const float lt2 = f32_from_f64(lnt) * 1.44269504f;
   const float thr = P.lg2_tc_f - lt2;
   const float thr_m = 2e-6f * (1.0f + fabsf(lt2) + fabsf(P.lg2_tc_f));
 
@@ -429,9 +429,9 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   const U4 rw = philox10(id, static_cast<uint32_t>(step), 0u, kDrawWinner, P.seed_lo, P.seed_hi);
   bool accept;
   {
-    const float zpf = static_cast<float>(task.zp);
-    const float zmf = static_cast<float>(1.0 - task.zp);
-    const float lf = 1.0f / static_cast<float>(task.inv_ls);
+    const float zpf = f32_from_f64(task.zp);
+    const float zmf = f32_from_f64(1.0 - task.zp);
+    const float lf = 1.0f / f32_from_f64(task.inv_ls);
     const float rzf = unit_float(rw.x, rw.y);
     float z, e;  // z and 1 - z
     if (task.kind == kGtoQQ) {
@@ -441,8 +441,8 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
       z = zmf - zpf * expm1f(-rzf * lf);
       e = zpf * __expf(-rzf * lf);
     }
-    const float lnt_f = static_cast<float>(task.lnt);
-    const float y = __expf(lnt_f) / (static_cast<float>(task.q2) * z * e);
+    const float lnt_f = f32_from_f64(task.lnt);
+    const float y = __expf(lnt_f) / (f32_from_f64(task.q2) * z * e);
     const float as_ratio = P.fixed ? 1.0f : P.as_mz_over_f / (1.0f + P.as_b0_f * (lnt_f - P.ln_mz2_f));
     float pr;  // P(z, y) / P^over(z)
     if (task.kind == kQtoQG) {

@@ -91,6 +91,7 @@ SIGNATURES = {
                                             C.c_void_p]),
     "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
     "gaps_log_fp64_host": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64]),
+    "gaps_f32_from_f64_host": (C.c_int, [_P(C.c_double), _P(C.c_float), C.c_int64]),
     "gaps_log_fp64_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "gaps_pool_reset": (C.c_int, [_P(Batch), C.c_void_p]),
     "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
@@ -271,6 +272,17 @@ def log_fp64_host(x):
     y = np.empty_like(x)
     _check(load().gaps_log_fp64_host(x.ctypes.data_as(_P(C.c_double)), y.ctypes.data_as(_P(C.c_double)),
                                      int(x.size)), "gaps_log_fp64_host")
+    return y
+
+
+def f32_from_f64_host(x):
+    """The kernels' integer double -> float conversion on a float64 numpy
+    array (host code)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(x.shape, dtype=np.float32)
+    _check(load().gaps_f32_from_f64_host(x.ctypes.data_as(_P(C.c_double)), y.ctypes.data_as(_P(C.c_float)),
+                                         int(x.size)), "gaps_f32_from_f64_host")
     return y
 
 

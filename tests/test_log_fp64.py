@@ -80,3 +80,27 @@ def test_bad_arguments(g):
     assert lib.gaps_log_fp64_host(None, None, -1) != 0
     assert lib.gaps_log_fp64_host(None, None, 5) != 0
     assert lib.gaps_log_fp64_host(None, None, 0) == 0
+
+
+def test_f32_from_f64_is_round_to_nearest_even(g):
+    """The kernels' integer double -> float conversion equals numpy's (IEEE
+    round to nearest even) on random doubles of every magnitude, on ties
+    (the dropped 29 bits exactly one half), on values that round up into
+    the next binade or to infinity, and on the special values."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([
+        rng.standard_normal(100_000) * np.exp(rng.uniform(-100.0, 100.0, 100_000)),
+        np.exp(rng.uniform(-745.0, 709.0, 20_000)) * rng.choice([-1.0, 1.0], 20_000),
+    ])
+    f = rng.standard_normal(20_000).astype(np.float32).astype(np.float64)
+    ties = np.abs(f) * (1.0 + 2.0**-24)                         # exactly half an FP32 ulp above
+    ties2 = np.nextafter(np.abs(f).astype(np.float32), np.float32(np.inf)).astype(np.float64) * (1.0 - 2.0**-25)
+    edge = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, 1e-40, 1.1754942e-38, 1.1754944e-38,
+                     3.4028234e38, 3.4028235e38, 3.40282357e38, 1e39, -1e39, 2.0**-126, 2.0**-127,
+                     np.nextafter(2.0, 0.0), 1.0 - 2.0**-25, 1.0 - 2.0**-26])
+    x = np.concatenate([x, ties, ties2, edge])
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32)
+    got = g.f32_from_f64_host(x)
+    assert np.array_equal(got.view(np.uint32)[~np.isnan(want)], want.view(np.uint32)[~np.isnan(want)])
+    assert np.isnan(got[np.isnan(want)]).all()
