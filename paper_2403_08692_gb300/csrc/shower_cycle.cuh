@@ -81,12 +81,16 @@ __device__ __forceinline__ DipoleEntry make_dipole(const DevParams& P, double q2
     d.screen = make_float2(-1.0f, -1.0f);
     return d;
   }
-  const double b1 = 1.0 + sqrt(1.0 - 4.0 * P.tc / q2);
+  // b = sqrt(1 - 4 t_C/Q^2) = a / sqrt(Q^2 a) with a = Q^2 - 4 t_C: one
+  // reciprocal square root instead of a division and a square root
+  const double a = q2 - 4.0 * P.tc;
+  const double b = __double_as_longlong(a) > 0 ? a * rsqrt(q2 * a) : 0.0;  // a > 0, tested on the bits
+  const double b1 = 1.0 + b;
   d.zp = 0.5 * b1;
   const double ls = log_fp64((b1 * b1) * (q2 * P.inv_4tc));
   d.inv_ls = 1.0 / ls;
   d.screen = make_float2(1.0f / (P.as2pi_f * f32_from_f64(ls)),
-                         1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * f32_from_f64(2.0 * d.zp - 1.0)));
+                         1.0f / (P.as2pi_f * 0.5f * static_cast<float>(kTR) * f32_from_f64(b)));
   return d;
 }
 
