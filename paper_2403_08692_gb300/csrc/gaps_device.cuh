@@ -260,22 +260,25 @@ __device__ __forceinline__ double det3(double a1, double a2, double a3, double b
 // spacelike vectors orthogonal to a, b and each other: n1 projects the
 // first of the references (1,1,0,0), (1,0,1,0), (1,0,0,1) whose projection
 // has |n1^2| >= 1e-4, n2 is the Minkowski-orthogonal complement of (a, b,
-// n1) (cofactor expansion of det[X; a; b; n1]).  The projections share one
-// reciprocal of a.b and both normalisations take the library's rsqrt (one
-// ulp), the oracle's 1/sqrt up to rounding.
+// n1) (cofactor expansion of det[X; a; b; n1]).  n1 is formed scaled by a.b
+// (no division) and both normalisations take the library's rsqrt (one ulp):
+// the oracle's vectors up to rounding.
 __device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, double y, double cphi,
                                            double sphi, V4& pi, V4& pj, V4& pb) {
   const double ab = mdot(a, b);
   const double q2 = 2.0 * ab;
-  const double inv_ab = 1.0 / ab;
+  // n1 scaled by a.b (a.b > 0): ab ref - (ref.b) a - (ref.a) b, so no
+  // division; the reference test |n1^2| >= 1e-4 becomes |(ab n1)^2| >=
+  // 1e-4 ab^2, and the normalisation below removes the scale.
+  const double lim = 1e-4 * ab * ab;
   V4 n1{0, 0, 0, 0};
   for (int r = 0; r < 3; ++r) {
     const V4 ref{1.0, r == 0 ? 1.0 : 0.0, r == 1 ? 1.0 : 0.0, r == 2 ? 1.0 : 0.0};
-    const double cb = mdot(ref, b) * inv_ab;
-    const double ca = mdot(ref, a) * inv_ab;
-    n1 = V4{ref.e - cb * a.e - ca * b.e, ref.x - cb * a.x - ca * b.x, ref.y - cb * a.y - ca * b.y,
-            ref.z - cb * a.z - ca * b.z};
-    if (fabs(mdot(n1, n1)) >= 1e-4) break;
+    const double cb = mdot(ref, b);
+    const double ca = mdot(ref, a);
+    n1 = V4{ab - cb * a.e - ca * b.e, (r == 0 ? ab : 0.0) - cb * a.x - ca * b.x,
+            (r == 1 ? ab : 0.0) - cb * a.y - ca * b.y, (r == 2 ? ab : 0.0) - cb * a.z - ca * b.z};
+    if (fabs(mdot(n1, n1)) >= lim) break;
   }
   const double s1 = rsqrt(-mdot(n1, n1));
   n1 = V4{n1.e * s1, n1.x * s1, n1.y * s1, n1.z * s1};
