@@ -294,13 +294,14 @@ int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mo
 
 /* The persistent form (Sec. 2, without the cutoff wait of Fig. 3): one
  * launch runs every event to the cutoff.  Each block keeps a pool of events,
- * runs cfg->compact_period veto cycles on it (each warp on its own events,
- * no block barrier), generates the period's accepted emissions together,
- * packs the still-active events to the front (warp ballot) and refills the
- * free threads from a global event cursor.  An event with a queued emission
- * skips its selects until the end of the period.  Events are identical to
- * the plain form's (same draws, same cycle code).  cfg = NULL uses
- * {128, 4, 0}.  Fully asynchronous: no host synchronisation; the
+ * two per thread for pools of up to 256 threads, runs cfg->compact_period
+ * veto cycles on it (each warp on its own events, no block barrier; a
+ * thread runs whichever of its events can run), generates the period's
+ * accepted emissions together, packs the still-active events to the front
+ * (warp ballot) and refills the free slots from a global event cursor.  An
+ * event with a queued emission skips its selects until the end of the
+ * period.  Events are identical to the plain form's (same draws, same cycle
+ * code).  cfg = NULL uses {128, 8, 0}.  Fully asynchronous: no host synchronisation; the
  * workspace counters record finished and step-limited events. */
 int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
                            const gaps_persistent_config* cfg, void* stream);

@@ -315,7 +315,7 @@ int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch,
 
 namespace {
 
-constexpr gaps_persistent_config kDefaultPersistent = {128, 4, 0, 0};
+constexpr gaps_persistent_config kDefaultPersistent = {128, 8, 0, 0};
 
 bool config_ok(const gaps_persistent_config& c) {
   const bool threads_ok = c.block_threads == 64 || c.block_threads == 128 || c.block_threads == 256 ||

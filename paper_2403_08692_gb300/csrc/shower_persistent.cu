@@ -1,11 +1,12 @@
 // Persistent shower form: one launch runs every event to the cutoff.
 //
-// Each block keeps a pool of events, one per thread.  It runs `period` veto
-// cycles on the pool (select/veto for every live event, each warp on its own
-// events with no block barrier), generates the period's accepted emissions
-// in packed threads, then compacts the still-active events to the front of
-// the pool with a warp ballot and refills the freed threads from a global
-// event cursor (one atomic per block per round).  Events therefore
+// Each block keeps a pool of events, two per thread (one for 512-thread
+// blocks).  It runs `period` veto cycles on the pool (select/veto for a
+// runnable event of every thread, each warp on its own events with no block
+// barrier), generates the period's accepted emissions in packed threads,
+// then compacts the still-active events to the front of the pool with warp
+// ballots and refills the freed slots from a global event cursor (one
+// atomic per block per round).  Events therefore
 // leave as soon as they finish -- the paper's cutoff inefficiency (Sec. 2,
 // Fig. 3: finished events wait for the last one) disappears -- and no
 // lane is spent on a finished event for more than `period` cycles.
@@ -67,14 +68,26 @@ struct SliceArgs {
   unsigned long long* out_count;
 };
 
+// Pool slots per thread.  With two, a thread runs whichever of its events
+// can run this cycle, so a lane idles only when both of its events have
+// finished or wait for their emission (with one, finished and waiting
+// events hold their lanes until the next compaction).  Shared memory bounds
+// a block's pool at 512 events.
+#ifndef GAPS_PERSIST_SLOTS
+#define GAPS_PERSIST_SLOTS 2
+#endif
+constexpr int persist_slots(int t) { return t * GAPS_PERSIST_SLOTS <= 512 ? GAPS_PERSIST_SLOTS : 1; }
+
 template <int T, int kMode, bool kSlice>
 __global__ void __launch_bounds__(T, persist_min_blocks(T))
     k_shower_persistent(DevParams P0, Events E, int period, SliceArgs sl) {
-  __shared__ int32_t s_pool[T];
-  __shared__ uint8_t s_alive[T];
-  __shared__ uint8_t s_cyc[kSlice ? T : 1];  // cycles run in this slice, per slot
-  __shared__ EmitTask s_task[T];
-  __shared__ uint32_t s_jobs[kMaxRefresh * T];
+  constexpr int S = persist_slots(T);
+  constexpr int kPool = S * T;  // events of the block's pool
+  __shared__ int32_t s_pool[kPool];
+  __shared__ uint8_t s_alive[kPool];
+  __shared__ uint8_t s_cyc[kSlice ? kPool : 1];  // cycles run in this slice, per slot
+  __shared__ EmitTask s_task[kPool];
+  __shared__ uint32_t s_jobs[kMaxRefresh * kPool];
   __shared__ int s_count[6];  // pool size, accepted emissions, lanes per event, refill count, refresh jobs, tail
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
@@ -83,11 +96,12 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
   int pool = 0;
   if (tid == 0) s_count[5] = 0;
   for (;;) {
-    // Refill the free threads from the global cursor.  Once the cursor has
-    // passed the last event the pool only shrinks, and its events get
-    // several lanes each (the last, longest showers).
+    // Refill the free slots from the global cursor.  Once the cursor has
+    // passed the last event the pool only shrinks, and once it fits in half
+    // the threads its events get several lanes each (the last, longest
+    // showers).
     if (tid == 0) {
-      const int want = T - pool;
+      const int want = kPool - pool;
       unsigned long long base = 0;
       int take = 0;
       if (want > 0 && s_count[5] == 0) {
@@ -105,13 +119,15 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     }
     __syncthreads();
     const int take = s_count[3];
-    if (tid >= pool && tid < pool + take) {
-      const int64_t k = static_cast<int64_t>(s_base) + (tid - pool);
-      s_pool[tid] = kSlice ? (sl.list_in ? sl.list_in[k] : static_cast<int32_t>(k)) : static_cast<int32_t>(k);
-      if constexpr (kSlice) s_cyc[tid] = 0;
+    for (int q = tid; q < kPool; q += T) {
+      if (q >= pool && q < pool + take) {
+        const int64_t k = static_cast<int64_t>(s_base) + (q - pool);
+        s_pool[q] = kSlice ? (sl.list_in ? sl.list_in[k] : static_cast<int32_t>(k)) : static_cast<int32_t>(k);
+        if constexpr (kSlice) s_cyc[q] = 0;
+      }
     }
     pool += take;
-    s_alive[tid] = tid < pool ? kSlotLive : kSlotDead;
+    for (int q = tid; q < kPool; q += T) s_alive[q] = q < pool ? kSlotLive : kSlotDead;
     __syncthreads();
     if (pool == 0) break;
     const int lanes = s_count[2];
@@ -125,12 +141,28 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     // `period` veto cycles with no block barrier: each warp runs its own
     // events, and a cycle's cost is the warp's, not the slowest warp's.  An
     // event whose emission waits in the queue skips its remaining selects of
-    // the period (its draws are keyed by its own cycle).
+    // the period (its draws are keyed by its own cycle).  With one lane per
+    // event a thread owns slots tid, tid + T, ... and runs the first that can
+    // run, starting from another slot each cycle; with several lanes (then
+    // pool <= T / 2 lanes) a group owns slot g.
     for (int c = 0; c < period; ++c) {
       __syncwarp();  // the group's first lane wrote s_alive / s_cyc last cycle
-      bool live = g < pool && s_alive[g] == kSlotLive;
-      if constexpr (kSlice) live = live && s_cyc[g] < sl.cycles;
-      const int64_t ev = live ? s_pool[g] : -1;
+      int slot = -1;
+      if (lanes == 1) {
+#pragma unroll
+        for (int o = 0; o < S; ++o) {
+          const int q = tid + ((c + o) % S) * T;
+          bool ok = slot < 0 && q < pool && s_alive[q] == kSlotLive;
+          if constexpr (kSlice) ok = ok && s_cyc[q] < sl.cycles;
+          if (ok) slot = q;
+        }
+      } else {
+        bool ok = g < pool && s_alive[g] == kSlotLive;
+        if constexpr (kSlice) ok = ok && s_cyc[g] < sl.cycles;
+        if (ok) slot = g;
+      }
+      const bool live = slot >= 0;
+      const int64_t ev = live ? s_pool[slot] : -1;
       Screen sc;
       screen_none(sc);
       int n = 0, step = 0;
@@ -144,7 +176,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
       }
       screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
       if (live && sub == 0) {
-        if constexpr (kSlice) s_cyc[g] = static_cast<uint8_t>(s_cyc[g] + 1);
+        if constexpr (kSlice) s_cyc[slot] = static_cast<uint8_t>(s_cyc[slot] + 1);
         const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
         EmitTask task;
         int r = kCycleFinished;
@@ -154,12 +186,12 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
         }
         if (r == kCycleAccepted) {
-          task.pad0 = static_cast<uint8_t>(g & 255);  // pool slot, to release it after the emission
-          task.pad1 = static_cast<uint8_t>(g >> 8);
-          s_alive[g] = kSlotPending;
+          task.pad0 = static_cast<uint8_t>(slot & 255);  // pool slot, to release it after the emission
+          task.pad1 = static_cast<uint8_t>(slot >> 8);
+          s_alive[slot] = kSlotPending;
           s_task[atomicAdd(&s_count[1], 1)] = task;
         } else if (r == kCycleFinished) {
-          s_alive[g] = kSlotDead;
+          s_alive[slot] = kSlotDead;
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
           if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
@@ -168,45 +200,60 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     }
     __syncthreads();
     // GenerateEmission for the period's accepted emissions, in full warps,
-    // before the pool is compacted (at most one per event: queued <= T).
+    // before the pool is compacted (at most one per event: queued <= kPool).
     const int queued = s_count[1];
     if (queued > 0) {
-      if (tid < queued) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_count[4]);
+      for (int q = tid; q < queued; q += T) cycle_emit<kMode == kModeMulti>(P0, E, s_task[q], q, s_jobs, &s_count[4]);
       __syncthreads();
       for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
-      if (tid < queued) s_alive[s_task[tid].pad0 | (s_task[tid].pad1 << 8)] = kSlotLive;
+      for (int q = tid; q < queued; q += T) s_alive[s_task[q].pad0 | (s_task[q].pad1 << 8)] = kSlotLive;
       __syncthreads();
     }
 
     // Compact: the still-active events move to the front of the pool; in a
-    // slice, those that have run their cycles leave for list_out.
-    bool alive = tid < pool && s_alive[tid] == kSlotLive;
-    const int32_t mine = alive ? s_pool[tid] : 0;
-    uint8_t my_cyc = 0;
-    if constexpr (kSlice) {
-      my_cyc = tid < pool ? s_cyc[tid] : 0;
-      const bool done = alive && my_cyc >= sl.cycles;
-      const unsigned dmask = __ballot_sync(0xffffffffu, done);
-      if (dmask) {
-        const int lane = tid & 31, leader = __ffs(dmask) - 1;
-        unsigned long long at = 0;
-        if (lane == leader) at = atomicAdd(sl.out_count, static_cast<unsigned long long>(__popc(dmask)));
-        at = __shfl_sync(0xffffffffu, at, leader);
-        if (done) sl.list_out[at + __popc(dmask & ((1u << lane) - 1u))] = mine;
+    // slice, those that have run their cycles leave for list_out.  Every
+    // slot is read before any is written.
+    bool alive[S];
+    int32_t mine[S];
+    uint8_t my_cyc[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) {
+      const int q = tid + o * T;
+      alive[o] = q < pool && s_alive[q] == kSlotLive;
+      mine[o] = alive[o] ? s_pool[q] : 0;
+      my_cyc[o] = 0;
+      if constexpr (kSlice) {
+        my_cyc[o] = q < pool ? s_cyc[q] : 0;
+        const bool done = alive[o] && my_cyc[o] >= sl.cycles;
+        const unsigned dmask = __ballot_sync(0xffffffffu, done);
+        if (dmask) {
+          const int lane = tid & 31, leader = __ffs(dmask) - 1;
+          unsigned long long at = 0;
+          if (lane == leader) at = atomicAdd(sl.out_count, static_cast<unsigned long long>(__popc(dmask)));
+          at = __shfl_sync(0xffffffffu, at, leader);
+          if (done) sl.list_out[at + __popc(dmask & ((1u << lane) - 1u))] = mine[o];
+        }
+        alive[o] = alive[o] && !done;
       }
-      alive = alive && !done;
     }
     if (tid == 0) s_count[0] = 0;
     __syncthreads();
-    const unsigned mask = __ballot_sync(0xffffffffu, alive);
-    int base = 0;
-    if ((tid & 31) == 0 && mask) base = atomicAdd(&s_count[0], __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    int at[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) {
+      const unsigned mask = __ballot_sync(0xffffffffu, alive[o]);
+      int base = 0;
+      if ((tid & 31) == 0 && mask) base = atomicAdd(&s_count[0], __popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      at[o] = base + __popc(mask & ((1u << (tid & 31)) - 1u));
+    }
     __syncthreads();
-    if (alive) {
-      const int at = base + __popc(mask & ((1u << (tid & 31)) - 1u));
-      s_pool[at] = mine;
-      if constexpr (kSlice) s_cyc[at] = my_cyc;
+#pragma unroll
+    for (int o = 0; o < S; ++o) {
+      if (alive[o]) {
+        s_pool[at[o]] = mine[o];
+        if constexpr (kSlice) s_cyc[at[o]] = my_cyc[o];
+      }
     }
     pool = s_count[0];
     __syncthreads();
@@ -225,7 +272,7 @@ cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks
   if (fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
   int64_t blocks = static_cast<int64_t>(sms) * per_sm;
-  const int64_t needed = ((kSlice ? sl.n_in : E.n) + T - 1) / T;
+  const int64_t needed = ((kSlice ? sl.n_in : E.n) + persist_slots(T) * T - 1) / (persist_slots(T) * T);
   if (blocks > needed) blocks = needed;
   if (blocks == 0) return cudaSuccess;
   k_shower_persistent<T, kMode, kSlice><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period, sl);
