@@ -81,7 +81,10 @@ constexpr int persist_slots(int t) { return t * GAPS_PERSIST_SLOTS <= 512 ? GAPS
 template <int T, int kMode, bool kSlice>
 __global__ void __launch_bounds__(T, persist_min_blocks(T))
     k_shower_persistent(DevParams P0, Events E, int period, SliceArgs sl) {
-  constexpr int S = persist_slots(T);
+  // A slice gives every event a fixed number of cycles: with two events per
+  // thread each would get about half of them per slice (serving latency
+  // measured 30 % higher), so slices keep one.
+  constexpr int S = kSlice ? 1 : persist_slots(T);
   constexpr int kPool = S * T;  // events of the block's pool
   __shared__ int32_t s_pool[kPool];
   __shared__ uint8_t s_alive[kPool];
@@ -94,14 +97,17 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
   unsigned long long* cursor = kSlice ? sl.cursor : &E.counters[6];
   const int64_t total = kSlice ? (sl.n_in_dev ? min(sl.n_in, static_cast<int64_t>(*sl.n_in_dev)) : sl.n_in) : E.n;
   int pool = 0;
+  bool first = true;
   if (tid == 0) s_count[5] = 0;
   for (;;) {
-    // Refill the free slots from the global cursor.  Once the cursor has
-    // passed the last event the pool only shrinks, and once it fits in half
-    // the threads its events get several lanes each (the last, longest
+    // Refill the free slots from the global cursor: one event per thread at
+    // first, so that a batch of fewer than two events per resident thread
+    // spreads over every block, then up to the whole pool.  Once the cursor
+    // has passed the last event the pool only shrinks, and once it fits in
+    // half the threads its events get several lanes each (the last, longest
     // showers).
     if (tid == 0) {
-      const int want = kPool - pool;
+      const int want = (first ? T : kPool) - pool;
       unsigned long long base = 0;
       int take = 0;
       if (want > 0 && s_count[5] == 0) {
@@ -127,6 +133,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
       }
     }
     pool += take;
+    first = false;
     for (int q = tid; q < kPool; q += T) s_alive[q] = q < pool ? kSlotLive : kSlotDead;
     __syncthreads();
     if (pool == 0) break;
@@ -272,7 +279,7 @@ cudaError_t launch_t(const DevParams& P, const Events& E, int period, int blocks
   if (fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
   int64_t blocks = static_cast<int64_t>(sms) * per_sm;
-  const int64_t needed = ((kSlice ? sl.n_in : E.n) + persist_slots(T) * T - 1) / (persist_slots(T) * T);
+  const int64_t needed = ((kSlice ? sl.n_in : E.n) + T - 1) / T;  // one event per thread to start
   if (blocks > needed) blocks = needed;
   if (blocks == 0) return cudaSuccess;
   k_shower_persistent<T, kMode, kSlice><<<static_cast<unsigned>(blocks), T, 0, s>>>(P, E, period, sl);
