@@ -279,10 +279,16 @@ int gaps_generate_me(const gaps_params* params, const gaps_batch* batch, void* s
  * per event, the winning trial emission over every colour-connected dipole
  * and matching splitting kernel (Eq. A.6), checks the cutoff, applies the
  * veto (Eq. A.8, A.9) and performs the accepted splitting.  mode =
- * GAPS_SHOWER_PLAIN.  Synchronises the stream once per cycle (the host
- * all-done check).  *launches_out (may be NULL) receives the number of
- * cycle launches.  Returns GAPS_ERR_STEP_LIMIT if any event stopped at
- * max_steps (the other events are complete). */
+ * GAPS_SHOWER_PLAIN: one launch per step (a step runs the select/veto phase
+ * of the listed events and the splittings the previous step accepted); the
+ * host checks the live count after every launch (the all-done check), read
+ * from host-mapped memory that the next launch writes as it starts, and
+ * keeps one launch queued ahead.  mode = GAPS_SHOWER_PERSISTENT: one
+ * persistent launch (gaps_shower_persistent with the default shape).  The
+ * stream is synchronised before returning.  *launches_out (may be NULL)
+ * receives the number of step launches that had work.  Returns
+ * GAPS_ERR_STEP_LIMIT if any event stopped at max_steps (the other events
+ * are complete). */
 int gaps_shower(const gaps_params* params, const gaps_batch* batch, int mode, int64_t* launches_out,
                 void* stream);
 
