@@ -371,6 +371,12 @@ HostCounters& host_counters() {
   return hc;
 }
 
+// The plain form rebuilds its active list in event order after a launch
+// while the list holds at least 1/GAPS_REBUILD_DIV of the batch.
+#ifndef GAPS_REBUILD_DIV
+#define GAPS_REBUILD_DIV 16
+#endif
+
 // Launches the plain form's host loop queues ahead of the one it reads back.
 #ifndef GAPS_PLAIN_LOOKAHEAD
 #define GAPS_PLAIN_LOOKAHEAD 1
@@ -478,7 +484,8 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     if (kernel_ms_out && (err = cudaEventRecord(tev[2 * c + 1], s)) != cudaSuccess) return err;
     // While the list is long, put it back in event order (appends scatter
     // it); the same events, so its length stands.
-    if (bound * 16 >= E.n && (err = launch_list_active(E, list_out, &E.counters[7], s)) != cudaSuccess) return err;
+    if (bound * GAPS_REBUILD_DIV >= E.n && (err = launch_list_active(E, list_out, &E.counters[7], s)) != cudaSuccess)
+      return err;
     return cudaSuccess;
   };
   // The live events launch c leaves, once launch c + 1 has published them
