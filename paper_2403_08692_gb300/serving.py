@@ -114,15 +114,22 @@ class Server:
     event and round; clock: "wall" (arrival times in seconds, served in real
     time) or "rounds" (arrival times in rounds, for deterministic tests);
     mode: "slice" (one persistent launch per round, launch shape cfg) or
-    "steps" (cycles_per_round plain-form steps per round)."""
+    "steps" (cycles_per_round plain-form steps per round).  device_layer:
+    (binding, torch) pair the server drives; None is this package's binding
+    and PyTorch on a CUDA device (the host-logic tests pass a host-side
+    stand-in and device "cpu")."""
 
     def __init__(self, pool_events=None, capacity=128, memory_budget=None, cycles_per_round=8, clock="wall",
-                 device="cuda", mode="slice", cfg=None):
-        import torch
+                 device="cuda", mode="slice", cfg=None, device_layer=None):
+        if device_layer is None:
+            import torch
+            device_layer = (gaps, torch)
+        self._gaps, torch = device_layer
+        G = self._gaps
         if pool_events is None:
             if memory_budget is None:
                 raise ValueError("give pool_events or memory_budget")
-            per_event = gaps.workspace_bytes(1 << 20, capacity) / float(1 << 20)
+            per_event = G.workspace_bytes(1 << 20, capacity) / float(1 << 20)
             pool_events = int(memory_budget // per_event)
         self.pool_events = int(pool_events)
         self.capacity = int(capacity)
@@ -134,21 +141,21 @@ class Server:
         self.clock = clock
         self.mode = mode
         self.cfg = cfg
-        self.ws = gaps.Workspace(self.pool_events, self.capacity, device=device)
+        pin = (lambda t: t) if device == "cpu" else (lambda t: t.pin_memory())
+        self.ws = G.Workspace(self.pool_events, self.capacity, device=device)
         self.stream = torch.cuda.Stream(device=device)
-        self.hist = torch.zeros((gaps.MAX_JOBS, gaps.HIST_DOUBLES), dtype=torch.float64, device=device)
-        self.hist_host = torch.empty((gaps.MAX_JOBS, gaps.HIST_DOUBLES), dtype=torch.float64).pin_memory()
+        self.hist = torch.zeros((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64, device=device)
+        self.hist_host = pin(torch.empty((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64))
         self._counters = self.ws.view("counters", torch.int64, (COUNTER_WORDS,))
-        self._job_done = self.ws.view("job_done", torch.int64, (gaps.MAX_JOBS,))
-        self._progress_host = [torch.empty(COUNTER_WORDS + gaps.MAX_JOBS, dtype=torch.int64).pin_memory()
-                               for _ in range(2)]
+        self._job_done = self.ws.view("job_done", torch.int64, (G.MAX_JOBS,))
+        self._progress_host = [pin(torch.empty(COUNTER_WORDS + G.MAX_JOBS, dtype=torch.int64)) for _ in range(2)]
         self._torch = torch
         self.reset()
 
     # ------------------------------------------------------------ state
     def reset(self):
         self.alloc = RangeAllocator(self.pool_events)
-        self.free_slots = list(range(gaps.MAX_JOBS - 1, -1, -1))
+        self.free_slots = list(range(self._gaps.MAX_JOBS - 1, -1, -1))
         self.queue = collections.deque()
         self.live = {}                  # slot -> (job, ev_begin, admitted time, admitted round)
         self.cycle = 0
@@ -159,7 +166,7 @@ class Server:
         self.peak_live_jobs = 0
         self._inflight = collections.deque()
         self._completions = []
-        gaps.pool_reset(self.ws, stream=self.stream)
+        self._gaps.pool_reset(self.ws, stream=self.stream)
 
     def _now(self, t0):
         return time.perf_counter() - t0 if self.clock == "wall" else float(self.rounds)
@@ -172,8 +179,8 @@ class Server:
                 return  # first in, first admitted: wait for room
             self.queue.popleft()
             slot = self.free_slots.pop()
-            gaps.pool_admit(job.params, slot, begin, job.n_events, job.first_event, self.ws, self.cycle,
-                            stream=self.stream)
+            self._gaps.pool_admit(job.params, slot, begin, job.n_events, job.first_event, self.ws, self.cycle,
+                                  stream=self.stream)
             self.live[slot] = (job, begin, now, self.rounds)
             self.admitted_events += job.n_events
             self.bound += job.n_events
@@ -185,10 +192,10 @@ class Server:
         bound = min(self.bound, self.pool_events)
         if self.mode == "slice":
             # self.cycle counts slices: the rotation index of the pool's lists
-            gaps.pool_slice(self.ws, self.cycle, k, bound, self.cfg, stream=self.stream)
+            self._gaps.pool_slice(self.ws, self.cycle, k, bound, self.cfg, stream=self.stream)
             self.cycle += 1
         else:
-            gaps.pool_cycles(self.ws, self.cycle, k, bound, stream=self.stream)
+            self._gaps.pool_cycles(self.ws, self.cycle, k, bound, stream=self.stream)
             self.cycle += k
         self.launched_cycles += k
         buf = self._progress_host[self.rounds % 2]
@@ -216,7 +223,7 @@ class Server:
                 continue
             with torch.cuda.stream(self.stream):
                 self.hist[slot].zero_()
-                gaps.pool_finish(slot, begin, job.n_events, self.ws, self.hist[slot], stream=self.stream)
+                self._gaps.pool_finish(slot, begin, job.n_events, self.ws, self.hist[slot], stream=self.stream)
                 if on_finish is not None:
                     on_finish(job, self.ws, begin, self.stream)
                 self.hist_host[slot].copy_(self.hist[slot], non_blocking=True)
