@@ -201,7 +201,10 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
   double bp = 0.0, bm = 0.0;
   for (int i = 0; i < n; ++i) {
-    const bool plus = jx[i] * ax + jy[i] * ay + jz[i] * az >= 0.0;
+    // p . n >= 0 on the bits (-0 counts as 0; the FP64 pipe's compares cost
+    // as much as its FMAs on this part)
+    const long long pn = __double_as_longlong(jx[i] * ax + jy[i] * ay + jz[i] * az);
+    const bool plus = pn >= 0 || pn == static_cast<long long>(0x8000000000000000ull);
     double* h = plus ? hp : hm;
     h[0] += je[i];
     h[1] += jx[i];

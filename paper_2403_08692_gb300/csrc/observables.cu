@@ -7,6 +7,14 @@ namespace gaps {
 namespace {
 
 // ------------------------------------------------------------ validation
+// Finite / positive tests on the bits of a double: on this part the FP64
+// pipe's compares cost as much as its FMAs, the ALU's tests a fraction.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ffull) != 0x7ffull;
+}
+// x > 0 for a finite x
+__device__ __forceinline__ bool positive_finite_bits(double x) { return __double_as_longlong(x) > 0; }
+
 // One thread per event.  Bits: 1 momentum not conserved to 1e-10 GeV, 2 a
 // parton off shell (|p^2| > 1e-10 E sqrt(s): every component is formed from
 // momenta of the event's scale, so FP64 masslessness holds to ~eps E
@@ -25,12 +33,13 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
   for (int i = 0; i < n; ++i) {
     const size_t a = E.at(i, ev);
     const double e = E.e[a], x = E.px[a], y = E.py[a], z = E.pz[a];
-    if (!isfinite(e) || !isfinite(x) || !isfinite(y) || !isfinite(z)) bits |= 32;
+    const bool finite = finite_bits(e) && finite_bits(x) && finite_bits(y) && finite_bits(z);
+    if (!finite) bits |= 32;
     se += e;
     sx += x;
     sy += y;
     sz += z;
-    if (!(e > 0.0)) bits |= 4;
+    if (!(finite_bits(e) ? positive_finite_bits(e) : e > 0.0)) bits |= 4;
     if (fabs(e * e - x * x - y * y - z * z) > 1e-10 * e * P.sqrt_s) bits |= 2;
     const int fl = E.flav[a];
     const int c = E.col[a], ac = E.acol[a];
