@@ -274,12 +274,13 @@ __device__ __forceinline__ PartonScreen load_parton_screen(const Events& E, int6
 // one are generated, so their latency hides behind the Philox rounds.
 template <int kMode>
 __device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step,
-                                               int n, int first, int stride, Screen& sc) {
+                                               int n, int first, int stride, Screen& sc,
+                                               const PartonScreen* first_loaded = nullptr) {
   screen_none(sc);
   if (first >= n) return;
   constexpr float kInvCF2 = static_cast<float>(1.0 / (2.0 * kCF));
   constexpr float kInvCA = static_cast<float>(1.0 / kCA);
-  PartonScreen cur = load_parton_screen(E, ev, first);
+  PartonScreen cur = first_loaded ? *first_loaded : load_parton_screen(E, ev, first);
   for (int i = first; i < n; i += stride) {
     PartonScreen nxt = cur;
     if (i + stride < n) nxt = load_parton_screen(E, ev, i + stride);

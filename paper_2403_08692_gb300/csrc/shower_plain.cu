@@ -194,17 +194,27 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     const int64_t idx = block * kGroups + tid / L;
     int64_t ev = -1;
     if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
-    const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
+    // The event's status, size, cycle and (one lane per event) first parton
+    // are loaded together, not one after another: every listed event has
+    // slot 0.
+    int status = -1, n = 0, step = 0;
+    PartonScreen first{};
+    if (ev >= 0) {
+      status = E.status[ev];
+      n = E.n_partons[ev];
+      step = E.n_steps[ev];
+      if (L == 1) first = load_parton_screen(E, ev, 0);
+    }
+    const bool active = status == GAPS_ACTIVE;
     Screen sc;
     screen_none(sc);
-    int n = 0, step = 0;
     bool limited = false;
     if (active) {
       const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
-      n = E.n_partons[ev];
-      step = E.n_steps[ev];
       limited = step >= P.max_steps;
-      if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc);
+      if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc, L == 1 ? &first : nullptr);
+    } else {
+      n = step = 0;
     }
     screen_group_reduce<L>(sc);  // every lane of the warp, one call site
     const bool lead = active && sub == 0;
