@@ -1,13 +1,15 @@
 // Matrix element + shower initial state (App. B; App. C main program) and the
 // plain event-parallel veto cycle (Sec. 2, Fig. 2, App. C).
 //
-// Plain form: one launch per veto cycle over every event of the batch, one
-// thread per event.  The paper's four per-cycle kernels (SelectWinnerEmission,
-// CheckCutoff, AcceptOrVeto, GenerateEmission) and its alpha_s kernel are
-// fused into one launch (shower_cycle), so an event's state stays in
-// registers for the whole cycle instead of making four round trips through
-// HBM.  Finished events leave at once (the paper's endShower early exit) and
-// bump the finished-event counter that the host polls between cycles.
+// Plain form: one launch per step with a host all-done check.  A step
+// (k_step_deferred) runs SelectWinnerEmission, CheckCutoff and AcceptOrVeto
+// (the paper's first three per-cycle kernels and its alpha_s kernel, fused)
+// for the events of the active list, one event per group of L lanes, and
+// GenerateEmission for the emissions the previous step accepted, in full
+// warps; the lists live on the device and the host only sizes the grids and
+// reads the live count.  Finished events leave at once (the paper's
+// endShower early exit).  k_step_plain, one fused cycle of every event with
+// its emissions in the same launch, serves gaps_shower_step.
 #include <algorithm>
 
 #include "gaps_launch.hpp"
