@@ -6,7 +6,8 @@
  * showered at once, every veto cycle running for all events in lock-step.
  * Around it sit the LO matrix element that creates the events (App. B) and
  * the observables computed on the finished events (Sec. 3.1: Durham jet
- * rates, thrust, heavy-jet mass) with their histograms.
+ * rates, thrust, heavy-jet mass; and the jet broadenings B_T, B_W of
+ * Table 1) with their histograms.
  *
  * Memory model.  The caller owns all device memory: one workspace of
  * gaps_workspace_bytes(n_events, capacity) bytes, 256-byte aligned, holds the
