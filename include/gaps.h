@@ -122,7 +122,9 @@ typedef struct gaps_layout {
   int64_t counters;       /* uint64 [32]: device counters of the last shower call: 0 finished events,
                              1 step-limited events, 2 cycles decided in full FP64, 3 vetoes decided in FP64;
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
-                             merges with several FP64 candidates; 6 the persistent form's event cursor;
+                             merges with several FP64 candidates, 8 finished events left without
+                             observables for a parton count outside 2..capacity; 6 the persistent
+                             form's event cursor;
                              7 scratch of the plain form's list rebuild; 21..23 the plain form's
                              active-list lengths and 24..26 its deferred-emission counts, rotating
                              over three launches; 10..12 and 18..20 the same for the serving pool;
@@ -363,24 +365,32 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
 #define GAPS_NOALLOC_MAX_EVENTS (1 << 20)
 
 /* The observables stage of gaps_observables (Durham y23..y56, 1-T, rho_H,
- * B_T, B_W)
- * for callers that cannot allocate device memory -- code that must stay
- * inside another framework's memory pool, plug-ins whose host forbids
+ * B_T, B_W) for callers that cannot allocate device memory -- code that must
+ * stay inside another framework's memory pool, plug-ins whose host forbids
  * allocation calls, or processes that hand out all device memory up front.
  * The paper has no counterpart; it is a deployment variant.  The caller
  * passes only inputs and outputs: momenta px, py, pz, e as slot-major
  * [capacity][n_events] doubles (the workspace layout), n_partons and status
- * (int32 [n_events]), and obs (double [GAPS_N_OBS][n_events], written: -1 for events
- * whose status is not GAPS_DONE and for undefined y values).  The working
- * arrays live in one fixed device array inside the library (about 4.2 MB,
- * held by every GPU that loads the library until the process exits), so the
- * call allocates nothing and calls no allocating routine.
+ * (int32 [n_events]), and obs (double [GAPS_N_OBS][n_events], written).  All
+ * are device pointers.  The working arrays live in one fixed device array
+ * inside the library, so the call allocates nothing and calls no allocating
+ * routine.
  * Limits and behaviour:
  *  - n_events <= GAPS_NOALLOC_MAX_EVENTS, 4 <= capacity <= 255, sqrt_s > 0,
- *    else GAPS_ERR_INVALID before any work; n_events == 0 is a no-op.
- *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture on the device.
+ *    and non-null arrays when n_events > 0, else GAPS_ERR_INVALID before any
+ *    work.
+ *  - obs gets -1 for events whose status is not GAPS_DONE, for events whose
+ *    n_partons is outside 2 .. capacity (no slot beyond the capacity is
+ *    read), and for undefined y values.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    (once per device, with that device current) and makes CUDA load the
+ *    library code that holds the array and the observables' kernels.  CUDA
+ *    loads that code lazily by default, so this first call is when the array
+ *    (about 4.2 MB) and the kernels take their device memory, held until the
+ *    process exits.  A call with n_events = 0 does only this set-up: make it
+ *    before handing out all device memory and before any stream capture on
+ *    the device.  The looked-up address is not valid after a
+ *    cudaDeviceReset of the device; do not call this entry point after one.
  *  - All calls share the array and it keeps the last call's contents; each
  *    call clears what must start at zero on its own stream.  Calls whose
  *    work overlaps on the GPU race on the array: order them on one stream or

@@ -330,14 +330,24 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
 }
 
 // ------------------------------------------------------------- buckets
-// counts[n] = finished events with n partons (n <= 255).
+// Parton count of event ev if it gets observables: finished, with 2 ..
+// capacity partons (the shower never writes another count; callers that pass
+// their own arrays may), else -1.
+__device__ __forceinline__ int shape_partons(const Events& E, int64_t ev) {
+  if (E.status[ev] != GAPS_DONE) return -1;
+  const int n = E.n_partons[ev];
+  return n >= 2 && n <= E.cap ? n : -1;
+}
+
+// counts[n] = finished events with n partons (2 <= n <= capacity <= 255).
 __global__ void __launch_bounds__(256) k_bucket_count(Events E, int* counts) {
   __shared__ int sh[256];
   sh[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; ev < E.n;
        ev += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (E.status[ev] == GAPS_DONE) atomicAdd(&sh[E.n_partons[ev]], 1);
+    const int n = shape_partons(E, ev);
+    if (n >= 0) atomicAdd(&sh[n], 1);
   }
   __syncthreads();
   if (sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
@@ -362,7 +372,9 @@ __global__ void __launch_bounds__(256) k_bucket_scan(const int* counts, int* off
   if (t == 255) offsets[256] = sh[255];
 }
 
-// Finished events go to their bucket; the others get undefined observables.
+// Finished events go to their bucket; the others get undefined observables,
+// and so do finished events with a parton count outside 2 .. capacity
+// (counted in counter word 8).
 // A warp's lanes of one bucket take their places with one shared-memory
 // atomic, a block's with one global atomic per bucket and round, so the
 // few hot buckets (a handful of multiplicities hold most events) see a
@@ -378,9 +390,9 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Events E, int* cursor, i
     const int64_t ev = first + tid;
     int n = -1;
     if (ev < E.n) {
-      if (E.status[ev] == GAPS_DONE) {
-        n = E.n_partons[ev];
-      } else {
+      n = shape_partons(E, ev);
+      if (n < 0) {
+        if (E.status[ev] == GAPS_DONE) atomicAdd(&E.counters[8], 1ull);
         for (int h = 0; h < GAPS_N_OBS; ++h) E.obs[h * E.stride + ev] = -1.0;
       }
     }
@@ -410,6 +422,19 @@ __global__ void __launch_bounds__(kShapeThreads) k_event_shapes(DevParams P, Eve
 
 }  // namespace
 
+cudaError_t preload_observables() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k_bucket_count);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scan);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scatter);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<16>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<32>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<64>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<256>);
+  return e;
+}
+
 cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s) {
   if (E.n == 0) return cudaSuccess;
   int sms = 152, dev = 0;
@@ -420,6 +445,7 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
   cudaError_t e = cudaMemsetAsync(counts, 0, 256 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(E.counters + 4, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + 8, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int64_t want = (E.n + 255) / 256;
   const unsigned grid_count = static_cast<unsigned>(want < 4 * sms ? want : 4 * sms);

@@ -64,6 +64,9 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s)
 // buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
 // scratch [n_events].
 cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s);
+// Make CUDA load the observables' kernels on the current device now (it
+// loads modules lazily by default, at their first use).
+cudaError_t preload_observables();
 // Single-job batch: hist is one histogram set; multi-job batch (E.jobs set):
 // hist holds one set per job.
 cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s);

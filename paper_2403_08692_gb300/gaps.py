@@ -302,10 +302,24 @@ NOALLOC_MAX_EVENTS = 1 << 20
 def event_shapes_noalloc(px, py, pz, e, n_partons, status, n_events, capacity, sqrt_s, obs, stream=None):
     """gaps_event_shapes_noalloc on caller-owned device tensors (no workspace,
     no allocation): momenta [capacity][n_events] float64, n_partons and
-    status int32 [n_events]; writes obs [N_OBS][n_events] float64."""
+    status int32 [n_events]; writes obs [N_OBS][n_events] float64.  The
+    tensors are checked (dtype, device, contiguity, length) before the call,
+    since the library only sees raw pointers.  n_events = 0 (tensors may be
+    None) runs only the per-device set-up."""
+    import torch
+    n, cap = int(n_events), int(capacity)
+    if n > 0:
+        need = {"px": (px, torch.float64, cap * n), "py": (py, torch.float64, cap * n),
+                "pz": (pz, torch.float64, cap * n), "e": (e, torch.float64, cap * n),
+                "n_partons": (n_partons, torch.int32, n), "status": (status, torch.int32, n),
+                "obs": (obs, torch.float64, N_OBS * n)}
+        for name, (t, dtype, count) in need.items():
+            if t is None or t.dtype != dtype or not t.is_cuda or not t.is_contiguous() or t.numel() < count:
+                raise ValueError(f"event_shapes_noalloc: {name} must be a contiguous CUDA {dtype} tensor "
+                                 f"of at least {count} elements")
     ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)
     _check(load().gaps_event_shapes_noalloc(ptr(px), ptr(py), ptr(pz), ptr(e), ptr(n_partons), ptr(status),
-                                            int(n_events), int(capacity), float(sqrt_s), ptr(obs),
+                                            n, cap, float(sqrt_s), ptr(obs),
                                             _stream_handle(stream)), "gaps_event_shapes_noalloc")
 
 
