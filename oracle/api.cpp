@@ -1,4 +1,5 @@
 // Oracle C interface (test infrastructure only; see oracle_api.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -18,14 +19,29 @@ std::vector<Vec4> momenta_of(const Event& ev) {
   return m;
 }
 
+// A given starting state (oracle_run_from_state) in place of the matrix
+// element: its partons and the next free colour line.
+struct StartState {
+  std::vector<Parton> partons;
+  int next_colour = 0;
+};
+
 void run_range(const oracle_params& p, uint32_t first_event, int64_t begin, int64_t end,
-               oracle_event_out* out, double* mom, int32_t* info, double* obs, double* hist) {
+               oracle_event_out* out, double* mom, int32_t* info, double* obs, double* hist,
+               const StartState* start) {
   const double s = p.sqrt_s * p.sqrt_s;
   Event ev;
   ev.partons.reserve(static_cast<size_t>(p.capacity) + 1);
   for (int64_t j = begin; j < end; ++j) {
     const uint32_t id = first_event + static_cast<uint32_t>(j);
-    generate_me(p, id, ev);
+    if (start) {
+      ev.partons = start->partons;
+      ev.next_colour = start->next_colour;
+      ev.me_flavour = 0;
+      ev.weight = 1.0;
+    } else {
+      generate_me(p, id, ev);
+    }
     shower(p, id, ev);
     const int valid = validate(ev.partons, p.sqrt_s);
     double o[kNObs] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -107,7 +123,7 @@ int oracle_run(const oracle_params* p, uint32_t first_event, int64_t n_events, i
   if (info) std::memset(info, 0, sizeof(int32_t) * n_events * p->capacity * 3);
   const size_t hsize = static_cast<size_t>(kNObs) * kRow * 3;
   if (n_threads <= 1 || n_events < 2 * n_threads) {
-    run_range(*p, first_event, 0, n_events, out, mom, info, obs, hist);
+    run_range(*p, first_event, 0, n_events, out, mom, info, obs, hist, nullptr);
     return 0;
   }
   std::vector<std::vector<double>> partial(n_threads, std::vector<double>(hist ? hsize : 0, 0.0));
@@ -116,12 +132,46 @@ int oracle_run(const oracle_params* p, uint32_t first_event, int64_t n_events, i
     const int64_t b = n_events * t / n_threads;
     const int64_t e = n_events * (t + 1) / n_threads;
     double* h = hist ? partial[t].data() : nullptr;
-    pool.emplace_back(run_range, std::cref(*p), first_event, b, e, out, mom, info, obs, h);
+    pool.emplace_back(run_range, std::cref(*p), first_event, b, e, out, mom, info, obs, h,
+                      static_cast<const StartState*>(nullptr));
   }
   for (auto& th : pool) th.join();
   if (hist)
     for (int t = 0; t < n_threads; ++t)
       for (size_t i = 0; i < hsize; ++i) hist[i] += partial[t][i];
+  return 0;
+}
+
+int oracle_run_from_state(const oracle_params* p, int n_init, const double* mom, const int32_t* info,
+                          uint32_t first_event, int64_t n_events, int n_threads, oracle_event_out* out,
+                          double* mom_out, int32_t* info_out) {
+  if (oracle_check_params(p) != 0 || n_events < 0 || !mom || !info || n_init < 2 || n_init > p->capacity)
+    return -1;
+  StartState st;
+  int top = 0;
+  for (int i = 0; i < n_init; ++i) {
+    const Parton q{Vec4{mom[4 * i], mom[4 * i + 1], mom[4 * i + 2], mom[4 * i + 3]}, info[3 * i], info[3 * i + 1],
+                   info[3 * i + 2]};
+    if (q.col < 0 || q.acol < 0 || q.col >= 1000 || q.acol >= 1000) return -1;
+    top = std::max(top, std::max(q.col, q.acol));
+    st.partons.push_back(q);
+  }
+  st.next_colour = top + 1;
+  if (mom_out) std::memset(mom_out, 0, sizeof(double) * n_events * p->capacity * 4);
+  if (info_out) std::memset(info_out, 0, sizeof(int32_t) * n_events * p->capacity * 3);
+  if (n_threads <= 1 || n_events < 2 * n_threads) {
+    run_range(*p, first_event, 0, n_events, out, mom_out, info_out, nullptr, nullptr, &st);
+    return 0;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < n_threads; ++t) {
+    const int64_t b = n_events * t / n_threads;
+    const int64_t e = n_events * (t + 1) / n_threads;
+    pool.emplace_back(run_range, std::cref(*p), first_event, b, e, out, mom_out, info_out,
+                      static_cast<double*>(nullptr), static_cast<double*>(nullptr),
+                      static_cast<const StartState*>(&st));
+  }
+  for (auto& th : pool) th.join();
   return 0;
 }
 

@@ -29,6 +29,9 @@ MUT_HJM_LIGHT = 1 << 10
 MUT_TRIAL_RESTART = 1 << 11
 MUT_KERNEL_UNIFORM = 1 << 12
 MUT_BROAD_DOT = 1 << 13
+MUT_NF_MINUS_ONE = 1 << 14
+MUT_PAIR_UNIFORM = 1 << 15
+MUT_GG_FULL = 1 << 16
 TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE = 0, 1
 
 
@@ -69,6 +72,8 @@ def lib():
         L.oracle_check_params.argtypes = [C.POINTER(Params)]
         L.oracle_run.argtypes = [C.POINTER(Params), C.c_uint32, C.c_int64, C.c_int, C.c_void_p,
                                  dp, ip, dp, dp]
+        L.oracle_run_from_state.argtypes = [C.POINTER(Params), C.c_int, dp, ip, C.c_uint32, C.c_int64, C.c_int,
+                                            C.c_void_p, dp, ip]
         L.oracle_philox4x32_10.argtypes = [up, up, up]
         L.oracle_philox4x32_10.restype = None
         L.oracle_uniform_pair.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, dp]
@@ -140,6 +145,28 @@ def run(p: Params, first_event: int, n_events: int, threads: int = 1, want_momen
         out["obs"] = obs
     if want_hist:
         out["hist"] = hist
+    return out
+
+
+def run_from_state(p: Params, mom, info, first_event: int, n_events: int, threads: int = 1, want_momenta=False):
+    """Shower events first_event .. first_event+n_events-1 from the given
+    parton state (mom [n][4] as (E, px, py, pz), info [n][3] as (flavour,
+    colour, anticolour)) instead of the matrix element.  Returns 'events' and,
+    with want_momenta, 'mom' [n_events, cap, 4] and 'info' [n_events, cap, 3]."""
+    m = np.ascontiguousarray(mom, dtype=np.float64)
+    i = np.ascontiguousarray(info, dtype=np.int32)
+    n = int(n_events)
+    ev = np.zeros(n, dtype=EVENT_DTYPE)
+    mo = np.zeros((n, p.capacity, 4)) if want_momenta else None
+    io = np.zeros((n, p.capacity, 3), dtype=np.int32) if want_momenta else None
+    rc = lib().oracle_run_from_state(C.byref(p), len(m), _dp(m), _ip(i), first_event, n, threads,
+                                     ev.ctypes.data_as(C.c_void_p), _dp(mo), _ip(io))
+    if rc != 0:
+        raise ValueError("oracle_run_from_state rejected its arguments")
+    out = {"events": ev}
+    if want_momenta:
+        out["mom"] = mo
+        out["info"] = io
     return out
 
 

@@ -72,7 +72,10 @@ enum {
   ORACLE_MUT_HJM_LIGHT = 1 << 10,    /* lighter hemisphere mass */
   ORACLE_MUT_TRIAL_RESTART = 1 << 11,/* a vetoed trial restarts from the old scale */
   ORACLE_MUT_KERNEL_UNIFORM = 1 << 12,/* per-dipole trials: kernel drawn uniformly, not by its share */
-  ORACLE_MUT_BROAD_DOT = 1 << 13     /* broadening from |p . n_T| instead of |p x n_T| */
+  ORACLE_MUT_BROAD_DOT = 1 << 13,    /* broadening from |p . n_T| instead of |p x n_T| */
+  ORACLE_MUT_NF_MINUS_ONE = 1 << 14, /* a gluon gets g -> q qbar kernels for flavours 1..n_f-1 only */
+  ORACLE_MUT_PAIR_UNIFORM = 1 << 15, /* both kernels of a trial slot take the slot's first uniform */
+  ORACLE_MUT_GG_FULL = 1 << 16       /* g -> gg without the half weight of a gluon's two dipoles */
 };
 
 /* Histogram layout: 6 observables x (100 bins + underflow + overflow) x
@@ -88,6 +91,19 @@ int oracle_check_params(const oracle_params* p);
  * that ended at the cutoff.  n_threads <= 1 runs serially. */
 int oracle_run(const oracle_params* p, uint32_t first_event, int64_t n_events, int n_threads,
                oracle_event_out* out, double* mom, int32_t* info, double* obs, double* hist);
+
+/* The shower of oracle_run started from a given parton state instead of the
+ * matrix element (tests: pins of the shower from states with gluons).
+ * n_init partons (2 <= n_init <= capacity), mom [n_init][4] (E, px, py, pz),
+ * info [n_init][3] (flavour, colour, anticolour; colour lines numbered
+ * below 1000).  Every event first_event + j starts from this state at
+ * t0 = s with weight 1, next colour line = the largest line + 1, and runs
+ * with p's settings (max_emissions applies).  Outputs as oracle_run (may be
+ * NULL): out, mom_out [n_events][capacity][4], info_out
+ * [n_events][capacity][3]. */
+int oracle_run_from_state(const oracle_params* p, int n_init, const double* mom, const int32_t* info,
+                          uint32_t first_event, int64_t n_events, int n_threads, oracle_event_out* out,
+                          double* mom_out, int32_t* info_out);
 
 /* Building blocks, exported so the tests can pin each one on its own. */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -66,14 +66,23 @@ struct KernelRef {
 // The splitting kernels whose splitter flavour matches (App. A listing: "P(u
 // -> ug) may not be same as P(d -> dg)").  Quark or antiquark: one q -> qg
 // kernel.  Gluon: g -> gg, then g -> q qbar for flavours 1..n_f.
-int kernels_for(int flav, int nf, KernelRef out[8]) {
+int kernels_for(int flav, int nf, KernelRef out[8], int mutation) {
   if (flav != kGluon) {
     out[0] = {kQtoQG, 0};
     return 1;
   }
   out[0] = {kGtoGG, 0};
-  for (int f = 1; f <= nf; ++f) out[f] = {kGtoQQ, f};
-  return 1 + nf;
+  const int nq = (mutation & ORACLE_MUT_NF_MINUS_ONE) ? nf - 1 : nf;
+  for (int f = 1; f <= nq; ++f) out[f] = {kGtoQQ, f};
+  return 1 + nq;
+}
+
+// c = alpha_s^over / (2 pi) times the integral of the kernel's overestimate
+// over [z-, z+] (Eq. A.4).
+double trial_density(int kind, double as_over, double zm, double zp, int mutation) {
+  const double c = as_over / (2.0 * kPi) * kernel_integral(kind, zm, zp);
+  // planted: g -> gg at the full C_A instead of half of it per dipole
+  return (kind == kGtoGG && (mutation & ORACLE_MUT_GG_FULL)) ? 2.0 * c : c;
 }
 
 struct Winner {
@@ -142,14 +151,14 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
         const double zm = 1.0 - zp;
         ++ev.n_dipoles;
         KernelRef kernels[8];
-        const int nk = kernels_for(ev.partons[i].flav, p.n_flavours, kernels);
+        const int nk = kernels_for(ev.partons[i].flav, p.n_flavours, kernels, p.mutation);
         if (p.trial_mode == 1) {
           // One trial for the dipole with c = sum of its kernels' c
           // (competing exponentials: the first of independent trials is one
           // trial with the summed rate, its kernel drawn by share).
           double c[8], c_sum = 0.0;
           for (int kappa = 0; kappa < nk; ++kappa) {
-            c[kappa] = as_over / (2.0 * kPi) * kernel_integral(kernels[kappa].kind, zm, zp);
+            c[kappa] = trial_density(kernels[kappa].kind, as_over, zm, zp, p.mutation);
             c_sum += c[kappa];
           }
           const uint32_t slot = static_cast<uint32_t>((2 * i + side) * 4);
@@ -175,10 +184,10 @@ void shower(const oracle_params& p, uint32_t event_id, Event& ev) {
           continue;
         }
         for (int kappa = 0; kappa < nk; ++kappa) {
-          const double c = as_over / (2.0 * kPi) * kernel_integral(kernels[kappa].kind, zm, zp);
+          const double c = trial_density(kernels[kappa].kind, as_over, zm, zp, p.mutation);
           const uint32_t slot = static_cast<uint32_t>((2 * i + side) * 4 + kappa / 2);
           const UniformPair r = uniform_pair(p.seed, event_id, step, slot, kPurposeTrial);
-          const double u = (kappa & 1) ? r.u1 : r.u0;
+          const double u = ((kappa & 1) && !(p.mutation & ORACLE_MUT_PAIR_UNIFORM)) ? r.u1 : r.u0;
           const double t_trial = ev.t * std::pow(u, 1.0 / c);
           ++ev.n_trials;
           if (t_trial > t_win) {

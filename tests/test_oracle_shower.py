@@ -289,3 +289,146 @@ def test_paper_scale_run_is_qualitatively_like_the_paper(oracle_mod):
     assert 15 <= np.median(ev["n_steps"]) <= 60
     assert ev["n_steps"].max() < 250
     assert np.mean(ev["status"] == oracle_mod.OVERFLOW) < 1e-3
+
+
+# ------------------- first emission from a q g qbar state (gluon branches)
+# A fixed three-parton state at sqrt(s) = 91.2 GeV with energy fractions
+# x_q = 0.8, x_qbar = 0.7, x_g = 0.5, colour-ordered q - g - qbar: four
+# dipoles, (q | g) and (g | q) of mass^2 0.3 s, (g | qbar) and (qbar | g) of
+# mass^2 0.2 s.  Each quark end has the q -> qg kernel; the gluon has, on each
+# of its two dipoles, half of g -> gg and half of g -> q qbar for every
+# flavour (App. A: competing kernels, each with its own overestimate and
+# veto).  The first emission then has P(t1 < t) = prod over dipoles and
+# kernels of Delta_{d,k}(t), and the kind of the first emission has the
+# density rho_k(t) Delta(t), both computed here by quadrature.
+QGQ_X = (0.8, 0.5, 0.7)  # x_q, x_g, x_qbar
+
+
+def _qgq_state(sqrt_s, flavour=1):
+    xq, xg, xqb = QGQ_X
+    s = sqrt_s ** 2
+    eq, eqb = 0.5 * xq * sqrt_s, 0.5 * xqb * sqrt_s
+    cos_qqb = 1.0 - (1.0 - xg) * s / (2.0 * eq * eqb)
+    sin_qqb = math.sqrt(1.0 - cos_qqb ** 2)
+    pq = np.array([eq, 0.0, 0.0, eq])
+    pqb = np.array([eqb, eqb * sin_qqb, 0.0, eqb * cos_qqb])
+    pg = np.array([sqrt_s - eq - eqb, -(pq[1] + pqb[1]), -(pq[2] + pqb[2]), -(pq[3] + pqb[3])])
+    mom = np.stack([pq, pg, pqb])
+    info = np.array([[flavour, 1, 0], [21, 2, 1], [-flavour, 0, 2]], dtype=np.int32)
+    return mom, info
+
+
+def _z_integral(t, q2, kind):
+    """int dz (1 - y) P(z, y) over the z range with y = t / (Q^2 z (1-z)) < 1;
+    P as pinned by its collinear limits: 0 q->qg (C_F), 1 half g->gg, 2 half
+    g->q qbar of one flavour."""
+    if t >= q2 / 4:
+        return 0.0
+    root = math.sqrt(1 - 4 * t / q2)
+    zlo, zhi = 0.5 * (1 - root), 0.5 * (1 + root)
+
+    def f(z):
+        y = t / (q2 * z * (1 - z))
+        if kind == 0:
+            p = CF * (2 / (1 - z * (1 - y)) - (1 + z))
+        elif kind == 1:
+            p = 0.5 * CA * (2 / (1 - z * (1 - y)) - 2 + z * (1 - z))
+        else:
+            p = 0.5 * TR * (1 - 2 * z * (1 - z))
+        return (1 - y) * p
+
+    val, _ = integrate.quad(f, zlo, zhi, epsabs=1e-13, epsrel=1e-11, limit=200)
+    return val
+
+
+def _qgq_prediction(sqrt_s, tc, as_mz, fixed, nf, n_bins, sub=60):
+    """Bin edges in t (log-uniform from t_C to the largest dipole's s/4-like
+    end), and per bin the probability of a first emission of each kind
+    (q->qg, g->gg, g->q qbar summed over flavours) plus the probability of
+    none above t_C; the emission CDF on the fine grid for a KS test."""
+    s = sqrt_s ** 2
+    xq, xg, xqb = QGQ_X
+    q2a, q2b = s * (1 - xqb), s * (1 - xq)  # (q|g) and (g|qbar) masses
+    tmax = max(q2a, q2b) / 4
+    lt = np.linspace(math.log(tc), math.log(tmax), n_bins * sub + 1)
+    t = np.exp(lt)
+    rho = np.zeros((3, len(t)))  # per kind, d P / d ln t
+    for j, tj in enumerate(t):
+        a = _alphas(tj, as_mz, fixed, nf) / (2 * math.pi)
+        for q2 in (q2a, q2b):
+            rho[0, j] += a * _z_integral(tj, q2, 0)
+            rho[1, j] += a * _z_integral(tj, q2, 1)
+            rho[2, j] += a * nf * _z_integral(tj, q2, 2)
+    tot = rho.sum(axis=0)
+    # F(L) = int_L^Lmax tot dL': cumulative trapezoid from the top
+    h = np.diff(lt)
+    seg = 0.5 * h * (tot[1:] + tot[:-1])
+    F = np.append(np.cumsum(seg[::-1])[::-1], 0.0)
+    delta = np.exp(-F)
+    dens = rho * delta  # joint density of (ln t1, kind)
+    seg_k = 0.5 * h * (dens[:, 1:] + dens[:, :-1])  # per fine interval
+    probs = seg_k.reshape(3, n_bins, sub).sum(axis=2)
+    edges = t[::sub]
+    p_none = delta[0]
+    return edges, probs, p_none, lt, delta
+
+
+def _qgq_first_emission(O, fixed, mutation=0, n=200000, seed=31, nf=5):
+    sqrt_s, tc, as_mz = 91.2, 1.0, 0.118
+    mom, info = _qgq_state(sqrt_s)
+    p = O.make_params(sqrt_s=sqrt_s, t_cutoff=tc, alphas_mz=as_mz, seed=seed, fixed_alphas=fixed, n_flavours=nf,
+                      max_emissions=1, mutation=mutation, capacity=8)
+    r = O.run_from_state(p, mom, info, 0, n, threads=_threads(O), want_momenta=True)
+    ev, fin = r["events"], r["info"]
+    t1 = ev["t_first"]
+    emitted = ev["n_emissions"] == 1
+    assert np.all(emitted == (t1 > 0))
+    new = fin[:, 3]  # the emitted parton (flavour, colour, anticolour)
+    m = 3  # the first new colour line: the state uses lines 1 and 2
+    kind = np.full(n, -1)
+    gluon = emitted & (new[:, 0] == 21)
+    split_g = (fin[:, 1, 1] == m) | (fin[:, 1, 2] == m)  # the gluon took the new line: it split
+    kind[gluon & ~split_g] = 0
+    kind[gluon & split_g] = 1
+    kind[emitted & (new[:, 0] < 0)] = 2
+    assert np.all(kind[emitted] >= 0)
+    qq = kind == 2
+    # g -> q qbar: the gluon (slot 1) became the quark of the new antiquark's flavour
+    assert np.all(fin[qq, 1, 0] == -new[qq, 0])
+    flavours = np.bincount(-new[qq, 0], minlength=nf + 1)[1:]
+    edges, probs, p_none, lt, delta = _qgq_prediction(sqrt_s, tc, as_mz, fixed, nf, n_bins=24)
+    obs = np.zeros_like(probs)
+    for k in range(3):
+        obs[k], _ = np.histogram(t1[kind == k], bins=edges)
+    exp = probs * n
+    cells = exp > 5
+    chi2 = float(np.sum((obs[cells] - exp[cells]) ** 2 / exp[cells]))
+    chi2 += (np.sum(~emitted) - p_none * n) ** 2 / (p_none * n)
+    ndf = int(cells.sum())
+    spline = interpolate.CubicSpline(lt, np.log(delta))
+    cdf = lambda t: (np.exp(spline(np.log(t))) - p_none) / (1 - p_none)
+    ks = stats.kstest(t1[emitted], cdf).pvalue
+    flav_p = stats.chisquare(flavours).pvalue
+    return {"chi2_ndf": chi2 / ndf, "ndf": ndf, "ks": ks, "flavour_p": flav_p, "flavours": flavours,
+            "kinds": np.bincount(kind[emitted], minlength=3), "expected_kinds": probs.sum(axis=1) * n}
+
+
+@pytest.mark.parametrize("fixed", [1, 0])
+def test_gluon_branches_match_exact_sudakov(oracle_mod, fixed):
+    """From the q g qbar state, the first emission's scale and kind (q->qg,
+    g->gg, g->q qbar) follow rho_k(t) prod Delta, binned chi^2/ndf < 2 and KS
+    p > 1e-3, at fixed and running alpha_s; the g->q qbar flavours are equally
+    shared (chi^2 p > 1e-3)."""
+    r = _qgq_first_emission(oracle_mod, fixed)
+    assert r["chi2_ndf"] < 2.0, r
+    assert r["ks"] > 1e-3, r
+    assert r["flavour_p"] > 1e-3, r
+    assert r["kinds"][2] > 2000, r  # the g->q qbar branch is well populated
+
+
+@pytest.mark.parametrize("mutation", [1 << 14, 1 << 15, 1 << 16])
+def test_gluon_pin_catches_planted_mistakes(oracle_mod, mutation):
+    """n_f - 1 g->q qbar kernels, both kernels of a trial slot drawing the
+    same uniform, or g->gg without the half weight each break the pin."""
+    r = _qgq_first_emission(oracle_mod, 1, mutation=mutation)
+    assert r["chi2_ndf"] > 10.0 or r["ks"] < 1e-6 or r["flavour_p"] < 1e-6, r
