@@ -41,11 +41,12 @@ def split_collinear(p, i, z):
 
 def planar_polygon(n, sqrt_s, eps, rng):
     """n >= 3 partons on a regular polygon in a randomly oriented plane, each
-    energy perturbed by a relative eps, then corrected along cos and sin of
-    the polygon angles so that the momenta still sum to zero, and rescaled to
-    sum to sqrt(s): several thrust partitions are then equal to a relative
-    ~eps."""
-    ang = 2.0 * np.pi * np.arange(n) / n
+    angle moved by a relative eps of the spacing and each energy by a
+    relative eps, then the energies corrected along cos and sin of the angles
+    so that the momenta still sum to zero, and rescaled to sum to sqrt(s):
+    several thrust partitions, and several Durham pairs, are then equal to a
+    relative ~eps (the angle jitter keeps pairs from tying exactly)."""
+    ang = 2.0 * np.pi * (np.arange(n) + eps * rng.uniform(-1.0, 1.0, n)) / n
     cs, sn = np.cos(ang), np.sin(ang)
     e = (sqrt_s / n) * (1.0 + eps * rng.uniform(-1.0, 1.0, n))
     m = np.array([[np.sum(cs * cs), np.sum(sn * cs)], [np.sum(cs * sn), np.sum(sn * sn)]])
