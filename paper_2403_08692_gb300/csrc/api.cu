@@ -121,6 +121,10 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   d.ln_mz2_f = static_cast<float>(std::log(kMZ * kMZ));
   d.seed_lo = static_cast<uint32_t>(p.seed);
   d.seed_hi = static_cast<uint32_t>(p.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    d.rk[2 * r] = d.seed_lo + static_cast<uint32_t>(r) * 0x9E3779B9u;
+    d.rk[2 * r + 1] = d.seed_hi + static_cast<uint32_t>(r) * 0xBB67AE85u;
+  }
   return d;
 }
 

@@ -37,6 +37,10 @@ struct DevParams {
   double alphas_mz, as_over;  // alpha_s(m_Z) and the overestimate alpha_s(t_C)
   double b0;                  // one-loop beta_0 = (33 - 2 n_f) / (12 pi)
   uint32_t seed_lo, seed_hi;
+  // Philox key schedule (Weyl sequence of the seed), rounds 0..9: key words
+  // rk[2r], rk[2r+1].  It depends on the seed only, so the host forms it once
+  // and every round reads its key words from the launch parameters.
+  uint32_t rk[20];
   int nf, fixed, max_steps;
   int trial_mode;  // GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE
   double ln_tc;                       // ln t_C
@@ -161,20 +165,17 @@ struct U4 {
   uint32_t x, y, z, w;
 };
 
-__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                       uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t lo0 = 0xD2511F53u * c0;
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
     const uint32_t lo1 = 0xCD9E8D57u * c2;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-    c0 = hi1 ^ c1 ^ k0;
+    c0 = hi1 ^ c1 ^ rk[2 * r];
     c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
+    c2 = hi0 ^ c3 ^ rk[2 * r + 1];
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return U4{c0, c1, c2, c3};
 }
@@ -198,7 +199,7 @@ struct Uniforms {
 
 __device__ __forceinline__ Uniforms draw2(const DevParams& P, uint32_t ev, uint32_t step, uint32_t slot,
                                           uint32_t purpose) {
-  const U4 r = philox10(ev, step, slot, purpose, P.seed_lo, P.seed_hi);
+  const U4 r = philox10(ev, step, slot, purpose, P.rk);
   return Uniforms{to_unit(r.x, r.y), to_unit(r.z, r.w)};
 }
 
