@@ -124,7 +124,7 @@ typedef struct gaps_layout {
                              of the last gaps_observables call: 4 thrust searches run in FP64, 5 Durham
                              merges with several FP64 candidates, 8 finished events left without
                              observables for a parton count outside 2..capacity; 6 the persistent
-                             form's event cursor;
+                             form's event cursor; 9 the job count of a multi-job batch;
                              7 scratch of the plain form's list rebuild; 21..23 the plain form's
                              active-list lengths and 24..26 its deferred-emission counts, rotating
                              over three launches; 10..12 and 18..20 the same for the serving pool;
@@ -132,6 +132,8 @@ typedef struct gaps_layout {
                              29..31 and 13..15 the emission-task cursors of the plain form's and the
                              pool's step launches */
   int64_t hist;           /* double [GAPS_HIST_DOUBLES]: histogram accumulator of gaps_run */
+  int64_t hist_fixed;     /* uint64 [GAPS_MAX_JOBS][GAPS_HIST_FIXED_WORDS]: fixed-point scratch of
+                             gaps_histograms */
   int64_t stats;          /* gaps_stats: statistics accumulator of gaps_run */
   int64_t jobs;           /* job table of a multi-job batch (library-internal, GAPS_MAX_JOBS entries) */
   int64_t job_begin;      /* int64 [GAPS_MAX_JOBS + 1]: first batch event of every job */
@@ -163,6 +165,18 @@ enum { GAPS_ACTIVE = 0, GAPS_DONE = 1, GAPS_OVERFLOW = 2, GAPS_STEP_LIMIT = 3, G
  * [0, 0.4]. */
 enum { GAPS_N_OBS = 8, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102 };
 #define GAPS_HIST_DOUBLES (GAPS_N_OBS * GAPS_HIST_ROW * 3)
+
+/* Exact histogram accumulators (gaps_histograms_fixed): per cell (observable
+ * h, bin b: cell = h * GAPS_HIST_ROW + b) five uint64 words -- sum w as a
+ * two's-complement 128-bit integer in units of 2^-k_w pb (words 5 cell, 5
+ * cell + 1: low, high), sum w^2 likewise in units of 2^-k_w2 pb^2 (words
+ * 5 cell + 2, 5 cell + 3) and the entries (word 5 cell + 4).  Every weight is
+ * rounded once to its unit; the sums are then exact, so they do not depend on
+ * the order of the fills and two accumulators of the same job merge exactly
+ * by 128-bit addition.  gaps_hist_fixed_scales gives k_w and k_w2 (chosen so
+ * that every weight the job's matrix element can give stays below 2^62
+ * units). */
+#define GAPS_HIST_FIXED_WORDS (GAPS_N_OBS * GAPS_HIST_ROW * 5)
 
 /* Totals over a batch, reduced on the device. */
 typedef struct gaps_stats {
@@ -342,10 +356,28 @@ int gaps_observables(const gaps_params* params, const gaps_batch* batch, void* s
 
 /* Sec. 3.2 (atomic histogramming): add the batch's observables, weighted by
  * the ME weight, to hist_device (GAPS_HIST_DOUBLES doubles, device memory,
- * not cleared by this call).  Only events with status GAPS_DONE and valid ==
- * 0 are filled.  Asynchronous. */
+ * not cleared by this call; n_jobs sets for a multi-job batch).  Only events
+ * with status GAPS_DONE and valid == 0 are filled.  The fills are summed
+ * exactly in fixed point (gaps_histograms_fixed) and converted once, so the
+ * result does not depend on the order of the fills.  Asynchronous. */
 int gaps_histograms(const gaps_params* params, const gaps_batch* batch, double* hist_device,
                     void* stream);
+
+/* gaps_histograms' exact fixed-point form: add the batch's fills to
+ * acc_device (device memory, GAPS_HIST_FIXED_WORDS uint64 per set, not
+ * cleared; one set per job for a multi-job batch).  Only events with status
+ * GAPS_DONE and valid == 0 are filled.  gaps_histograms accumulates this way
+ * in the workspace and adds the converted sums to its double histograms, so
+ * its results are bitwise reproducible too.  Asynchronous. */
+int gaps_histograms_fixed(const gaps_params* params, const gaps_batch* batch, uint64_t* acc_device, void* stream);
+
+/* The fixed-point exponents k_w, k_w2 of a job's accumulators (host only). */
+int gaps_hist_fixed_scales(const gaps_params* params, int32_t* k_w, int32_t* k_w2);
+
+/* One fixed-point set (host memory) as double histograms (host memory,
+ * GAPS_HIST_DOUBLES, overwritten): sum w, sum w^2, entries per cell, each
+ * converted with one rounding.  Host only. */
+int gaps_hist_fixed_to_double(const gaps_params* params, const uint64_t* acc_host, double* hist_host);
 
 /* Reduce the batch's per-event counters into *stats_device (device memory,
  * one gaps_stats).  Asynchronous. */

@@ -1,5 +1,6 @@
 // C ABI entry points (include/gaps.h): argument checks, workspace layout,
 // launch sequencing and the host all-done loop of the plain shower form.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -67,6 +68,7 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->tasks = take(2 * static_cast<int64_t>(kEmitTaskBytes) * n);
   L->counters = take(8 * kCounterWords);
   L->hist = take(8 * GAPS_HIST_DOUBLES);
+  L->hist_fixed = take(8 * static_cast<int64_t>(GAPS_MAX_JOBS) * GAPS_HIST_FIXED_WORDS);
   L->stats = take(sizeof(gaps_stats));
   L->jobs = take(static_cast<int64_t>(sizeof(DevParams)) * GAPS_MAX_JOBS);
   L->job_begin = take(8 * (GAPS_MAX_JOBS + 1));
@@ -86,6 +88,18 @@ int check_batch(const gaps_batch* b) {
 }  // namespace
 
 int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+// Fixed-point histogram exponents of a job: every weight its matrix element
+// can give, w = a (1 + cos^2) + b cos, has |w| <= 2 |a| + |b| < 2^e, so
+// |w| 2^(62 - e) and w^2 2^(62 - 2 e) stay below 2^62.
+void hist_scales(const DevParams& d, int* k_w, int* k_w2) {
+  double bound = 0.0;
+  for (int f = 0; f < 5; ++f) bound = std::max(bound, 2.0 * std::fabs(d.me_a[f]) + std::fabs(d.me_b[f]));
+  int e = 0;
+  std::frexp(bound, &e);
+  *k_w = 62 - e;
+  *k_w2 = 62 - 2 * e;
+}
 
 DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
   DevParams d{};
@@ -125,6 +139,12 @@ DevParams make_dev_params(const gaps_params& p, int64_t id_offset) {
     d.rk[2 * r] = d.seed_lo + static_cast<uint32_t>(r) * 0x9E3779B9u;
     d.rk[2 * r + 1] = d.seed_hi + static_cast<uint32_t>(r) * 0xBB67AE85u;
   }
+  int k_w = 0, k_w2 = 0;
+  hist_scales(d, &k_w, &k_w2);
+  d.hist_sw = std::ldexp(1.0, k_w);
+  d.hist_sw2 = std::ldexp(1.0, k_w2);
+  d.hist_sw_inv = std::ldexp(1.0, -k_w);
+  d.hist_sw2_inv = std::ldexp(1.0, -k_w2);
   return d;
 }
 
@@ -166,6 +186,7 @@ Events make_events(const gaps_batch& b) {
   E.tasks = reinterpret_cast<EmitTask*>(base + L.tasks);
   E.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
   E.hist = reinterpret_cast<double*>(base + L.hist);
+  E.hist_fixed = reinterpret_cast<unsigned long long*>(base + L.hist_fixed);
   E.stats = reinterpret_cast<gaps_stats*>(base + L.stats);
   E.n = b.n_events;
   E.stride = b.n_events;
@@ -310,6 +331,10 @@ int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch,
   cudaError_t e = cudaMemcpyAsync(base + L.jobs, table, sizeof(DevParams) * n_jobs, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + L.job_begin, begin, sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s);
+  const unsigned long long count = static_cast<unsigned long long>(n_jobs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(reinterpret_cast<unsigned long long*>(base + L.counters) + kJobCountWord, &count,
+                        sizeof(count), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = launch_fill_job_of(reinterpret_cast<uint16_t*>(base + L.job_of),
                            reinterpret_cast<const int64_t*>(base + L.job_begin), n_jobs, batch->n_events, s);
@@ -331,8 +356,9 @@ bool config_ok(const gaps_persistent_config& c) {
 // Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
 // persistent form's event cursor).
 cudaError_t clear_shower_counters(const Events& E, cudaStream_t s) {
-  // words 0..9 and the plain form's list and task counts and emission cursors
-  cudaError_t e = cudaMemsetAsync(E.counters, 0, 10 * sizeof(unsigned long long), s);
+  // words 0..8 (word 9 keeps the job count) and the plain form's list and
+  // task counts and emission cursors
+  cudaError_t e = cudaMemsetAsync(E.counters, 0, 9 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainListWord, 0, 7 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(E.counters + kPlainEmitCursorWord, 0, 3 * sizeof(unsigned long long), s);
   return e;
@@ -635,8 +661,38 @@ int gaps_histograms(const gaps_params* params, const gaps_batch* batch, double* 
   DevParams P;
   Events E;
   if (!hist_device || prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
-  const cudaError_t e = launch_histograms(E, hist_device, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = launch_histograms(P, nullptr, E, hist_device, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_histograms_fixed(const gaps_params* params, const gaps_batch* batch, uint64_t* acc_device, void* stream) {
+  DevParams P;
+  Events E;
+  if (!acc_device || prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  const cudaError_t e = launch_hist_fixed(P, nullptr, E, reinterpret_cast<unsigned long long*>(acc_device),
+                                          static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_hist_fixed_scales(const gaps_params* params, int32_t* k_w, int32_t* k_w2) {
+  if (!params || !k_w || !k_w2 || gaps_check_params(params) != GAPS_OK) return GAPS_ERR_INVALID;
+  int a = 0, b = 0;
+  hist_scales(make_dev_params(*params, 0), &a, &b);
+  *k_w = a;
+  *k_w2 = b;
+  return GAPS_OK;
+}
+
+int gaps_hist_fixed_to_double(const gaps_params* params, const uint64_t* acc_host, double* hist_host) {
+  if (!params || !acc_host || !hist_host || gaps_check_params(params) != GAPS_OK) return GAPS_ERR_INVALID;
+  const DevParams d = make_dev_params(*params, 0);
+  for (int cell = 0; cell < GAPS_N_OBS * GAPS_HIST_ROW; ++cell) {
+    const uint64_t* c = acc_host + 5 * cell;
+    hist_host[3 * cell + 0] = fixed128_to_double(c[0], c[1], d.hist_sw_inv);
+    hist_host[3 * cell + 1] = fixed128_to_double(c[2], c[3], d.hist_sw2_inv);
+    hist_host[3 * cell + 2] = static_cast<double>(c[4]);
+  }
+  return GAPS_OK;
 }
 
 int gaps_reduce_stats(const gaps_batch* batch, gaps_stats* stats_device, void* stream) {
@@ -800,10 +856,10 @@ int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const
   const Events V = sub_view(E, ev_begin, n_events);
   cudaError_t e = launch_validate(P, V, s);
   if (e == cudaSuccess) e = launch_observables(P, V, E.buckets, E.order, s);
-  Events H = V;  // one histogram set: the range is one job
+  Events H = V;  // one histogram set: the range is one job, at its scales
   H.jobs = nullptr;
   H.job_of = nullptr;
-  if (e == cudaSuccess) e = launch_histograms(H, hist_device, s);
+  if (e == cudaSuccess) e = launch_histograms(P, E.jobs + job_slot, H, hist_device, s);
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 

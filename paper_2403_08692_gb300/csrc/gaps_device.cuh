@@ -54,6 +54,11 @@ struct DevParams {
   float tcf, as2pi_f, lg2_tc_f, as_mz_over_f, as_b0_f, ln_mz2_f;
   // Philox event id of batch event ev: ev + id_offset (mod 2^32)
   int64_t id_offset;
+  // Fixed-point histogram units: w and w^2 are accumulated as integers
+  // w 2^k_w and w^2 2^k_w2 (hist_sw = 2^k_w, hist_sw2 = 2^k_w2, and their
+  // inverses), with k chosen so that every weight the job can give stays
+  // within 2^62.
+  double hist_sw, hist_sw2, hist_sw_inv, hist_sw2_inv;
 };
 
 // Everything GenerateEmission needs about an accepted winner (56 bytes:
@@ -77,6 +82,16 @@ constexpr int kSliceCursorWord = 28;
 // plain form words 29..31, serving pool words 13..15.
 constexpr int kPlainEmitCursorWord = 29;
 constexpr int kPoolEmitCursorWord = 13;
+// The number of jobs of a multi-job batch (written by gaps_set_jobs).
+constexpr int kJobCountWord = 9;
+
+// The signed 128-bit fixed-point value (lo, hi) times scale_inv (= 2^-k) as
+// a double: hi 2^64 + lo, each part converted, their sum rounded once (the
+// power-of-two scalings are exact).  Host and device run the same code.
+__host__ __device__ inline double fixed128_to_double(unsigned long long lo, unsigned long long hi, double scale_inv) {
+  const double h = static_cast<double>(static_cast<long long>(hi)) * 18446744073709551616.0;
+  return (h + static_cast<double>(lo)) * scale_inv;
+}
 
 // Pointers into the workspace (gaps_layout) for one batch.
 struct Events {
@@ -98,6 +113,7 @@ struct Events {
   EmitTask* tasks;  // [2][n] scratch: the plain form's deferred emissions
   unsigned long long* counters;
   double* hist;
+  unsigned long long* hist_fixed;  // [GAPS_MAX_JOBS][GAPS_HIST_FIXED_WORDS] fixed-point histogram scratch
   gaps_stats* stats;
   // Multi-job batches: parameters per job and the job of every event
   // (NULL for a single-job batch, whose parameters come with the launch).

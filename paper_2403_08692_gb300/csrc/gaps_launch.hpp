@@ -67,9 +67,17 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
 // Make CUDA load the observables' kernels on the current device now (it
 // loads modules lazily by default, at their first use).
 cudaError_t preload_observables();
-// Single-job batch: hist is one histogram set; multi-job batch (E.jobs set):
-// hist holds one set per job.
-cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s);
+// Histograms of the batch added to hist (doubles): one set for a single-job
+// batch (scales from P, or from the device job-table entry *scale_src when
+// given), one set per job for a multi-job batch (E.jobs and E.job_of set;
+// the job count in counter word kJobCountWord).  Accumulated exactly in
+// fixed point in the workspace's hist_fixed scratch, then converted.
+cudaError_t launch_histograms(const DevParams& P, const DevParams* scale_src, const Events& E, double* hist,
+                              cudaStream_t s);
+// The exact fixed-point fills alone, added to acc (GAPS_HIST_FIXED_WORDS per
+// set, not cleared).
+cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, const Events& E, unsigned long long* acc,
+                              cudaStream_t s);
 cudaError_t launch_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s);
 

@@ -1,5 +1,7 @@
 // Event validation, atomic histogramming of the observables (Sec. 3.2) and
 // batch statistics.
+#include <algorithm>
+
 #include "gaps_launch.hpp"
 
 namespace gaps {
@@ -143,22 +145,48 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
   return f < 0.0f ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
 }
 
-// Weighted fills (sum w, sum w^2, entries) of every finished valid event.
-// The lanes of a warp that fill the same cell are merged first (match on
-// the cell, the first lane sums its peers' weights from shared memory), so
-// a crowded bin costs one atomic per warp, not one per event.  Single-job
-// batch (kJobs false): block-private histograms in shared memory, merged
-// with one atomic per cell; multi-job batch: every event fills its own
-// job's histograms (hist + job * GAPS_HIST_DOUBLES) with global atomics.
+// ------------------------------------------- fixed-point accumulation
+// Weighted fills (sum w, sum w^2, entries) in exact integer arithmetic, so
+// the histograms do not depend on the order of the fills (and merge exactly
+// across batches or ranks): w is taken in units of 2^-k_w (w 2^k_w rounded
+// to an integer, |w 2^k_w| <= 2^62 for every weight the job's matrix element
+// can give) and w^2 in units of 2^-k_w2; each cell sums them as 128-bit
+// two's-complement integers (low word, high word) and counts its entries.
+constexpr int kCells = GAPS_N_OBS * GAPS_HIST_ROW;
+
+// Add the signed 128-bit value (lo, hi) to the accumulator at acc[0..1]:
+// the low words add atomically, and the carry out of this addition (read
+// from the value the low word held) goes to the high word.
+__device__ __forceinline__ void add128(unsigned long long* acc, unsigned long long lo, long long hi) {
+  const unsigned long long old = atomicAdd(acc, lo);
+  const long long up = hi + (old + lo < old ? 1 : 0);
+  if (up != 0) atomicAdd(acc + 1, static_cast<unsigned long long>(up));
+}
+
+// Every finished valid event fills each observable's bin.  The lanes of a
+// warp that fill the same cell are merged first (match on the cell; the
+// first lane sums its peers' fixed-point weights from shared memory as
+// 128-bit integers), so a crowded bin costs one atomic per warp, not one per
+// event.  Single-job batch (kJobs false): block-private accumulators in
+// shared memory, merged into acc once per block; scales from P, or from
+// *scale_src (a job-table entry on the device) when it is given.  Multi-job
+// batch: every event fills its own job's accumulators (acc + job *
+// GAPS_HIST_FIXED_WORDS) with global atomics, at its job's scales.
 template <bool kJobs>
-__global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
+__global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams* scale_src, Events E,
+                                                    unsigned long long* acc) {
   constexpr bool kShared = !kJobs;  // (global atomics for one job measured 70 % slower)
-  __shared__ double sh[kShared ? GAPS_HIST_DOUBLES : 1];
-  __shared__ double s_w[256], s_w2[256];
+  __shared__ unsigned long long sh[kShared ? GAPS_HIST_FIXED_WORDS : 1];
+  __shared__ long long s_w[256], s_w2[256];
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
   if (kShared) {
-    for (int i = tid; i < GAPS_HIST_DOUBLES; i += blockDim.x) sh[i] = 0.0;
+    for (int i = tid; i < GAPS_HIST_FIXED_WORDS; i += blockDim.x) sh[i] = 0ull;
     __syncthreads();
+  }
+  double sc_w = P.hist_sw, sc_w2 = P.hist_sw2;
+  if (!kJobs && scale_src) {
+    sc_w = scale_src->hist_sw;
+    sc_w2 = scale_src->hist_sw2;
   }
   const int64_t N = E.n;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -166,34 +194,72 @@ __global__ void __launch_bounds__(256) k_histograms(Events E, double* hist) {
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + warp0; base < N; base += stride) {
     const int64_t ev = base + lane;
     const bool fill = ev < N && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
-    const double w = fill ? E.weight[ev] : 0.0;
-    s_w[tid] = w;
-    s_w2[tid] = w * w;
     const int job = kJobs && fill ? static_cast<int>(E.job_of[ev]) : 0;
+    if (kJobs && fill) {
+      sc_w = E.jobs[job].hist_sw;
+      sc_w2 = E.jobs[job].hist_sw2;
+    }
+    const double w = fill ? E.weight[ev] : 0.0;
+    // exact scalings by powers of two, then one rounding to an integer
+    s_w[tid] = __double2ll_rn(w * sc_w);
+    s_w2[tid] = __double2ll_rn((w * w) * sc_w2);
     __syncwarp();
     for (int h = 0; h < GAPS_N_OBS; ++h) {
       const int bin = fill ? hist_bin(h, E.obs[h * E.stride + ev]) : -1;
-      const int cell = bin < 0 ? -1 : job * GAPS_HIST_ROW * GAPS_N_OBS + h * GAPS_HIST_ROW + bin;
+      const int cell = bin < 0 ? -1 : job * kCells + h * GAPS_HIST_ROW + bin;
       const unsigned peers = __match_any_sync(0xffffffffu, cell);
       if (cell >= 0 && lane == __ffs(peers) - 1) {
-        double sw = 0.0, sw2 = 0.0;
+        unsigned long long lo1 = 0, lo2 = 0;
+        long long hi1 = 0, hi2 = 0;
         for (unsigned m = peers; m; m &= m - 1) {
           const int l = __ffs(m) - 1;
-          sw += s_w[warp0 + l];
-          sw2 += s_w2[warp0 + l];
+          const long long a = s_w[warp0 + l], b = s_w2[warp0 + l];
+          const unsigned long long n1 = lo1 + static_cast<unsigned long long>(a);
+          hi1 += (a < 0 ? -1 : 0) + (n1 < lo1 ? 1 : 0);
+          lo1 = n1;
+          const unsigned long long n2 = lo2 + static_cast<unsigned long long>(b);
+          hi2 += (b < 0 ? -1 : 0) + (n2 < lo2 ? 1 : 0);
+          lo2 = n2;
         }
-        double* c = (kShared ? sh : hist) + static_cast<size_t>(cell) * 3;
-        atomicAdd(c + 0, sw);
-        atomicAdd(c + 1, sw2);
-        atomicAdd(c + 2, static_cast<double>(__popc(peers)));
+        unsigned long long* c = (kShared ? sh : acc) + static_cast<size_t>(cell) * 5;
+        add128(c + 0, lo1, hi1);
+        add128(c + 2, lo2, hi2);
+        atomicAdd(c + 4, static_cast<unsigned long long>(__popc(peers)));
       }
     }
     __syncwarp();
   }
   if (kShared) {
     __syncthreads();
-    for (int i = tid; i < GAPS_HIST_DOUBLES; i += blockDim.x)
-      if (sh[i] != 0.0) atomicAdd(hist + i, sh[i]);
+    for (int cell = tid; cell < kCells; cell += blockDim.x) {
+      const unsigned long long* c = sh + cell * 5;
+      if (c[4] == 0ull) continue;
+      unsigned long long* g = acc + cell * 5;
+      add128(g + 0, c[0], static_cast<long long>(c[1]));
+      add128(g + 2, c[2], static_cast<long long>(c[3]));
+      atomicAdd(g + 4, c[4]);
+    }
+  }
+}
+
+// Add the accumulators of sets 0 .. n_sets - 1 (n_sets: *n_sets_dev when
+// given) to hist as doubles, set j at hist + j * GAPS_HIST_DOUBLES.  Scales:
+// P, or *scale_src, or the job table (multi-job sets).
+__global__ void __launch_bounds__(256) k_hist_finalize(DevParams P, const DevParams* scale_src, const DevParams* jobs,
+                                                       int n_sets, const unsigned long long* n_sets_dev,
+                                                       unsigned long long* acc, double* hist) {
+  const int sets = n_sets_dev ? static_cast<int>(*n_sets_dev) : n_sets;
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < static_cast<int64_t>(sets) * kCells;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int job = static_cast<int>(k / kCells), cell = static_cast<int>(k % kCells);
+    const DevParams& S = jobs ? jobs[job] : (scale_src ? *scale_src : P);
+    unsigned long long* c = acc + k * 5;
+    double* h = hist + static_cast<size_t>(job) * GAPS_HIST_DOUBLES + static_cast<size_t>(cell) * 3;
+    if (c[4] != 0ull) {
+      h[0] += fixed128_to_double(c[0], c[1], S.hist_sw_inv);
+      h[1] += fixed128_to_double(c[2], c[3], S.hist_sw2_inv);
+      h[2] += static_cast<double>(c[4]);
+    }
   }
 }
 
@@ -289,20 +355,43 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s)
 #define GAPS_HIST_BLOCKS_PER_SM 2
 #endif
 
-cudaError_t launch_histograms(const Events& E, double* hist, cudaStream_t s) {
+cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, const Events& E, unsigned long long* acc,
+                              cudaStream_t s) {
   if (E.n == 0) return cudaSuccess;
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (E.n + 255) / 256;
   const int64_t most = static_cast<int64_t>(GAPS_HIST_BLOCKS_PER_SM) * sms;
-  const unsigned blocks = static_cast<unsigned>(want < most ? want : most);
-  if (E.jobs) {
-    k_histograms<true><<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(E, hist);
+  if (E.jobs && E.job_of) {
+    k_hist_fixed<true><<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(P, nullptr, E, acc);
   } else {
-    k_histograms<false><<<blocks, 256, 0, s>>>(E, hist);
+    k_hist_fixed<false><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, scale_src, E, acc);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_hist_finalize(const DevParams& P, const DevParams* scale_src, const DevParams* jobs, int n_sets,
+                                 const unsigned long long* n_sets_dev, unsigned long long* acc, double* hist,
+                                 cudaStream_t s) {
+  const int64_t cells = static_cast<int64_t>(n_sets) * kCells;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((cells + 255) / 256, 1024));
+  k_hist_finalize<<<blocks, 256, 0, s>>>(P, scale_src, jobs, n_sets, n_sets_dev, acc, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histograms(const DevParams& P, const DevParams* scale_src, const Events& E, double* hist,
+                              cudaStream_t s) {
+  if (E.n == 0) return cudaSuccess;
+  const bool multi = E.jobs && E.job_of;
+  // every job slot of a multi-job batch (the job count is on the device)
+  const size_t sets = multi ? GAPS_MAX_JOBS : 1;
+  cudaError_t e = cudaMemsetAsync(E.hist_fixed, 0, sets * GAPS_HIST_FIXED_WORDS * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_hist_fixed(P, scale_src, E, E.hist_fixed, s);
+  if (e == cudaSuccess)
+    e = launch_hist_finalize(P, scale_src, multi ? E.jobs : nullptr, multi ? GAPS_MAX_JOBS : 1,
+                             multi ? E.counters + kJobCountWord : nullptr, E.hist_fixed, hist, s);
+  return e;
 }
 
 cudaError_t launch_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n, cudaStream_t s) {

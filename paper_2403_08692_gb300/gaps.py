@@ -13,6 +13,7 @@ ACTIVE, DONE, OVERFLOW, STEP_LIMIT, PENDING = 0, 1, 2, 3, 4
 SHOWER_PLAIN, SHOWER_PERSISTENT = 0, 1
 N_OBS, N_BINS, HIST_ROW = 8, 100, 102
 HIST_DOUBLES = N_OBS * HIST_ROW * 3
+HIST_FIXED_WORDS = N_OBS * HIST_ROW * 5
 
 
 class Params(C.Structure):
@@ -39,7 +40,7 @@ _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "
                   "n_partons", "status", "n_steps", "n_emissions", "n_winners", "n_trials",
                   "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "tasks",
                   "counters",
-                  "hist",
+                  "hist", "hist_fixed",
                   "stats", "jobs", "job_begin", "job_of", "job_done", "total_bytes"]
 
 
@@ -85,6 +86,9 @@ SIGNATURES = {
     "gaps_observables": (C.c_int, [_P(Params), _P(Batch), C.c_void_p]),
     "gaps_histograms": (C.c_int, [_P(Params), _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_reduce_stats": (C.c_int, [_P(Batch), C.c_void_p, C.c_void_p]),
+    "gaps_histograms_fixed": (C.c_int, [_P(Params), _P(Batch), C.c_void_p, C.c_void_p]),
+    "gaps_hist_fixed_scales": (C.c_int, [_P(Params), _P(C.c_int32), _P(C.c_int32)]),
+    "gaps_hist_fixed_to_double": (C.c_int, [_P(Params), C.c_void_p, C.c_void_p]),
     "gaps_run": (C.c_int, [_P(Params), _P(Batch), C.c_int, _P(C.c_double), _P(Stats), C.c_void_p]),
     "gaps_event_shapes_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
@@ -247,6 +251,31 @@ def observables(p, ws, stream=None):
 def histograms(p, ws, hist_device, stream=None):
     _check(load().gaps_histograms(_pp(p), C.byref(_batch(ws)), C.c_void_p(hist_device.data_ptr()),
                                   _stream_handle(stream)), "gaps_histograms")
+
+
+def histograms_fixed(p, ws, acc_device, stream=None):
+    """gaps_histograms_fixed: add the batch's exact fixed-point fills to
+    acc_device (a CUDA int64 tensor of HIST_FIXED_WORDS per set)."""
+    _check(load().gaps_histograms_fixed(_pp(p), C.byref(_batch(ws)), C.c_void_p(acc_device.data_ptr()),
+                                        _stream_handle(stream)), "gaps_histograms_fixed")
+
+
+def hist_fixed_scales(p):
+    """(k_w, k_w2): the fixed-point exponents of a job's accumulators."""
+    a, b = C.c_int32(0), C.c_int32(0)
+    _check(load().gaps_hist_fixed_scales(C.byref(p), C.byref(a), C.byref(b)), "gaps_hist_fixed_scales")
+    return a.value, b.value
+
+
+def hist_fixed_to_double(p, acc):
+    """One fixed-point set (host int64/uint64 numpy array of HIST_FIXED_WORDS)
+    as a float64 numpy array of HIST_DOUBLES."""
+    import numpy as np
+    a = np.ascontiguousarray(acc).view(np.uint64)
+    out = np.empty(HIST_DOUBLES, dtype=np.float64)
+    _check(load().gaps_hist_fixed_to_double(C.byref(p), C.c_void_p(a.ctypes.data), C.c_void_p(out.ctypes.data)),
+           "gaps_hist_fixed_to_double")
+    return out
 
 
 def reduce_stats(ws, stats_device, stream=None):
