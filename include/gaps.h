@@ -282,6 +282,56 @@ int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_ou
 int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const gaps_batch* pool,
                      double* hist_device, void* stream);
 
+/* ------------------------------------------- serving: the C scheduler */
+
+/* The serving loop as a C API: continuous batching over one pool, with the
+ * schedule kept by the library (Sec. 2 / App. C's host driver turned into a
+ * request loop).  The caller owns the pool workspace (gaps_batch, first_event
+ * 0) and hist_device (device memory, max_jobs * GAPS_HIST_DOUBLES doubles,
+ * one set per job slot); the server keeps host state and a little pinned
+ * host memory, never device memory.  Jobs are submitted as they arrive;
+ * every gaps_poll advances the schedule by one step:
+ *  - admission in submission order: a job takes a free slot (< max_jobs) and
+ *    the first free contiguous range of the pool that holds its events (first
+ *    fit, freed neighbours coalesced), its matrix elements are generated in
+ *    place and its events join the live list (gaps_pool_admit);
+ *  - one round: every live event runs up to cycles_per_round more veto
+ *    cycles, by one time-sliced persistent launch (GAPS_SERVE_SLICE,
+ *    gaps_pool_slice with cfg, NULL = default shape) or by that many
+ *    plain-form steps (GAPS_SERVE_STEPS, gaps_pool_cycles);
+ *  - progress read one round behind (the GPU keeps a round queued);
+ *  - a job whose events have all finished is finalised on its range
+ *    (gaps_pool_finish) and its histograms copied to the host; its range is
+ *    reused at once, its slot once the copy has landed.
+ * Every event equals the event a single-job batch of its job produces, and
+ * the histograms are exact fixed-point sums converted once, so a job's
+ * histograms are bitwise those of the same job run alone.  All calls on one
+ * server must come from one host thread, on its stream. */
+enum { GAPS_SERVE_SLICE = 0, GAPS_SERVE_STEPS = 1 };
+typedef struct gaps_server gaps_server;
+
+/* Create a server over the pool (resets its lists and counters).  max_jobs
+ * 1..GAPS_MAX_JOBS, cycles_per_round 1..255, mode GAPS_SERVE_SLICE or
+ * GAPS_SERVE_STEPS; cfg may be NULL.  *out = NULL on failure. */
+int gaps_server_create(const gaps_batch* pool, double* hist_device, int32_t max_jobs, int32_t cycles_per_round,
+                       int32_t mode, const gaps_persistent_config* cfg, void* stream, gaps_server** out);
+/* Queue a job (params as for gaps_generate_me; 1 <= n_events <= the pool's
+ * events; event ids first_event + k).  *job_id identifies it in gaps_poll.
+ * Host only: the GPU work starts at the next poll. */
+int gaps_submit(gaps_server* server, const gaps_params* params, int64_t n_events, uint32_t first_event,
+                uint64_t* job_id);
+/* One step of the schedule, then *done = 1 if job job_id has finished, with
+ * its histograms copied to host_hist (GAPS_HIST_DOUBLES doubles, may be NULL;
+ * the job is then forgotten), else *done = 0.  GAPS_ERR_INVALID for a job id
+ * that was never submitted or was already reported finished.  May wait for
+ * the round before the last to finish on the GPU. */
+int gaps_poll(gaps_server* server, uint64_t job_id, double* host_hist, int32_t* done);
+/* Jobs waiting for admission, jobs live or being finalised, and finished jobs
+ * not yet reported by gaps_poll (each may be NULL). */
+int gaps_server_counts(const gaps_server* server, int64_t* queued, int64_t* live, int64_t* finished_unread);
+/* Wait for the server's work on its stream and free it. */
+void gaps_server_destroy(gaps_server* server);
+
 /* ------------------------------------------------------------- hot path */
 
 /* App. B: draw each event's flavour, cos(theta) and phi, set the quark and
@@ -435,27 +485,6 @@ int gaps_event_shapes_noalloc(const double* px, const double* py, const double* 
 
 /* --------------------------------------------------------------- misc */
 
-/* Measurement helper (no counterpart in the paper): FP64 results per second
- * of this GPU with every SM busy, for DFMA, log, exp, division, sqrt,
- * sincospi and the shower's own logarithm (gaps_log_fp64_*), in
- * host_rates[0..6] (caller-owned, 7 doubles).  device_sink: one device
- * double, never written in practice.  Synchronous; about 60 ms. */
-int gaps_probe_fp64_rates(double* device_sink, double* host_rates, void* stream);
-
-/* The FP64 natural logarithm the shower kernels use for the winning trial's
- * scale, ln t' = ln t + ln(r)/c (Eq. (A.5) in log form), and for the dipole
- * cache's ln(z+/z-) (Eq. (A.4)): P. T. P. Tang's table-driven method (ACM
- * TOMS 16 (1990) 378), error below one ulp for positive normal x; other
- * inputs take the CUDA library's log.  y[i] = ln x[i] for 0 <= i < n.
- * _host: host arrays, computed on the calling thread.  _device: device
- * arrays, asynchronous on `stream`.  Both return GAPS_ERR_INVALID for n < 0
- * or a null array with n > 0.  Exported for the accuracy tests. */
-int gaps_log_fp64_host(const double* x, double* y, int64_t n);
-/* The double -> float conversion (round to nearest even) the kernels do with
- * integer instructions, host build, for the tests: y[i] = (float) x[i].
- * GAPS_ERR_INVALID for n < 0 or a null array with n > 0. */
-int gaps_f32_from_f64_host(const double* x, float* y, int64_t n);
-int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream);
 const char* gaps_strerror(int status);
 const char* gaps_last_cuda_error(void);
 /* Library version as major * 10000 + minor * 100 + patch. */

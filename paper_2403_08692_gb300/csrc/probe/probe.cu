@@ -1,15 +1,31 @@
+// Measurement and test library (libgaps_probe.so, include/gaps_probe.h),
+// kept out of the product library libgaps.so.
+//
 // FP64 throughput probe: how many DFMA, log, exp, division, square root,
 // sincospi and table-driven log (log_fp64) results per second this GPU
 // delivers, with every SM busy.  The benchmark uses it to express the
 // shower's required FP64 work in DFMA-equivalents measured on the same device
-// in the same run.  Also the exported log_fp64, host and device, for the
-// accuracy tests.
-#include "gaps_launch.hpp"
+// in the same run.  Also the shower's log_fp64 and its double -> float
+// conversion, host and device builds of the same source, for the accuracy
+// tests.
+#include <cstdio>
+
+#include <cuda_runtime.h>
+
+#include "gaps.h"
+#include "gaps_probe.h"
 #include "log_fp64.cuh"
 
 namespace gaps {
 
 namespace {
+
+thread_local char g_probe_error[256] = "";
+
+int record_cuda_error(cudaError_t e) {
+  std::snprintf(g_probe_error, sizeof(g_probe_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return GAPS_ERR_CUDA;
+}
 
 constexpr int kProbeThreads = 256;
 constexpr int kChains = 4;
@@ -142,3 +158,5 @@ extern "C" int gaps_log_fp64_device(const double* x, double* y, int64_t n, void*
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GAPS_OK : record_cuda_error(e);
 }
+
+extern "C" const char* gaps_probe_last_cuda_error(void) { return g_probe_error; }

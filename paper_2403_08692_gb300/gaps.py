@@ -93,10 +93,6 @@ SIGNATURES = {
     "gaps_event_shapes_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
                                             C.c_void_p]),
-    "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
-    "gaps_log_fp64_host": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64]),
-    "gaps_f32_from_f64_host": (C.c_int, [_P(C.c_double), _P(C.c_float), C.c_int64]),
-    "gaps_log_fp64_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "gaps_pool_reset": (C.c_int, [_P(Batch), C.c_void_p]),
     "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
                                   C.c_void_p]),
@@ -104,16 +100,64 @@ SIGNATURES = {
     "gaps_pool_slice": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(PersistentConfig), C.c_void_p]),
     "gaps_pool_progress": (C.c_int, [_P(Batch), C.c_int64, _P(C.c_int64), C.c_void_p, C.c_void_p]),
     "gaps_pool_finish": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, _P(Batch), C.c_void_p, C.c_void_p]),
+    "gaps_server_create": (C.c_int, [_P(Batch), C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(PersistentConfig),
+                                     C.c_void_p, _P(C.c_void_p)]),
+    "gaps_submit": (C.c_int, [C.c_void_p, _P(Params), C.c_int64, C.c_uint32, _P(C.c_uint64)]),
+    "gaps_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, _P(C.c_int32)]),
+    "gaps_server_counts": (C.c_int, [C.c_void_p, _P(C.c_int64), _P(C.c_int64), _P(C.c_int64)]),
+    "gaps_server_destroy": (None, [C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
     "gaps_last_cuda_error": (C.c_char_p, []),
     "gaps_version": (C.c_int, []),
 }
 
+# The measurement and test library (include/gaps_probe.h), separate from the
+# product library.
+PROBE_SIGNATURES = {
+    "gaps_probe_fp64_rates": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_void_p]),
+    "gaps_log_fp64_host": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64]),
+    "gaps_f32_from_f64_host": (C.c_int, [_P(C.c_double), _P(C.c_float), C.c_int64]),
+    "gaps_log_fp64_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "gaps_probe_last_cuda_error": (C.c_char_p, []),
+}
+
 _lib = None
+_probe = None
 
 
 def library_path() -> str:
     return _build.LIB
+
+
+def probe_library_path() -> str:
+    return _build.PROBE_LIB
+
+
+def load_probe(build_if_missing: bool = True):
+    """Load libgaps_probe.so (the FP64 probe and the accuracy-test exports)."""
+    global _probe
+    if _probe is None:
+        if build_if_missing:
+            _build.build()
+        path = _build.PROBE_LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"probe library {path} is missing; build it with paper_2403_08692_gb300.build")
+        L = C.CDLL(path)
+        for name, (res, args) in PROBE_SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _probe = L
+    return _probe
+
+
+def _check_probe(code, where):
+    if code != GAPS_OK:
+        msg = f"{where}: status {code}"
+        if code == GAPS_ERR_CUDA:
+            msg += ": " + load_probe().gaps_probe_last_cuda_error().decode()
+        raise RuntimeError(msg)
+    return code
 
 
 def load(build_if_missing: bool = True):
@@ -289,8 +333,8 @@ def probe_fp64_rates(stream=None):
     import torch
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     rates = (C.c_double * 7)()
-    _check(load().gaps_probe_fp64_rates(C.c_void_p(sink.data_ptr()), rates, _stream_handle(stream)),
-           "gaps_probe_fp64_rates")
+    _check_probe(load_probe().gaps_probe_fp64_rates(C.c_void_p(sink.data_ptr()), rates, _stream_handle(stream)),
+                 "gaps_probe_fp64_rates")
     return dict(zip(("dfma", "log", "exp", "div", "sqrt", "sincospi", "log_fp64"), list(rates)))
 
 
@@ -299,8 +343,9 @@ def log_fp64_host(x):
     import numpy as np
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)
-    _check(load().gaps_log_fp64_host(x.ctypes.data_as(_P(C.c_double)), y.ctypes.data_as(_P(C.c_double)),
-                                     int(x.size)), "gaps_log_fp64_host")
+    _check_probe(load_probe().gaps_log_fp64_host(x.ctypes.data_as(_P(C.c_double)),
+                                                 y.ctypes.data_as(_P(C.c_double)), int(x.size)),
+                 "gaps_log_fp64_host")
     return y
 
 
@@ -310,8 +355,9 @@ def f32_from_f64_host(x):
     import numpy as np
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(x.shape, dtype=np.float32)
-    _check(load().gaps_f32_from_f64_host(x.ctypes.data_as(_P(C.c_double)), y.ctypes.data_as(_P(C.c_float)),
-                                         int(x.size)), "gaps_f32_from_f64_host")
+    _check_probe(load_probe().gaps_f32_from_f64_host(x.ctypes.data_as(_P(C.c_double)),
+                                                     y.ctypes.data_as(_P(C.c_float)), int(x.size)),
+                 "gaps_f32_from_f64_host")
     return y
 
 
@@ -320,8 +366,8 @@ def log_fp64_device(x, stream=None):
     import torch
     x = x.contiguous()
     y = torch.empty_like(x)
-    _check(load().gaps_log_fp64_device(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.numel()),
-                                       _stream_handle(stream)), "gaps_log_fp64_device")
+    _check_probe(load_probe().gaps_log_fp64_device(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                   int(x.numel()), _stream_handle(stream)), "gaps_log_fp64_device")
     return y
 
 
@@ -390,6 +436,60 @@ def pool_progress(ws, cycle, job_done=None, stream=None):
 def pool_finish(job_slot, ev_begin, n_events, ws, hist_device, stream=None):
     _check(load().gaps_pool_finish(int(job_slot), int(ev_begin), int(n_events), C.byref(_batch(ws)),
                                    C.c_void_p(hist_device.data_ptr()), _stream_handle(stream)), "gaps_pool_finish")
+
+
+SERVE_SLICE, SERVE_STEPS = 0, 1
+
+
+class CServer:
+    """The library's C serving scheduler (gaps_server_*, gaps_submit,
+    gaps_poll) over a pool workspace and a device histogram buffer this object
+    allocates with PyTorch (the library allocates no device memory)."""
+
+    def __init__(self, pool_events, capacity=128, max_jobs=64, cycles_per_round=8, mode=SERVE_SLICE, cfg=None,
+                 stream=None):
+        import torch
+        self.ws = Workspace(pool_events, capacity)
+        self.hist = torch.zeros((max_jobs, HIST_DOUBLES), dtype=torch.float64, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if isinstance(cfg, dict):
+            cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
+                                   int(cfg.get("blocks_per_sm", 0)), 0)
+        self._batch = _batch(self.ws)
+        h = C.c_void_p()
+        _check(load().gaps_server_create(C.byref(self._batch), C.c_void_p(self.hist.data_ptr()), int(max_jobs),
+                                         int(cycles_per_round), int(mode), C.byref(cfg) if cfg is not None else None,
+                                         _stream_handle(self.stream), C.byref(h)), "gaps_server_create")
+        self._h = h
+
+    def submit(self, p, n_events, first_event=0):
+        jid = C.c_uint64(0)
+        _check(load().gaps_submit(self._h, C.byref(p), int(n_events), int(first_event), C.byref(jid)), "gaps_submit")
+        return jid.value
+
+    def poll(self, job_id):
+        """None while the job runs, else its histograms (numpy, HIST_DOUBLES)."""
+        import numpy as np
+        out = np.empty(HIST_DOUBLES, dtype=np.float64)
+        done = C.c_int32(0)
+        _check(load().gaps_poll(self._h, C.c_uint64(job_id), C.c_void_p(out.ctypes.data), C.byref(done)), "gaps_poll")
+        return out if done.value else None
+
+    def counts(self):
+        q, l, f = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        _check(load().gaps_server_counts(self._h, C.byref(q), C.byref(l), C.byref(f)), "gaps_server_counts")
+        return q.value, l.value, f.value
+
+    def close(self):
+        if self._h:
+            load().gaps_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def run(p, ws, host_hist, mode=SHOWER_PLAIN, stream=None):

@@ -10,10 +10,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
+def _declared_functions(header=None):
     names = []
     for hdr in os.listdir(os.path.join(ROOT, "include")):
-        if not hdr.endswith(".h"):
+        if not hdr.endswith(".h") or (header is not None and hdr != header):
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -29,13 +29,24 @@ def g():
 
 
 def test_every_declared_symbol_is_exported(g):
-    names = _declared_functions()
+    """gaps.h: the product library libgaps.so; gaps_probe.h: the measurement
+    and test library libgaps_probe.so, whose symbols the product library
+    does not carry."""
+    names = _declared_functions("gaps.h")
     assert len(names) >= 14, names
     lib = C.CDLL(g.gaps.library_path())
     for n in names:
         assert hasattr(lib, n), n
     # and the binding knows every one of them, with the same names
     assert set(names) <= set(g.gaps.SIGNATURES), set(names) - set(g.gaps.SIGNATURES)
+    probe_names = _declared_functions("gaps_probe.h")
+    assert "gaps_probe_fp64_rates" in probe_names and "gaps_log_fp64_host" in probe_names
+    probe = C.CDLL(g.gaps.probe_library_path())
+    for n in probe_names:
+        assert hasattr(probe, n), n
+        assert not hasattr(lib, n), n
+    assert set(probe_names) <= set(g.gaps.PROBE_SIGNATURES)
+    assert not set(names) & set(probe_names)
 
 
 def test_header_constants_match_binding(g):

@@ -76,7 +76,7 @@ def test_special_inputs(g):
 
 
 def test_bad_arguments(g):
-    lib = g.load()
+    lib = g.gaps.load_probe()
     assert lib.gaps_log_fp64_host(None, None, -1) != 0
     assert lib.gaps_log_fp64_host(None, None, 5) != 0
     assert lib.gaps_log_fp64_host(None, None, 0) == 0
