@@ -44,6 +44,25 @@ WORK_PER_EMISSION = {"simple": 164, "div": 18, "sqrt": 7, "log": 4, "exp": 2, "s
 # peak ncu reports for this GB300), two flops per DFMA.
 DFMA_PER_SM_PER_CLOCK = 2
 
+# The oracle's arithmetic, unit by unit, as the oracle does it: every trial,
+# dipole, veto and splitting in FP64 with the library's transcendentals.
+#   per trial:    c from its kernel integral (log of (1-z-)/(1-z+), a
+#                 division), t' = t r^(1/c) = t exp(ln r / c) (log, exp,
+#                 division), the comparison
+#   per dipole:   Q^2 = 2 p_i.p_k and z+- = (1 +- sqrt(1 - 4 t_C/Q^2)) / 2
+#   per winner:   z (the kernel's inverse integral), y, alpha_s(t), and the
+#                 acceptance ratio (1-y) alpha_s P / (alpha_s^over P^over)
+#   per emission: the azimuth and the dipole map (transverse frame, k_perp,
+#                 three momenta), colours
+ORACLE_PER_TRIAL = {"simple": 4, "log": 2, "exp": 1, "div": 2}
+ORACLE_PER_DIPOLE = {"simple": 10, "div": 1, "sqrt": 1}
+ORACLE_PER_WINNER = {"simple": 20, "log": 1, "exp": 1, "div": 4}
+ORACLE_PER_EMISSION = {"simple": 140, "div": 6, "sqrt": 3, "sincospi": 1}
+# Algorithmic bytes of a pass: the final event records, 44 bytes per parton
+# (four momentum components, flavour, colour lines, links, with the event's
+# share of its scalars), for the final partons and the two initial ones.
+RECORD_BYTES_PER_PARTON = 44
+
 
 def step_kernel_profile():
     """Figures of the committed ncu captures of the plain-form step kernel
@@ -89,11 +108,14 @@ def pipe_fractions():
             "source": "profiles/k_step_deferred_500k.md (ncu --set full, launches 21-22 of a 5x10^5-event pass)"}
 
 
-def dfma_equivalents(counts, rates):
+def dfma_equivalents(counts, rates, library_log=False):
     """DFMA-equivalents of an operation count; a logarithm costs what the
-    faster of the library's log and the shower's table-driven one costs."""
+    faster of the library's log and the shower's table-driven one costs (the
+    library's alone with library_log)."""
     def rate(op):
-        return max(rates["log"], rates.get("log_fp64", 0.0)) if op == "log" else rates[op]
+        if op == "log" and not library_log:
+            return max(rates["log"], rates.get("log_fp64", 0.0))
+        return rates[op]
     return sum(n * (1.0 if op == "simple" else rates["dfma"] / rate(op)) for op, n in counts.items())
 
 
@@ -122,8 +144,11 @@ def parse():
                     help="events of the batched persistent variant (0: skip it)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival schedule of the serving variant (0: skip it)")
+    ap.add_argument("--uneven-jobs", type=int, default=64,
+                    help="jobs of the uneven multi-job batch variant (0: skip it)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory of the serving pool")
     ap.add_argument("--serve-cycles-per-round", type=int, default=8)
+    ap.add_argument("--serve-max-jobs", type=int, default=256, help="job slots of the serving pool")
     ap.add_argument("--serve-mode", default="slice", choices=["slice", "steps"])
     ap.add_argument("--early-stop", action="store_true",
                     help="instead of the benchmark line: the early-termination trade-off, pass time against "
@@ -343,6 +368,42 @@ def run_early_stop(args, g, torch, np):
                           "mean_bin_shift": [float(x) for x in (means - means_full)]}), flush=True)
 
 
+# ------------------------------------------------------------- serving
+def serve_c(server, jobs, realtime):
+    """Serve (arrival s, events, seed) jobs at LEP energy through the C
+    scheduler: each job is submitted at its arrival time (all at once unless
+    realtime); the schedule advances one step at a time (gaps_server_step)
+    and every job it reports finished is polled for its histograms.  Latency
+    runs from the scheduled arrival to the moment they are on the host."""
+    import numpy as np
+    import paper_2403_08692_gb300 as g
+    pending = sorted(jobs, key=lambda j: j[0])
+    open_jobs, lat, done_events = {}, [], 0
+    i = 0
+    t0 = time.perf_counter()
+    while i < len(pending) or open_jobs:
+        now = time.perf_counter() - t0
+        while i < len(pending) and (not realtime or pending[i][0] <= now):
+            arr, nev, sd = pending[i]
+            jid = server.submit(g.make_params(seed=sd), nev, 0)
+            open_jobs[jid] = (arr if realtime else 0.0, nev)
+            i += 1
+        if not open_jobs:
+            time.sleep(max(0.0, pending[i][0] - (time.perf_counter() - t0)))
+            continue
+        # one step of the schedule, then every job it reports finished
+        for jid in server.step():
+            if server.poll(jid) is not None:
+                arr, nev = open_jobs.pop(jid)
+                lat.append(time.perf_counter() - t0 - arr)
+                done_events += nev
+    wall = time.perf_counter() - t0
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"jobs": len(jobs), "events": done_events, "wall_s": wall, "events_per_s": done_events / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "max_latency_s": float(lat.max())}
+
+
 # ------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -453,6 +514,13 @@ def main():
     launches_per_pass = launches_total / args.steps
     kernel_s_per_launch = kernel_ms_total / 1e3 / launches_total
     achieved_tflops = 2.0 * dfma_per_pass / (kernel_ms_total / 1e3 / args.steps) / 1e12
+    # the oracle's arithmetic on the same units, at the same kernel time
+    oracle_dfma_per_pass = (dfma_equivalents(ORACLE_PER_TRIAL, rates, True) * st.sum_trials +
+                            dfma_equivalents(ORACLE_PER_DIPOLE, rates, True) * st.sum_dipoles +
+                            dfma_equivalents(ORACLE_PER_WINNER, rates, True) * st.sum_winners +
+                            dfma_equivalents(ORACLE_PER_EMISSION, rates, True) * st.sum_emissions)
+    oracle_tflops = 2.0 * oracle_dfma_per_pass / (kernel_ms_total / 1e3 / args.steps) / 1e12
+    record_bytes = RECORD_BYTES_PER_PARTON * (st.sum_partons + 2 * st.n_events)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = 2.0 * DFMA_PER_SM_PER_CLOCK * sms * clock_mhz * 1e6 / 1e12
@@ -601,50 +669,109 @@ def main():
         torch.cuda.empty_cache()
         ws = g.Workspace(n, args.capacity, first_event=first_event, device=dev)
 
+    # The uneven multi-job batch: 64 jobs of 10^3..10^6 events (log-uniform),
+    # sqrt(s) in {91.2, 133, 200} GeV, t_C in {0.5, 1, 2} GeV^2, a Philox key
+    # per job, showered in one persistent launch with per-job histograms.
+    if not args.no_variants and args.uneven_jobs > 0:
+        from paper_2403_08692_gb300 import workloads
+        try:
+            del ws
+        except NameError:
+            pass
+        torch.cuda.empty_cache()
+        jobs = workloads.uneven_batch(n_jobs=args.uneven_jobs, seed=4)
+        nu = sum(j["n_events"] for j in jobs)
+        wsu = g.Workspace(nu, args.capacity, device=dev)
+        g.set_jobs([(g.make_params(sqrt_s=j["sqrt_s"], t_cutoff=j["t_cutoff"], alphas_mz=j["alphas_mz"],
+                                   seed=j["seed"]), j["n_events"], j["first_event"]) for j in jobs], wsu, stream)
+        hist_u = torch.zeros(len(jobs) * g.HIST_DOUBLES, dtype=torch.float64, device=dev)
+        cfg_u = cfg_b.as_dict() if args.batched_events > 0 else None
+
+        def pass_uneven():
+            hist_u.zero_()
+            g.generate_me(None, wsu, stream)
+            g.shower_persistent(None, wsu, cfg_u, stream)
+            g.validate(None, wsu, stream)
+            g.observables(None, wsu, stream)
+            g.histograms(None, wsu, hist_u, stream)
+
+        for _ in range(2):
+            pass_uneven()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pass_uneven()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        # per-job shower lengths: the longest event of each job (all jobs run
+        # together, so a job's share of the launch follows its events' cycles)
+        job_of = wsu.view("job_of", torch.int16, (nu,)).to(torch.int64) & 0xFFFF
+        steps = wsu.scalars()["n_steps"].to(torch.int64)
+        job_max = torch.zeros(len(jobs), dtype=torch.int64, device=dev).scatter_reduce(0, job_of, steps, "amax")
+        job_sum = torch.zeros(len(jobs), dtype=torch.int64, device=dev).scatter_add(0, job_of, steps)
+        sizes = np.array([j["n_events"] for j in jobs])
+        mean_cycles = job_sum.cpu().numpy() / sizes
+        variants["uneven_64"] = {
+            "workload": f"{len(jobs)} jobs, {nu} events (10^3-10^6 per job, log-uniform, seed 4), sqrt(s) in "
+                        f"{{91.2, 133, 200}} GeV, t_C in {{0.5, 1, 2}} GeV^2, one persistent launch, "
+                        f"per-job histograms",
+            "value": nu * len(times) / (sum(times) / 1e3), "unit": UNIT, "ms_per_step": sum(times) / len(times),
+            "ms_iqr": [float(np.percentile(times, 25)), float(np.percentile(times, 75))],
+            "config": cfg_u, "jobs": len(jobs), "events": nu,
+            "job_events_min_median_max": [int(sizes.min()), int(np.median(sizes)), int(sizes.max())],
+            "job_mean_cycles_min_median_max": [float(mean_cycles.min()), float(np.median(mean_cycles)),
+                                               float(mean_cycles.max())],
+            "job_max_cycles_min_median_max": [int(x) for x in np.percentile(job_max.cpu().numpy(), [0, 50, 100])]}
+        del wsu, hist_u
+        torch.cuda.empty_cache()
+        ws = g.Workspace(n, args.capacity, first_event=first_event, device=dev)
+
     # The serving loop: Poisson job arrivals served in real time by
     # continuous batching over a resident pool (histograms of every job back
     # on the host), and the same jobs all queued at once (saturated).
     if args.serve_seconds > 0:
         from paper_2403_08692_gb300 import workloads
-        del ws
+        try:
+            del ws
+        except NameError:
+            pass
         torch.cuda.empty_cache()
         arrivals = workloads.poisson_arrivals(rate_per_s=50.0, duration_s=args.serve_seconds, seed=5)
-        server = g.Server(memory_budget=args.serve_budget_gb * 2**30, capacity=args.capacity,
-                          cycles_per_round=args.serve_cycles_per_round, clock="wall", device=dev,
-                          mode=args.serve_mode)
-        warm = [g.ServeJob(g.make_params(seed=7), 20000, 0, 0.0)] * 4
-        server.serve(warm)
-        server.reset()
-        jobs = [g.ServeJob(g.make_params(seed=s), nev, 0, t, tag=k) for k, (t, nev, s) in enumerate(arrivals)]
-        offered = sum(j.n_events for j in jobs) / args.serve_seconds
-        t0 = time.perf_counter()
-        results = server.serve(jobs)
-        wall = time.perf_counter() - t0
-        s = g.latency_summary(results, wall)
+        per_event = g.workspace_bytes(1 << 20, args.capacity) / float(1 << 20)
+        pool_events = int(args.serve_budget_gb * 2**30 // per_event)
+        mode = g.SERVE_SLICE if args.serve_mode == "slice" else g.SERVE_STEPS
+        server = g.CServer(pool_events, args.capacity, max_jobs=args.serve_max_jobs,
+                           cycles_per_round=args.serve_cycles_per_round, mode=mode, stream=stream)
+        serve_c(server, [(0.0, 20000, 7)] * 4, realtime=False)  # warm-up
+        jobs = [(t, nev, sd) for (t, nev, sd) in arrivals]
+        offered = sum(j[1] for j in jobs) / args.serve_seconds
+        s = serve_c(server, jobs, realtime=True)
         variants["serving"] = {
             "workload": f"Poisson arrivals, 50 jobs/s for {args.serve_seconds:g} s (seed 5), 10^3-10^6 events "
                         f"per job log-uniform, sqrt(s)=91.2 GeV, each job its own Philox key",
+            "api": "C scheduler: gaps_submit at each arrival, gaps_poll until done (gaps_server_*)",
             "value": s["events_per_s"], "unit": UNIT, "offered_events_per_s": offered,
             "p50_latency_ms": 1e3 * s["p50_latency_s"], "p99_latency_ms": 1e3 * s["p99_latency_s"],
-            "max_latency_ms": 1e3 * s["max_latency_s"], "jobs": s["jobs"], "events": s["events"], "wall_s": wall,
-            "pool_events": server.pool_events, "memory_budget_gb": args.serve_budget_gb,
-            "cycles_per_round": server.cycles_per_round, "peak_live_jobs": server.peak_live_jobs,
-            "mode": server.mode + (" (one persistent launch per round)" if server.mode == "slice"
-                                   else " (plain-form steps)"),
-            "veto_cycles": server.launched_cycles}
-        server.reset()
-        sat_jobs = [g.ServeJob(j.params, j.n_events, 0, 0.0, tag=j.tag) for j in jobs
-                    if j.arrival < args.serve_seconds / 6.0]
-        t0 = time.perf_counter()
-        results = server.serve(sat_jobs)
-        wall = time.perf_counter() - t0
-        s = g.latency_summary(results, wall)
+            "max_latency_ms": 1e3 * s["max_latency_s"], "jobs": s["jobs"], "events": s["events"],
+            "wall_s": s["wall_s"], "pool_events": pool_events, "memory_budget_gb": args.serve_budget_gb,
+            "cycles_per_round": args.serve_cycles_per_round, "max_jobs": args.serve_max_jobs,
+            "mode": args.serve_mode + (" (one persistent launch per round)" if args.serve_mode == "slice"
+                                       else " (plain-form steps)")}
+        sat_jobs = [(0.0, nev, sd) for (t, nev, sd) in jobs if t < args.serve_seconds / 6.0]
+        s = serve_c(server, sat_jobs, realtime=False)
         variants["serving_saturated"] = {
             "workload": f"the jobs arriving in the first {args.serve_seconds / 6.0:g} s of the serving workload, "
                         f"all queued at time 0",
-            "value": s["events_per_s"], "unit": UNIT, "jobs": s["jobs"], "events": s["events"], "wall_s": wall,
-            "p50_latency_ms": 1e3 * s["p50_latency_s"], "p99_latency_ms": 1e3 * s["p99_latency_s"],
-            "peak_live_jobs": server.peak_live_jobs}
+            "api": "C scheduler (gaps_submit / gaps_poll)",
+            "value": s["events_per_s"], "unit": UNIT, "jobs": s["jobs"], "events": s["events"], "wall_s": s["wall_s"],
+            "p50_latency_ms": 1e3 * s["p50_latency_s"], "p99_latency_ms": 1e3 * s["p99_latency_s"]}
+        server.close()
         del server
         torch.cuda.empty_cache()
         ws = g.Workspace(n, args.capacity, first_event=first_event, device=dev)
@@ -696,6 +823,21 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_step_deferred (plain-form step: select/veto + deferred emissions)",
                      "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak_tflops,
+                     "frac_of_probe": achieved_tflops / (2.0 * rates["dfma"] / 1e12),
+                     "oracle_arithmetic": {
+                         "label": "FP64-equivalent rate of the oracle's arithmetic: every trial, dipole, veto and "
+                                  "splitting of the run evaluated in FP64 as the oracle does it, at the library's "
+                                  "measured transcendental costs, over the step kernels' time; above the FP64 peak "
+                                  "because the kernels rank trials and decide vetoes in FP32 under error bounds "
+                                  "and redo only undecided cases in FP64",
+                         "achieved": oracle_tflops, "unit": "TFLOP/s", "over_peak": oracle_tflops / peak_tflops,
+                         "dfma_equivalents": {"per_trial": dfma_equivalents(ORACLE_PER_TRIAL, rates, True),
+                                              "per_dipole": dfma_equivalents(ORACLE_PER_DIPOLE, rates, True),
+                                              "per_winner": dfma_equivalents(ORACLE_PER_WINNER, rates, True),
+                                              "per_emission": dfma_equivalents(ORACLE_PER_EMISSION, rates, True)}},
+                     "algorithmic_record_bytes_per_pass": record_bytes,
+                     "dram_over_algorithmic": (None if step_kernel_traffic(1.0) is None else
+                                               step_kernel_traffic(float(st.sum_steps)) / record_bytes),
                      "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
                      "traffic_source": "profiles/k_step_deferred_500k.md: DRAM bytes per event-cycle from one ncu "
                                        "capture x this run's event-cycles per launch",

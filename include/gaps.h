@@ -290,7 +290,8 @@ int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const
  * 0) and hist_device (device memory, max_jobs * GAPS_HIST_DOUBLES doubles,
  * one set per job slot); the server keeps host state and a little pinned
  * host memory, never device memory.  Jobs are submitted as they arrive;
- * every gaps_poll advances the schedule by one step:
+ * every step (gaps_server_step, or gaps_poll of a job not yet finished)
+ * advances the schedule:
  *  - admission in submission order: a job takes a free slot (< max_jobs) and
  *    the first free contiguous range of the pool that holds its events (first
  *    fit, freed neighbours coalesced), its matrix elements are generated in
@@ -320,11 +321,16 @@ int gaps_server_create(const gaps_batch* pool, double* hist_device, int32_t max_
  * Host only: the GPU work starts at the next poll. */
 int gaps_submit(gaps_server* server, const gaps_params* params, int64_t n_events, uint32_t first_event,
                 uint64_t* job_id);
-/* One step of the schedule, then *done = 1 if job job_id has finished, with
- * its histograms copied to host_hist (GAPS_HIST_DOUBLES doubles, may be NULL;
- * the job is then forgotten), else *done = 0.  GAPS_ERR_INVALID for a job id
- * that was never submitted or was already reported finished.  May wait for
- * the round before the last to finish on the GPU. */
+/* One step of the schedule.  Then the ids of the finished jobs not yet
+ * reported by gaps_poll go to finished_ids[0 .. min(count, max_ids)) and
+ * their count to *n_finished (may be NULL).  May wait for the round before
+ * the last to finish on the GPU. */
+int gaps_server_step(gaps_server* server, uint64_t* finished_ids, int32_t max_ids, int32_t* n_finished);
+/* Report job job_id: if it has not finished yet, one step of the schedule
+ * first.  *done = 1 if it has finished, with its histograms copied to
+ * host_hist (GAPS_HIST_DOUBLES doubles, may be NULL; the job is then
+ * forgotten), else *done = 0.  GAPS_ERR_INVALID for a job id that was never
+ * submitted or was already reported finished. */
 int gaps_poll(gaps_server* server, uint64_t job_id, double* host_hist, int32_t* done);
 /* Jobs waiting for admission, jobs live or being finalised, and finished jobs
  * not yet reported by gaps_poll (each may be NULL). */

@@ -237,7 +237,7 @@ Events sub_view(const Events& E, int64_t a, int64_t count) {
 // batch whose event j has id first_event + j.  Without, a multi-job batch
 // prepared by gaps_set_jobs: every event takes its job's parameters from the
 // workspace's job table; the host-side step bound is then only a guard.
-int prepare(const gaps_params* params, const gaps_batch* batch, DevParams* P, Events* E) {
+int prepare(const gaps_params* params, const gaps_batch* batch, DevParams* P, Events* E, bool pool = false) {
   if (check_batch(batch) != GAPS_OK) return GAPS_ERR_INVALID;
   *E = make_events(*batch);
   if (params) {
@@ -250,7 +250,8 @@ int prepare(const gaps_params* params, const gaps_batch* batch, DevParams* P, Ev
   char* base = static_cast<char*>(batch->workspace);
   E->jobs = reinterpret_cast<const DevParams*>(base + L.jobs);
   E->job_of = reinterpret_cast<const uint16_t*>(base + L.job_of);
-  E->job_done = reinterpret_cast<unsigned long long*>(base + L.job_done);
+  // only the serving pool tracks its jobs' finished events
+  E->job_done = pool ? reinterpret_cast<unsigned long long*>(base + L.job_done) : nullptr;
   *P = DevParams{};
   P->max_steps = 0x7fffffff;
   return GAPS_OK;
@@ -753,7 +754,7 @@ int gaps_run(const gaps_params* params, const gaps_batch* batch, int mode, doubl
 int gaps_pool_reset(const gaps_batch* pool, void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(E.counters, 0, kCounterWords * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(E.job_done, 0, GAPS_MAX_JOBS * sizeof(unsigned long long), s);
@@ -764,7 +765,7 @@ int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begi
                     uint32_t first_event, const gaps_batch* pool, int64_t cycle, void* stream) {
   DevParams P;
   Events E;
-  if (!params || gaps_check_params(params) != GAPS_OK || prepare(nullptr, pool, &P, &E) != GAPS_OK)
+  if (!params || gaps_check_params(params) != GAPS_OK || prepare(nullptr, pool, &P, &E, true) != GAPS_OK)
     return GAPS_ERR_INVALID;
   if (job_slot < 0 || job_slot >= GAPS_MAX_JOBS || ev_begin < 0 || n_events < 0 || cycle < 0 ||
       ev_begin + n_events > pool->n_events ||
@@ -789,7 +790,7 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
                      void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || first_cycle < 0 || n_cycles < 0 || max_active < 0 ||
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || first_cycle < 0 || n_cycles < 0 || max_active < 0 ||
       max_active > pool->n_events)
     return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -810,7 +811,7 @@ int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64
                     const gaps_persistent_config* cfg, void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || round < 0 || cycles < 1 || cycles > 255 || max_active < 0 ||
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || round < 0 || cycles < 1 || cycles > 255 || max_active < 0 ||
       max_active > pool->n_events)
     return GAPS_ERR_INVALID;
   const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
@@ -832,7 +833,7 @@ int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_ou
                        void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || cycle < 0 || !active_out) return GAPS_ERR_INVALID;
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || cycle < 0 || !active_out) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned long long counts[kCounterWords] = {0};
   cudaError_t e = cudaMemcpyAsync(counts, E.counters, sizeof(counts), cudaMemcpyDeviceToHost, s);
@@ -848,7 +849,7 @@ int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const
                      double* hist_device, void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E) != GAPS_OK || !hist_device || job_slot < 0 || job_slot >= GAPS_MAX_JOBS ||
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || !hist_device || job_slot < 0 || job_slot >= GAPS_MAX_JOBS ||
       ev_begin < 0 || n_events < 0 || ev_begin + n_events > pool->n_events)
     return GAPS_ERR_INVALID;
   if (n_events == 0) return GAPS_OK;

@@ -145,6 +145,17 @@ __device__ __forceinline__ const DevParams& params_of(const DevParams& launch, c
   }
 }
 
+// The parameters of a job: the multi-job table's entry `job` (kMulti), else
+// the launch's.  For kernels that already hold an event's job index.
+template <bool kMulti>
+__device__ __forceinline__ const DevParams& job_params(const DevParams& launch, const Events& E, int job) {
+  if constexpr (kMulti) {
+    return E.jobs[job];
+  } else {
+    return launch;
+  }
+}
+
 // Compile-time policy of the shower kernels: a single job with one trial per
 // (dipole, kernel), a single job with one trial per dipole, or a multi-job
 // batch (parameters and trial mode read per event).  Single-job kernels then
@@ -194,6 +205,40 @@ __device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, ui
     c3 = lo0;
   }
   return U4{c0, c1, c2, c3};
+}
+
+// The same generator with the key schedule formed on the fly from the seed
+// words (two additions per round).  Multi-job kernels take their parameters
+// from the job table in global memory, where reading twenty round keys per
+// call would put a load into every round of the dependent chain.
+__device__ __forceinline__ U4 philox10_seed(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                            uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// A draw of event-keyed counter (c0..c3) with a launch's parameters: round
+// keys from the parameter bank (single-job launches), or from the seed for
+// parameters read from the job table (kMulti).
+template <bool kMulti>
+__device__ __forceinline__ U4 philox_draw(const DevParams& P, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  if constexpr (kMulti) {
+    return philox10_seed(c0, c1, c2, c3, P.seed_lo, P.seed_hi);
+  } else {
+    return philox10(c0, c1, c2, c3, P.rk);
+  }
 }
 
 // 52-bit uniform strictly inside (0, 1): the top 26 bits of each word, plus

@@ -167,34 +167,37 @@ __device__ __forceinline__ void add128(unsigned long long* acc, unsigned long lo
 // warp that fill the same cell are merged first (match on the cell; the
 // first lane sums its peers' fixed-point weights from shared memory as
 // 128-bit integers), so a crowded bin costs one atomic per warp, not one per
-// event.  Single-job batch (kJobs false): block-private accumulators in
-// shared memory, merged into acc once per block; scales from P, or from
-// *scale_src (a job-table entry on the device) when it is given.  Multi-job
-// batch: every event fills its own job's accumulators (acc + job *
-// GAPS_HIST_FIXED_WORDS) with global atomics, at its job's scales.
+// event.  Each block takes a contiguous chunk of events and accumulates the
+// fills of its first event's job (the home job) in shared memory, merged
+// into that job's set of acc (acc + job * GAPS_HIST_FIXED_WORDS) once per
+// block.  Single-job batch (kJobs false): every fill is the home job's, at
+// the scales of P, or of *scale_src (a job-table entry on the device) when
+// it is given.  Multi-job batch: a job's events lie together, so nearly
+// every fill is the home job's; the others go to global memory directly;
+// every event at its own job's scales.
 template <bool kJobs>
 __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams* scale_src, Events E,
                                                     unsigned long long* acc) {
-  constexpr bool kShared = !kJobs;  // (global atomics for one job measured 70 % slower)
-  __shared__ unsigned long long sh[kShared ? GAPS_HIST_FIXED_WORDS : 1];
+  __shared__ unsigned long long sh[GAPS_HIST_FIXED_WORDS];
   __shared__ long long s_w[256], s_w2[256];
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
-  if (kShared) {
-    for (int i = tid; i < GAPS_HIST_FIXED_WORDS; i += blockDim.x) sh[i] = 0ull;
-    __syncthreads();
-  }
+  for (int i = tid; i < GAPS_HIST_FIXED_WORDS; i += blockDim.x) sh[i] = 0ull;
+  __syncthreads();
+  const int64_t N = E.n;
+  const int64_t chunk = ((N + gridDim.x - 1) / gridDim.x + 31) & ~static_cast<int64_t>(31);
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t b1 = b0 + chunk < N ? b0 + chunk : N;
+  const int home = kJobs && b0 < N ? static_cast<int>(E.job_of[b0]) : 0;
   double sc_w = P.hist_sw, sc_w2 = P.hist_sw2;
   if (!kJobs && scale_src) {
     sc_w = scale_src->hist_sw;
     sc_w2 = scale_src->hist_sw2;
   }
-  const int64_t N = E.n;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   // every lane of a warp runs the same iterations (the match needs them all)
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + warp0; base < N; base += stride) {
+  for (int64_t base = b0 + warp0; base < b1; base += blockDim.x) {
     const int64_t ev = base + lane;
-    const bool fill = ev < N && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
-    const int job = kJobs && fill ? static_cast<int>(E.job_of[ev]) : 0;
+    const bool fill = ev < b1 && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
+    const int job = kJobs && fill ? static_cast<int>(E.job_of[ev]) : home;
     if (kJobs && fill) {
       sc_w = E.jobs[job].hist_sw;
       sc_w2 = E.jobs[job].hist_sw2;
@@ -221,7 +224,8 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
           hi2 += (b < 0 ? -1 : 0) + (n2 < lo2 ? 1 : 0);
           lo2 = n2;
         }
-        unsigned long long* c = (kShared ? sh : acc) + static_cast<size_t>(cell) * 5;
+        unsigned long long* c = job == home ? sh + static_cast<size_t>(cell - home * kCells) * 5
+                                            : acc + static_cast<size_t>(cell) * 5;
         add128(c + 0, lo1, hi1);
         add128(c + 2, lo2, hi2);
         atomicAdd(c + 4, static_cast<unsigned long long>(__popc(peers)));
@@ -229,16 +233,15 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
     }
     __syncwarp();
   }
-  if (kShared) {
-    __syncthreads();
-    for (int cell = tid; cell < kCells; cell += blockDim.x) {
-      const unsigned long long* c = sh + cell * 5;
-      if (c[4] == 0ull) continue;
-      unsigned long long* g = acc + cell * 5;
-      add128(g + 0, c[0], static_cast<long long>(c[1]));
-      add128(g + 2, c[2], static_cast<long long>(c[3]));
-      atomicAdd(g + 4, c[4]);
-    }
+  __syncthreads();
+  unsigned long long* g_home = acc + static_cast<size_t>(home) * GAPS_HIST_FIXED_WORDS;
+  for (int cell = tid; cell < kCells; cell += blockDim.x) {
+    const unsigned long long* c = sh + cell * 5;
+    if (c[4] == 0ull) continue;
+    unsigned long long* g = g_home + cell * 5;
+    add128(g + 0, c[0], static_cast<long long>(c[1]));
+    add128(g + 2, c[2], static_cast<long long>(c[3]));
+    atomicAdd(g + 4, c[4]);
   }
 }
 
@@ -364,7 +367,7 @@ cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, co
   const int64_t want = (E.n + 255) / 256;
   const int64_t most = static_cast<int64_t>(GAPS_HIST_BLOCKS_PER_SM) * sms;
   if (E.jobs && E.job_of) {
-    k_hist_fixed<true><<<static_cast<unsigned>(want < 16 * sms ? want : 16 * sms), 256, 0, s>>>(P, nullptr, E, acc);
+    k_hist_fixed<true><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, nullptr, E, acc);
   } else {
     k_hist_fixed<false><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, scale_src, E, acc);
   }

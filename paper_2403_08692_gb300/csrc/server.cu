@@ -1,7 +1,8 @@
 // C-ABI serving scheduler: continuous batching of shower jobs over one
 // resident pool (the paper's host driver, Sec. 2 and App. C, turned into a
-// request loop).  Jobs are submitted as they arrive; every poll advances the
-// schedule by one step:
+// request loop).  Jobs are submitted as they arrive; every step (an explicit
+// gaps_server_step, or a gaps_poll of an unfinished job) advances the
+// schedule:
 //   1. admission, in submission order: a job takes a free job slot and the
 //      first free contiguous range of the pool that holds its events (first
 //      fit, freed neighbours coalesced); its matrix elements are generated in
@@ -304,12 +305,28 @@ int gaps_submit(gaps_server* s, const gaps_params* params, int64_t n_events, uin
   return GAPS_OK;
 }
 
+int gaps_server_step(gaps_server* s, uint64_t* finished_ids, int32_t max_ids, int32_t* n_finished) {
+  if (!s || max_ids < 0 || (max_ids > 0 && !finished_ids)) return GAPS_ERR_INVALID;
+  const int rc = step(s);
+  if (rc != GAPS_OK) return rc;
+  int32_t k = 0;
+  for (const auto& r : s->results) {
+    if (k < max_ids) finished_ids[k] = r.first;
+    ++k;
+  }
+  if (n_finished) *n_finished = k;
+  return GAPS_OK;
+}
+
 int gaps_poll(gaps_server* s, uint64_t job_id, double* host_hist, int32_t* done) {
   if (!s || !done || s->open.count(job_id) == 0) return GAPS_ERR_INVALID;
   *done = 0;
-  const int rc = step(s);
-  if (rc != GAPS_OK) return rc;
   auto it = s->results.find(job_id);
+  if (it == s->results.end()) {
+    const int rc = step(s);
+    if (rc != GAPS_OK) return rc;
+    it = s->results.find(job_id);
+  }
   if (it == s->results.end()) return GAPS_OK;
   if (host_hist) std::memcpy(host_hist, it->second.data(), GAPS_HIST_DOUBLES * sizeof(double));
   s->results.erase(it);

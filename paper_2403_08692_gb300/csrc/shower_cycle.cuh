@@ -176,8 +176,8 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
       const DipoleEntry d = make_dipole(P, 2.0 * mdot(pi, load_p(E, k, ev)));
       if (d.screen.x < 0.0f) continue;
       for (int kp = 0; kp < nk; kp += 2) {
-        const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
-                              kDrawTrial, P.rk);
+        const U4 r = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step),
+                                                      static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
         for (int h = 0; h < 2 && kp + h < nk; ++h) {
           const int kappa = kp + h;
           const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
@@ -223,6 +223,17 @@ __device__ __forceinline__ double z_fp64(int kind, double zp, double lsoft, doub
 }
 
 enum : int { kCycleVetoed = 0, kCycleFinished = 1, kCycleAccepted = 2 };
+
+// The serving pool counts every job's finished events (E.job_done, set only
+// for the pool): the lanes of a warp that finished events of the same job
+// add them with one atomic.  Every lane of the warp must call it.
+__device__ __forceinline__ void count_job_done(const Events& E, int64_t ev, bool finished) {
+  if (!E.job_done) return;  // the same for every lane (a launch argument)
+  const int job = finished ? static_cast<int>(E.job_of[ev]) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, job);
+  if (finished && static_cast<int>(threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicAdd(&E.job_done[job], static_cast<unsigned long long>(__popc(peers)));
+}
 
 // Leave the active state with `status`, recording the final scale.
 __device__ __forceinline__ void finish_event(const Events& E, int64_t ev, int status, double t) {
@@ -295,8 +306,8 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
       // per-dipole trial of a gluon: 1/c of all its kernels (a few ulp)
       const float inv_sum = combined ? 1.0f / (static_cast<float>(kCA) / d.x + static_cast<float>(P.nf) / d.y) : 0.0f;
       for (int kp = 0; kp < nk; kp += 2) {
-        const U4 r = philox10(id, static_cast<uint32_t>(step), static_cast<uint32_t>((2 * i + side) * 4 + kp / 2),
-                              kDrawTrial, P.rk);
+        const U4 r = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step),
+                                                      static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int kappa = kp + h;
@@ -424,14 +435,14 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   E.n_winners[ev] += 1;
   if (task.kind == kKindUnchosen) {
     // per-dipole trial of a gluon: its kernel from the winner's second draw
-    const U4 rk = philox10(id, static_cast<uint32_t>(step), 1u, kDrawWinner, P.rk);
+    const U4 rk = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step), 1u, kDrawWinner);
     const int kappa = choose_kernel(P, task.zp, task.inv_ls, to_unit(rk.z, rk.w));
     task.kappa = static_cast<uint8_t>(kappa);
     task.kind = static_cast<uint8_t>(kappa == 0 ? kGtoGG : kGtoQQ);
   }
 
   // ---- AcceptOrVeto: FP32 screen of Eq. (A.8)-(A.9), FP64 near the edge.
-  const U4 rw = philox10(id, static_cast<uint32_t>(step), 0u, kDrawWinner, P.rk);
+  const U4 rw = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step), 0u, kDrawWinner);
   bool accept;
   {
     const float zpf = f32_from_f64(task.zp);
@@ -520,7 +531,7 @@ __device__ inline void cycle_emit(const DevParams& P0, const Events& E, const Em
   const double t = exp(w.lnt);
   const double z = z_fp64(w.kind, w.zp, 1.0 / w.inv_ls, to_unit(w.rz_hi, w.rz_lo));
   const double y = t / (w.q2 * z * (1.0 - z));
-  const U4 rphi = philox10(id, static_cast<uint32_t>(w.step), 1u, kDrawWinner, P.rk);
+  const U4 rphi = philox_draw<kMulti>(P, id, static_cast<uint32_t>(w.step), 1u, kDrawWinner);
   double sphi, cphi;
   sincospi(2.0 * to_unit(rphi.x, rphi.y), &sphi, &cphi);
   const V4 a = load_p(E, w.i, ev);

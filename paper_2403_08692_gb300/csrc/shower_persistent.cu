@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
         if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, lanes, sc);
       }
       screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
+      bool finished = false;
       if (live && sub == 0) {
         if constexpr (kSlice) s_cyc[slot] = static_cast<uint8_t>(s_cyc[slot] + 1);
         const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
@@ -201,9 +202,10 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           s_alive[slot] = kSlotDead;
           atomicAdd(&E.counters[0], 1ull);
           if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
-          if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
+          finished = true;
         }
       }
+      count_job_done(E, ev, finished);
     }
     __syncthreads();
     // GenerateEmission for the period's accepted emissions, in full warps,

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   if (idx < len) ev = list_in ? static_cast<int64_t>(list_in[idx]) : idx;
   const bool active = ev >= 0 && E.status[ev] == GAPS_ACTIVE;
   __syncthreads();
-  bool survive = false;
+  bool survive = false, finished = false;
   if (active) {
     EmitTask task;
     const int r = cycle_select_veto<kMode>(P, E, ev, task);
@@ -126,10 +126,11 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     } else if (r == kCycleFinished) {
       atomicAdd(&E.counters[0], 1ull);
       if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
-      if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
+      finished = true;
     }
     survive = r != kCycleFinished;
   }
+  count_job_done(E, ev, finished);
   if (list_out) {
     const unsigned mask = __ballot_sync(0xffffffffu, survive);
     if (mask != 0u) {
@@ -199,12 +200,15 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     // The event's status, size, cycle and (one lane per event) first parton
     // are loaded together, not one after another: every listed event has
     // slot 0.
-    int status = -1, n = 0, step = 0;
+    // A multi-job batch's job index is loaded with them.
+    constexpr bool kMulti = kMode == kModeMulti;
+    int status = -1, n = 0, step = 0, job = 0;
     PartonScreen first{};
     if (ev >= 0) {
       status = E.status[ev];
       n = E.n_partons[ev];
       step = E.n_steps[ev];
+      if (kMulti) job = E.job_of[ev];
       if (L == 1) first = load_parton_screen(E, ev, 0);
     }
     const bool active = status == GAPS_ACTIVE;
@@ -212,7 +216,7 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     screen_none(sc);
     bool limited = false;
     if (active) {
-      const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
+      const DevParams& P = job_params<kMulti>(P0, E, job);
       limited = step >= P.max_steps;
       if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc, L == 1 ? &first : nullptr);
     } else {
@@ -223,7 +227,7 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     int r = kCycleFinished;
     EmitTask task;
     if (lead) {
-      const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
+      const DevParams& P = job_params<kMulti>(P0, E, job);
       if (limited) {
         finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
       } else {
@@ -232,9 +236,9 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
       if (r == kCycleFinished) {
         atomicAdd(&E.counters[0], 1ull);
         if (E.status[ev] == GAPS_STEP_LIMIT) atomicAdd(&E.counters[1], 1ull);
-        if (E.job_done) atomicAdd(&E.job_done[E.job_of[ev]], 1ull);
       }
     }
+    count_job_done(E, ev, lead && r == kCycleFinished);
     const int64_t at_task = warp_append_slot(lead && r == kCycleAccepted, task_count);
     if (at_task >= 0) {
       tasks_out[at_task] = task;

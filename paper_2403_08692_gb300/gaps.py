@@ -104,6 +104,7 @@ SIGNATURES = {
                                      C.c_void_p, _P(C.c_void_p)]),
     "gaps_submit": (C.c_int, [C.c_void_p, _P(Params), C.c_int64, C.c_uint32, _P(C.c_uint64)]),
     "gaps_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, _P(C.c_int32)]),
+    "gaps_server_step": (C.c_int, [C.c_void_p, _P(C.c_uint64), C.c_int32, _P(C.c_int32)]),
     "gaps_server_counts": (C.c_int, [C.c_void_p, _P(C.c_int64), _P(C.c_int64), _P(C.c_int64)]),
     "gaps_server_destroy": (None, [C.c_void_p]),
     "gaps_strerror": (C.c_char_p, [C.c_int]),
@@ -474,6 +475,14 @@ class CServer:
         done = C.c_int32(0)
         _check(load().gaps_poll(self._h, C.c_uint64(job_id), C.c_void_p(out.ctypes.data), C.byref(done)), "gaps_poll")
         return out if done.value else None
+
+    def step(self, max_ids=1024):
+        """One step of the schedule; returns the ids of the finished jobs not
+        yet reported by poll."""
+        ids = (C.c_uint64 * max_ids)()
+        n = C.c_int32(0)
+        _check(load().gaps_server_step(self._h, ids, int(max_ids), C.byref(n)), "gaps_server_step")
+        return list(ids[:min(n.value, max_ids)])
 
     def counts(self):
         q, l, f = C.c_int64(0), C.c_int64(0), C.c_int64(0)
