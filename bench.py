@@ -66,12 +66,12 @@ RECORD_BYTES_PER_PARTON = 44
 
 def step_kernel_profile():
     """Figures of the committed ncu captures of the plain-form step kernel
-    (profiles/k_step_deferred_500k.md): DRAM bytes per event-cycle of a whole
+    (profiles/k_step_deferred_1e5.md): DRAM bytes per event-cycle of a whole
     pass and the FP64-pipe, issue-slot and SM-active fractions of mid-shower
     launches; None once the kernel sources differ from the captured ones."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "k_step_deferred_500k.md")
+    path = os.path.join(ROOT, "profiles", "k_step_deferred_1e5.md")
     try:
         text = open(path).read()
         want = re.search(r"source_sha256:\s*([0-9a-f]+)", text).group(1)
@@ -89,23 +89,24 @@ def step_kernel_profile():
 
 def step_kernel_traffic(event_cycles_per_launch):
     """DRAM bytes per launch of the plain-form step kernel: the per-event-cycle
-    traffic of the committed ncu capture (all step launches of one pass, the
-    deferred emissions included) times this run's event-cycles per launch;
-    None once the kernel sources differ from the captured ones."""
+    traffic of the committed ncu capture (all step launches of one pass at
+    10^5 events, the deferred emissions included) times this run's
+    event-cycles per launch; None once the kernel sources differ from the
+    captured ones."""
     prof = step_kernel_profile()
     return None if prof is None else prof["dram_bytes_per_event_cycle"] * event_cycles_per_launch
 
 
 def pipe_fractions():
     """The FP64-pipe and issue-slot fractions of the step kernel (ncu, two
-    mid-shower launches at 5x10^5 events), as the profile records them."""
+    mid-shower launches at 10^5 events), as the profile records them."""
     prof = step_kernel_profile()
     if prof is None:
         return None
     return {"fp64_pipe_of_active_cycles": prof["fp64_pipe_active_frac"],
             "issue_slots_of_active_cycles": prof["issue_active_frac"],
             "sm_active_of_elapsed_cycles": prof["sm_active_frac"],
-            "source": "profiles/k_step_deferred_500k.md (ncu --set full, launches 21-22 of a 5x10^5-event pass)"}
+            "source": "profiles/k_step_deferred_1e5.md (ncu --set full, launches 21-22 of a 10^5-event pass)"}
 
 
 def dfma_equivalents(counts, rates, library_log=False):
@@ -839,7 +840,7 @@ def main():
                      "dram_over_algorithmic": (None if step_kernel_traffic(1.0) is None else
                                                step_kernel_traffic(float(st.sum_steps)) / record_bytes),
                      "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
-                     "traffic_source": "profiles/k_step_deferred_500k.md: DRAM bytes per event-cycle from one ncu "
+                     "traffic_source": "profiles/k_step_deferred_1e5.md: DRAM bytes per event-cycle from one ncu "
                                        "capture x this run's event-cycles per launch",
                      "pipes": pipe_fractions(),
                      "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "

@@ -20,7 +20,7 @@ def _stamp(root):
     """Rewrite the profile's source hash to the tree's current sources."""
     import hashlib
     import re
-    path = os.path.join(root, "profiles", "k_step_deferred_500k.md")
+    path = os.path.join(root, "profiles", "k_step_deferred_1e5.md")
     text = open(path).read()
     files = re.search(r"sources:\s*(.+)", text).group(1).split()
     h = hashlib.sha256()
