@@ -148,7 +148,7 @@ def parse():
     ap.add_argument("--uneven-jobs", type=int, default=64,
                     help="jobs of the uneven multi-job batch variant (0: skip it)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory of the serving pool")
-    ap.add_argument("--serve-cycles-per-round", type=int, default=8)
+    ap.add_argument("--serve-cycles-per-round", type=int, default=32)
     ap.add_argument("--serve-max-jobs", type=int, default=256, help="job slots of the serving pool")
     ap.add_argument("--serve-mode", default="slice", choices=["slice", "steps"])
     ap.add_argument("--early-stop", action="store_true",
