@@ -137,7 +137,9 @@ def parse():
     ap.add_argument("--events", type=int, default=1_000_000)
     ap.add_argument("--capacity", type=int, default=128)
     ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle events for the CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000,
+                    help="oracle events for the CPU baseline on all host cores (about 10 s on 16 Grace cores; "
+                         "one core gets 1/16 of them)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-variants", action="store_true", help="skip the persistent-form variants")
@@ -225,11 +227,18 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- CPU oracle
-def oracle_rate(seed, n_events, capacity, threads, first_event=0):
+def oracle_rate(seed, n_events, capacity, threads, first_event=0, chunk=1_000_000):
+    """The oracle's full pipeline (ME, shower, validation, observables,
+    histograms) over n_events events of the workload, in chunks of at most
+    `chunk` events so that host memory stays bounded; events/s and seconds."""
     from oracle import oracle as O
     p = O.make_params(seed=seed, capacity=capacity)
     t0 = time.perf_counter()
-    O.run(p, first_event, n_events, threads=threads, want_obs=True, want_hist=True)
+    done = 0
+    while done < n_events:
+        k = min(chunk, n_events - done)
+        O.run(p, first_event + done, k, threads=threads, want_obs=True, want_hist=True)
+        done += k
     dt = time.perf_counter() - t0
     return n_events / dt, dt
 
@@ -247,7 +256,7 @@ def run_reference(args, rank, world):
     from oracle import oracle as O
     O.lib()
     cores = host_cores()
-    sample = max(1000, args.cpu_sample // 2)
+    sample = max(1000, args.cpu_sample // 20)
     for w in range(args.warmup):
         oracle_rate(args.seed, sample // 10, args.capacity, cores, first_event=w * sample)
     times = []
@@ -798,7 +807,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         rate, dt = oracle_rate(args.seed, args.cpu_sample, args.capacity, cores)
-        one = max(1000, args.cpu_sample // 20)
+        one = max(1000, args.cpu_sample // 16)
         rate1, dt1 = oracle_rate(args.seed, one, args.capacity, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_sample} events of the same workload (seed {args.seed}), full "
