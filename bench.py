@@ -541,6 +541,7 @@ def main():
     variants = {}
     if not args.no_variants:
         cfg, _ = g.autotune_persistent(p, ws, stream)
+        ws.record_layout = cfg.layout  # the record layout the autotuner picked, for every persistent pass
 
         def pass_persistent():
             hist_dev.zero_()
@@ -595,8 +596,10 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         variants["persistent_graph"] = {"value": n * args.steps / (sum(times) / 1e3), "unit": UNIT,
-                                        "ms_per_step": sum(times) / args.steps}
+                                        "ms_per_step": sum(times) / args.steps,
+                                        "layout": g.LAYOUT_NAMES[cfg.layout]}
         del graph
+        ws.record_layout = g.LAYOUT_SOA
 
     # The per-dipole trial mode (one trial per dipole with the summed
     # overestimate; the same distribution, other events) on the same
@@ -605,6 +608,8 @@ def main():
         pd = g.make_params(seed=args.seed, trial_mode=g.TRIALS_PER_DIPOLE)
         cfg_pd, _ = g.autotune_persistent(pd, ws, stream)
         for name, persistent in (("plain_per_dipole", False), ("persistent_per_dipole", True)):
+            ws.record_layout = cfg_pd.layout if persistent else g.LAYOUT_SOA
+
             def pass_pd():
                 hist_dev.zero_()
                 g.generate_me(pd, ws, stream)
@@ -634,6 +639,7 @@ def main():
                               "unit": UNIT, "ms_per_step": sum(times) / args.steps}
             if persistent:
                 variants[name]["config"] = cfg_pd.as_dict()
+        ws.record_layout = g.LAYOUT_SOA
 
     # The batched persistent form at its own paper-scale workload (10^7 LEP
     # events, seed 3): autotuned shape, the whole pass in one CUDA graph.
@@ -644,6 +650,7 @@ def main():
         pb = g.make_params(seed=3)
         wsb = g.Workspace(nb, args.capacity, first_event=sharding.shard(rank, world, nb)[0], device=dev)
         cfg_b, _ = g.autotune_persistent(pb, wsb, stream)
+        wsb.record_layout = cfg_b.layout
         side = torch.cuda.Stream()
         side.wait_stream(stream)
         graph = torch.cuda.CUDAGraph()
@@ -691,7 +698,8 @@ def main():
         torch.cuda.empty_cache()
         jobs = workloads.uneven_batch(n_jobs=args.uneven_jobs, seed=4)
         nu = sum(j["n_events"] for j in jobs)
-        wsu = g.Workspace(nu, args.capacity, device=dev)
+        wsu = g.Workspace(nu, args.capacity, device=dev,
+                          layout=cfg_b.layout if args.batched_events > 0 else g.LAYOUT_SOA)
         g.set_jobs([(g.make_params(sqrt_s=j["sqrt_s"], t_cutoff=j["t_cutoff"], alphas_mz=j["alphas_mz"],
                                    seed=j["seed"]), j["n_events"], j["first_event"]) for j in jobs], wsu, stream)
         hist_u = torch.zeros(len(jobs) * g.HIST_DOUBLES, dtype=torch.float64, device=dev)

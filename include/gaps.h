@@ -74,21 +74,38 @@ typedef struct gaps_params {
  * six), but other random numbers, so other events. */
 enum { GAPS_TRIALS_PER_KERNEL = 0, GAPS_TRIALS_PER_DIPOLE = 1 };
 
+/* Record layouts of the per-parton arrays of a workspace.  Structure of
+ * arrays: slot-major [capacity][n_events], element (slot i, event e) at index
+ * i * n_events + e.  Tiles of T = 8 or 32 events (array of structures of
+ * arrays): [ceil(n_events / T)][capacity][T], element (i, e) at
+ * (e / T) * capacity * T + i * T + e % T, so all slots of an event lie within
+ * capacity * T elements while a warp of consecutive events still reads
+ * contiguous segments.  The [2][capacity] arrays (link, dip, dq2, dzp, dinv)
+ * are [2][capacity][n_events] and [ceil(n_events / T)][2][capacity][T]. */
+enum { GAPS_LAYOUT_SOA = 0, GAPS_LAYOUT_TILE8 = 1, GAPS_LAYOUT_TILE32 = 2 };
+
 /* One batch of events inside a caller-owned device workspace.  Event j of
- * the batch has id first_event + j (the Philox counter's event word). */
+ * the batch has id first_event + j (the Philox counter's event word).  The
+ * layout is a property of the workspace's contents: every call on the same
+ * events must give the layout gaps_generate_me (or gaps_pool_admit) wrote
+ * them with.  A workspace sized by gaps_workspace_bytes holds any layout. */
 typedef struct gaps_batch {
   void* workspace;      /* device pointer, 256-byte aligned, gaps_workspace_bytes() long */
   int64_t n_events;     /* 0 .. 2^31-1 */
   int32_t capacity;     /* parton slots per event, 4..255; the paper uses 50 (App. C) */
   uint32_t first_event; /* id of the batch's first event */
+  int32_t layout;       /* GAPS_LAYOUT_SOA (0), GAPS_LAYOUT_TILE8 or GAPS_LAYOUT_TILE32 */
+  int32_t reserved;     /* must be 0 */
 } gaps_batch;
 
 /* Byte offsets, from the workspace base, of every array in the workspace.
- * Parton arrays are slot-major, [capacity][n_events]: element (slot i, event
- * e) is at index i * n_events + e, so a warp of consecutive events reads one
- * contiguous segment per slot. */
+ * Each per-parton array has room for capacity * n_events events rounded up
+ * to a multiple of 32, in the batch's layout (above); with the default
+ * structure-of-arrays layout element (slot i, event e) is at index
+ * i * n_events + e, so a warp of consecutive events reads one contiguous
+ * segment per slot. */
 typedef struct gaps_layout {
-  int64_t px, py, pz, e;  /* double [capacity][n_events], GeV */
+  int64_t px, py, pz, e;  /* double [capacity][n_events] (in the batch's layout), GeV */
   int64_t flav;           /* int8   [capacity][n_events]: PDG id, 21 = gluon */
   int64_t col, acol;      /* int16  [capacity][n_events]: colour / anticolour line, 0 = none */
   int64_t link;           /* uint8  [2][capacity][n_events]: colour partner slot on side 0
@@ -199,12 +216,15 @@ enum {
 /* Launch shape of the persistent form.  block_threads: 64, 128, 256 or 512
  * events per block pool; compact_period: veto cycles between compactions
  * and refills of a pool (>= 1); blocks_per_sm: resident blocks per SM (0 =
- * as many as fit). */
+ * as many as fit); layout: the record layout the autotuner found fastest
+ * with this shape (gaps_autotune_persistent's output, to be used as the
+ * batch's layout; launches take the layout from the batch and ignore this
+ * field, which must be a valid layout). */
 typedef struct gaps_persistent_config {
   int32_t block_threads;
   int32_t compact_period;
   int32_t blocks_per_sm;
-  int32_t reserved; /* must be 0 */
+  int32_t layout;
 } gaps_persistent_config;
 
 /* ---------------------------------------------------------------- sizing */
@@ -385,12 +405,13 @@ int gaps_shower_timed(const gaps_params* params, const gaps_batch* batch, int mo
 int gaps_shower_persistent(const gaps_params* params, const gaps_batch* batch,
                            const gaps_persistent_config* cfg, void* stream);
 
-/* Autotuner of the persistent form: times every block size in {128, 256,
- * 512} with compaction periods {2, 4, 8, 16} on this batch, the better of two
- * timings each (matrix element +
- * shower each time, CUDA events on `stream`) and returns the fastest in
- * *best (and its time in *best_ms, may be NULL).  Overwrites the batch's
- * events.  Synchronous. */
+/* Autotuner of the persistent form (batching): times every record layout
+ * (structure of arrays, tiles of 8 and of 32 events), block size {128, 256,
+ * 512} and compaction period {2, 4, 8, 16} on this batch's workspace, the
+ * better of two timings each (matrix element + shower each time, CUDA events
+ * on `stream`), and returns the fastest in *best (layout included; its time
+ * in *best_ms, may be NULL).  Overwrites the batch's events: regenerate them
+ * with the chosen layout as the batch's layout.  Synchronous. */
 int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch, gaps_persistent_config* best,
                              double* best_ms, void* stream);
 

@@ -34,7 +34,9 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
     off = align_up(off + bytes);
     return at;
   };
-  const int64_t pc = static_cast<int64_t>(cap) * n;
+  // per-parton arrays: room for the events rounded up to whole tiles of 32,
+  // so that every record layout fits
+  const int64_t pc = static_cast<int64_t>(cap) * ((n + 31) / 32 * 32);
   L->px = take(8 * pc);
   L->py = take(8 * pc);
   L->pz = take(8 * pc);
@@ -77,8 +79,13 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->total_bytes = off;
 }
 
+bool layout_ok(int layout) {
+  return layout == GAPS_LAYOUT_SOA || layout == GAPS_LAYOUT_TILE8 || layout == GAPS_LAYOUT_TILE32;
+}
+
 int check_batch(const gaps_batch* b) {
   if (!b || !sizes_ok(b->n_events, b->capacity)) return GAPS_ERR_INVALID;
+  if (!layout_ok(b->layout) || b->reserved != 0) return GAPS_ERR_INVALID;
   if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % kAlign) != 0) return GAPS_ERR_INVALID;
   if (static_cast<uint64_t>(b->first_event) + static_cast<uint64_t>(b->n_events) > 0x100000000ull)
     return GAPS_ERR_INVALID;
@@ -192,26 +199,16 @@ Events make_events(const gaps_batch& b) {
   E.stride = b.n_events;
   E.base = 0;
   E.cap = b.capacity;
+  set_layout(E, b.layout, b.n_events, b.capacity);
   return E;
 }
 
 // The view of workspace events [a, a + count) of E: same arrays, every
-// per-event pointer moved to event a, indices still strided by the whole
-// workspace.
+// per-event pointer moved to event a; the per-parton arrays keep their base
+// and the view's events are offset by a in their layout.
 Events sub_view(const Events& E, int64_t a, int64_t count) {
   Events V = E;
-  V.px += a;
-  V.py += a;
-  V.pz += a;
-  V.e += a;
-  V.flav += a;
-  V.col += a;
-  V.acol += a;
-  V.link += a;
-  V.dip += a;
-  V.dq2 += a;
-  V.dzp += a;
-  V.dinv += a;
+  V.slot_off = E.slot_off + static_cast<int>(a);
   V.lnt += a;
   V.t += a;
   V.weight += a;
@@ -345,13 +342,13 @@ int gaps_set_jobs(const gaps_job* jobs, int32_t n_jobs, const gaps_batch* batch,
 
 namespace {
 
-constexpr gaps_persistent_config kDefaultPersistent = {128, 8, 0, 0};
+constexpr gaps_persistent_config kDefaultPersistent = {128, 8, 0, GAPS_LAYOUT_SOA};
 
 bool config_ok(const gaps_persistent_config& c) {
   const bool threads_ok = c.block_threads == 64 || c.block_threads == 128 || c.block_threads == 256 ||
                           c.block_threads == 512;
   return threads_ok && c.compact_period >= 1 && c.compact_period <= 64 && c.blocks_per_sm >= 0 &&
-         c.blocks_per_sm <= 32 && c.reserved == 0;
+         c.blocks_per_sm <= 32 && layout_ok(c.layout);
 }
 
 // Clear the shower's counters (finished, step-limited, FP64 fallbacks, the
@@ -606,32 +603,43 @@ int gaps_autotune_persistent(const gaps_params* params, const gaps_batch* batch,
   if (!best || prepare(params, batch, &P, &E) != GAPS_OK) return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   *best = kDefaultPersistent;
+  best->layout = batch->layout;
   if (best_ms) *best_ms = 0.0;
   if (E.n == 0) return GAPS_OK;
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   double best_time = -1.0;
+  const int layouts[3] = {GAPS_LAYOUT_SOA, GAPS_LAYOUT_TILE8, GAPS_LAYOUT_TILE32};
   const int threads[3] = {128, 256, 512};
   const int periods[4] = {2, 4, 8, 16};
-  for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
-    for (int pi = 0; pi < 4 && e == cudaSuccess; ++pi) {
-      const gaps_persistent_config c = {threads[ti], periods[pi], 0, 0};
-      float shape_ms = -1.0f;  // the better of two timings of the shape
-      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-        e = launch_me(P, E, s);
-        if (e == cudaSuccess) e = clear_shower_counters(E, s);
-        if (e == cudaSuccess) e = cudaEventRecord(a, s);
-        if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
-        if (e == cudaSuccess) e = cudaEventRecord(b, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e == cudaSuccess && (shape_ms < 0.0f || ms < shape_ms)) shape_ms = ms;
-      }
-      if (e == cudaSuccess && (best_time < 0.0 || shape_ms < best_time)) {
-        best_time = shape_ms;
-        *best = c;
+  for (int li = 0; li < 3 && e == cudaSuccess; ++li) {
+    // the same workspace read in another record layout (sized for all)
+    gaps_batch bl = *batch;
+    bl.layout = layouts[li];
+    if (prepare(params, &bl, &P, &E) != GAPS_OK) {
+      e = cudaErrorInvalidValue;
+      break;
+    }
+    for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
+      for (int pi = 0; pi < 4 && e == cudaSuccess; ++pi) {
+        const gaps_persistent_config c = {threads[ti], periods[pi], 0, layouts[li]};
+        float shape_ms = -1.0f;  // the better of two timings of the shape
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+          e = launch_me(P, E, s);
+          if (e == cudaSuccess) e = clear_shower_counters(E, s);
+          if (e == cudaSuccess) e = cudaEventRecord(a, s);
+          if (e == cudaSuccess) e = launch_shower_persistent(P, E, c, s);
+          if (e == cudaSuccess) e = cudaEventRecord(b, s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+          if (e == cudaSuccess && (shape_ms < 0.0f || ms < shape_ms)) shape_ms = ms;
+        }
+        if (e == cudaSuccess && (best_time < 0.0 || shape_ms < best_time)) {
+          best_time = shape_ms;
+          *best = c;
+        }
       }
     }
   }
@@ -815,7 +823,7 @@ int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64
       max_active > pool->n_events)
     return GAPS_ERR_INVALID;
   const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
-  if (c.compact_period < 1 || c.reserved != 0 || c.blocks_per_sm < 0) return GAPS_ERR_INVALID;
+  if (c.compact_period < 1 || !layout_ok(c.layout) || c.blocks_per_sm < 0) return GAPS_ERR_INVALID;
   if (c.block_threads != 64 && c.block_threads != 128 && c.block_threads != 256 && c.block_threads != 512)
     return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -96,6 +96,7 @@ extern "C" int gaps_event_shapes_noalloc(const double* px, const double* py, con
   E.stride = n_events;
   E.base = 0;
   E.cap = capacity;
+  set_layout(E, GAPS_LAYOUT_SOA, n_events, capacity);
   DevParams P{};
   P.sqrt_s = sqrt_s;
   P.s = sqrt_s * sqrt_s;

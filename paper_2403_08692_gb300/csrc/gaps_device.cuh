@@ -121,17 +121,52 @@ struct Events {
   const uint16_t* job_of;
   unsigned long long* job_done;  // [GAPS_MAX_JOBS] finished events per job (multi-job batches)
   int64_t n;       // events in this view
-  int64_t stride;  // events in the whole workspace (the slot-major row length)
+  int64_t stride;  // events in the whole workspace (the row length of the per-event arrays)
   int64_t base;    // workspace index of this view's event 0
   int cap;
+  // Record layout of the per-parton arrays (gaps_batch::layout): element
+  // (slot, workspace event e) of a [cap] array is at
+  //   (e >> tile_shift) * tile_stride + slot * slot_stride + (e & ev_mask),
+  // and of a [2][cap] array at the same with 2 tile_stride and slot side * cap
+  // + slot.  Structure of arrays: tile_shift 31 (a single tile), slot_stride
+  // = the workspace's events, ev_mask all ones.  Tiles of T events: tile_shift
+  // log2 T, tile_stride cap T, slot_stride T, ev_mask T - 1.  slot_off is the
+  // workspace index of this view's event 0 (the per-parton arrays are never
+  // shifted; the per-event ones are).
+  // Workspace events number fewer than 2^31, and strides fit 32 bits, so
+  // each term is one 32 x 32 -> 64-bit multiply.
+  int tile_shift, ev_mask, tile_stride, slot_stride, slot_off;
 
+  // The part of an element's index that depends on the event only.
+  __device__ __forceinline__ int64_t event_base(int64_t ev, int tiles) const {
+    const int e = static_cast<int>(ev) + slot_off;
+    return static_cast<int64_t>(e >> tile_shift) * (tiles * tile_stride) + (e & ev_mask);
+  }
   __device__ __forceinline__ size_t at(int slot, int64_t ev) const {
-    return static_cast<size_t>(slot) * static_cast<size_t>(stride) + static_cast<size_t>(ev);
+    return static_cast<size_t>(event_base(ev, 1) + static_cast<int64_t>(slot) * slot_stride);
   }
   __device__ __forceinline__ size_t link_at(int side, int slot, int64_t ev) const {
-    return (static_cast<size_t>(side) * cap + slot) * static_cast<size_t>(stride) + static_cast<size_t>(ev);
+    return static_cast<size_t>(event_base(ev, 2) + static_cast<int64_t>(side * cap + slot) * slot_stride);
   }
 };
+
+// The layout fields of a view of n_events events (the workspace's row
+// length) with `capacity` slots.
+inline void set_layout(Events& E, int layout, int64_t n_events, int capacity) {
+  E.slot_off = 0;
+  if (layout == GAPS_LAYOUT_TILE8 || layout == GAPS_LAYOUT_TILE32) {
+    const int T = layout == GAPS_LAYOUT_TILE8 ? 8 : 32;
+    E.tile_shift = layout == GAPS_LAYOUT_TILE8 ? 3 : 5;
+    E.tile_stride = capacity * T;
+    E.slot_stride = T;
+    E.ev_mask = T - 1;
+  } else {
+    E.tile_shift = 31;  // events < 2^31: one tile
+    E.tile_stride = 0;
+    E.slot_stride = static_cast<int>(n_events);
+    E.ev_mask = 0x7fffffff;
+  }
+}
 
 // The parameters of event ev: its job's in a multi-job batch (kMulti), else
 // the launch's.  A compile-time choice, so that single-job kernels read

@@ -22,17 +22,30 @@ class Params(C.Structure):
                 ("max_steps", C.c_int32), ("trial_mode", C.c_int32)]
 
 
+LAYOUT_SOA, LAYOUT_TILE8, LAYOUT_TILE32 = 0, 1, 2
+LAYOUT_NAMES = {LAYOUT_SOA: "structure of arrays", LAYOUT_TILE8: "tiles of 8 events", LAYOUT_TILE32: "tiles of 32 events"}
+_TILE = {LAYOUT_TILE8: 8, LAYOUT_TILE32: 32}
+
+
 class PersistentConfig(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("compact_period", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("layout", C.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def persistent_config(cfg):
+    """A PersistentConfig from a PersistentConfig, a dict of its fields or None."""
+    if isinstance(cfg, dict):
+        return PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
+                                int(cfg.get("blocks_per_sm", 0)), int(cfg.get("layout", LAYOUT_SOA)))
+    return cfg
 
 
 class Batch(C.Structure):
     _fields_ = [("workspace", C.c_void_p), ("n_events", C.c_int64), ("capacity", C.c_int32),
-                ("first_event", C.c_uint32)]
+                ("first_event", C.c_uint32), ("layout", C.c_int32), ("reserved", C.c_int32)]
 
 
 _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "dq2", "dzp", "dinv", "t", "lnt",
@@ -212,6 +225,9 @@ def layout(n_events, capacity) -> Layout:
     return L
 
 
+_workspace_layout = layout
+
+
 def check_params(p: Params) -> int:
     return load().gaps_check_params(C.byref(p))
 
@@ -228,7 +244,7 @@ def _pp(p):
 
 
 def _batch(ws) -> Batch:
-    return Batch(C.c_void_p(ws.buffer.data_ptr()), ws.n_events, ws.capacity, ws.first_event)
+    return Batch(C.c_void_p(ws.buffer.data_ptr()), ws.n_events, ws.capacity, ws.first_event, ws.record_layout, 0)
 
 
 def generate_me(p, ws, stream=None):
@@ -264,9 +280,7 @@ def set_jobs(jobs, ws, stream=None):
 def shower_persistent(p, ws, cfg=None, stream=None):
     """gaps_shower_persistent: asynchronous, one launch.  cfg: PersistentConfig,
     a dict of its fields, or None for the library default."""
-    if isinstance(cfg, dict):
-        cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
-                               int(cfg.get("blocks_per_sm", 0)), 0)
+    cfg = persistent_config(cfg)
     ptr = C.byref(cfg) if cfg is not None else None
     _check(load().gaps_shower_persistent(_pp(p), C.byref(_batch(ws)), ptr, _stream_handle(stream)),
            "gaps_shower_persistent")
@@ -416,9 +430,7 @@ def pool_cycles(ws, first_cycle, n_cycles, max_active, stream=None):
 def pool_slice(ws, round_index, cycles, max_active, cfg=None, stream=None):
     """gaps_pool_slice: every live event runs up to `cycles` more cycles in one
     persistent launch.  cfg: PersistentConfig, a dict of its fields, or None."""
-    if isinstance(cfg, dict):
-        cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
-                               int(cfg.get("blocks_per_sm", 0)), 0)
+    cfg = persistent_config(cfg)
     ptr = C.byref(cfg) if cfg is not None else None
     _check(load().gaps_pool_slice(C.byref(_batch(ws)), int(round_index), int(cycles), int(max_active), ptr,
                                   _stream_handle(stream)), "gaps_pool_slice")
@@ -453,9 +465,7 @@ class CServer:
         self.ws = Workspace(pool_events, capacity)
         self.hist = torch.zeros((max_jobs, HIST_DOUBLES), dtype=torch.float64, device="cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        if isinstance(cfg, dict):
-            cfg = PersistentConfig(int(cfg["block_threads"]), int(cfg["compact_period"]),
-                                   int(cfg.get("blocks_per_sm", 0)), 0)
+        cfg = persistent_config(cfg)
         self._batch = _batch(self.ws)
         h = C.c_void_p()
         _check(load().gaps_server_create(C.byref(self._batch), C.c_void_p(self.hist.data_ptr()), int(max_jobs),
@@ -516,11 +526,15 @@ class Workspace:
     """A device workspace for one batch, allocated by PyTorch, with typed
     views of every array in the layout."""
 
-    def __init__(self, n_events, capacity=128, first_event=0, device="cuda"):
+    def __init__(self, n_events, capacity=128, first_event=0, device="cuda", layout=LAYOUT_SOA):
         import torch
         self.n_events = int(n_events)
         self.capacity = int(capacity)
         self.first_event = int(first_event)
+        # the record layout the library reads and writes this workspace in
+        # (gaps_batch::layout); a workspace holds any layout, so it may change
+        # between passes (the events must then be generated again)
+        self.record_layout = int(layout)
         nbytes = workspace_bytes(self.n_events, self.capacity)
         if nbytes == 0:
             raise ValueError("batch sizes out of range")
@@ -528,7 +542,7 @@ class Workspace:
         self._raw = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device)
         off = (-self._raw.data_ptr()) % 256
         self.buffer = self._raw[off:off + nbytes]
-        self.layout = layout(self.n_events, self.capacity)
+        self.layout = _workspace_layout(self.n_events, self.capacity)  # byte offsets of every array
 
     def view(self, name, dtype, shape):
         import torch
@@ -539,10 +553,27 @@ class Workspace:
         nbytes *= torch.empty((), dtype=dtype).element_size()
         return self.buffer[off:off + nbytes].view(dtype).view(*shape)
 
-    def momenta(self):
+    def slot_view(self, name, dtype, sides=0):
+        """A per-parton array as [capacity][n_events] ([2][capacity][n_events]
+        with sides=2): a view for the structure-of-arrays layout, a copy
+        (read only) for the tiled layouts."""
         import torch
         n, cap = self.n_events, self.capacity
-        return {c: self.view(c, torch.float64, (cap, n)) for c in ("e", "px", "py", "pz")}
+        shape = (cap, n) if not sides else (2, cap, n)
+        if self.record_layout == LAYOUT_SOA:
+            return self.view(name, dtype, shape)
+        T = _TILE[self.record_layout]
+        n_pad = (n + 31) // 32 * 32
+        tiles = n_pad // T
+        inner = (tiles, cap, T) if not sides else (tiles, 2, cap, T)
+        raw = self.view(name, dtype, inner)
+        if not sides:
+            return raw.permute(1, 0, 2).reshape(cap, n_pad)[:, :n]
+        return raw.permute(1, 2, 0, 3).reshape(2, cap, n_pad)[:, :, :n]
+
+    def momenta(self):
+        import torch
+        return {c: self.slot_view(c, torch.float64) for c in ("e", "px", "py", "pz")}
 
     def scalars(self):
         import torch
@@ -561,6 +592,5 @@ class Workspace:
 
     def colours(self):
         import torch
-        n, cap = self.n_events, self.capacity
-        return {"flav": self.view("flav", torch.int8, (cap, n)), "col": self.view("col", torch.int16, (cap, n)),
-                "acol": self.view("acol", torch.int16, (cap, n)), "link": self.view("link", torch.uint8, (2, cap, n))}
+        return {"flav": self.slot_view("flav", torch.int8), "col": self.slot_view("col", torch.int16),
+                "acol": self.slot_view("acol", torch.int16), "link": self.slot_view("link", torch.uint8, sides=2)}

@@ -23,8 +23,8 @@ cycles queued while the host inspects the last one.
 
 Every event is the event a single-job batch of its job produces: its
 draws are keyed by (seed, event id, its own cycle), never by where or when it
-ran, so a job's results are the same alone and in any mix (the histograms up
-to the order of floating-point additions).
+ran, so a job's results are the same alone and in any mix (the histograms
+too: they are exact fixed-point sums).
 """
 import bisect
 import collections
@@ -120,7 +120,7 @@ class Server:
     stand-in and device "cpu")."""
 
     def __init__(self, pool_events=None, capacity=128, memory_budget=None, cycles_per_round=8, clock="wall",
-                 device="cuda", mode="slice", cfg=None, device_layer=None):
+                 device="cuda", mode="slice", cfg=None, device_layer=None, layout=0):
         if device_layer is None:
             import torch
             device_layer = (gaps, torch)
@@ -142,7 +142,7 @@ class Server:
         self.mode = mode
         self.cfg = cfg
         pin = (lambda t: t) if device == "cpu" else (lambda t: t.pin_memory())
-        self.ws = G.Workspace(self.pool_events, self.capacity, device=device)
+        self.ws = G.Workspace(self.pool_events, self.capacity, device=device, layout=layout)
         self.stream = torch.cuda.Stream(device=device)
         self.hist = torch.zeros((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64, device=device)
         self.hist_host = pin(torch.empty((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64))

@@ -54,7 +54,7 @@ def test_header_constants_match_binding(g):
     assert f"GAPS_N_OBS = {g.N_OBS}, GAPS_N_BINS = 100, GAPS_HIST_ROW = 102" in text
     assert g.N_OBS == 8 and g.HIST_DOUBLES == 8 * 102 * 3
     assert C.sizeof(g.gaps.Params) == 48
-    assert C.sizeof(g.gaps.Batch) == 24
+    assert C.sizeof(g.gaps.Batch) == 32
     assert C.sizeof(g.gaps.Stats) == 15 * 8
 
 

@@ -20,9 +20,9 @@ def g():
     return g
 
 
-def _run(g, p, n, persistent, cfg=None, capacity=128, first_event=0):
+def _run(g, p, n, persistent, cfg=None, capacity=128, first_event=0, layout=0):
     import torch
-    ws = g.Workspace(n, capacity, first_event)
+    ws = g.Workspace(n, capacity, first_event, layout=layout)
     g.generate_me(p, ws)
     if persistent:
         g.shower_persistent(p, ws, cfg)
@@ -59,13 +59,16 @@ def test_persistent_equals_plain(g):
     assert pers[4][0] == 20011 and pers[4][6] >= 20011
 
 
+@pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("threads,period,per_sm", [(64, 1, 0), (128, 2, 0), (256, 4, 1), (512, 3, 0), (128, 8, 0),
                                                   (256, 16, 0), (512, 7, 1)])
-def test_persistent_launch_shapes(g, threads, period, per_sm):
+def test_persistent_launch_shapes(g, threads, period, per_sm, layout):
+    """Every launch shape, in every record layout (structure of arrays,
+    tiles of 8 and of 32 events), gives the plain form's events."""
     p = g.make_params(seed=6)
     plain = _run(g, p, 7001, persistent=False)
-    cfg = {"block_threads": threads, "compact_period": period, "blocks_per_sm": per_sm}
-    _assert_same(plain, _run(g, p, 7001, persistent=True, cfg=cfg))
+    cfg = {"block_threads": threads, "compact_period": period, "blocks_per_sm": per_sm, "layout": layout}
+    _assert_same(plain, _run(g, p, 7001, persistent=True, cfg=cfg, layout=layout))
 
 
 def test_persistent_matches_oracle(g, oracle_mod):

@@ -41,7 +41,7 @@ class FakePool:
         def view(self, name, dtype, shape):
             return {"counters": self.counters, "job_done": self.job_done}[name]
 
-    def Workspace(self, n, capacity, device="cpu"):
+    def Workspace(self, n, capacity, device="cpu", layout=0):
         return FakePool._Workspace(n, capacity, device)
 
     @staticmethod
