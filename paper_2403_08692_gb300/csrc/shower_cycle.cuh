@@ -159,13 +159,16 @@ __device__ __forceinline__ int choose_kernel(const DevParams& P, double zp, doub
 // The full FP64 SelectWinnerEmission (every trial exact, recomputed from the
 // momenta); the fallback of the FP32 screen.  The log-space scale of trial
 // j is L + ln(r_j)/c_j; the highest above ln t_C wins, the first on ties.
-// Returns false if no trial is above t_C.
+// This form covers partons first, first + stride, ... and keeps, in *best,
+// *code and w, the best of those trials above the incoming *best (the first
+// in loop order on ties; code = (2 i + side) * 8 + kappa orders the trials
+// as the loop does); returns whether one was found.
 template <int kMode>
-__device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
-                                   double lnt, EmitTask& w) {
-  double best = P.ln_tc;
+__device__ inline bool select_winner_fp64_range(const DevParams& P, const Events& E, int64_t ev, uint32_t id,
+                                                int step, int n, double lnt, int first, int stride, EmitTask& w,
+                                                double& best, int& code) {
   bool found = false;
-  for (int i = 0; i < n; ++i) {
+  for (int i = first; i < n; i += stride) {
     const bool gluon = E.flav[E.at(i, ev)] == kGluon;
     const bool combined = gluon && per_dipole<kMode>(P);
     const int nk = gluon && !combined ? 1 + P.nf : 1;
@@ -186,6 +189,7 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
           const double lt = lnt + log_fp64(u) * inv_c;
           if (lt > best) {
             best = lt;
+            code = (2 * i + side) * 8 + kappa;
             found = true;
             w.lnt = lt;
             w.q2 = d.q2;
@@ -202,6 +206,16 @@ __device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, i
     }
   }
   return found;
+}
+
+// The serial form: every parton in one thread.  Returns false if no trial
+// is above t_C.
+template <int kMode>
+__device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+                                   double lnt, EmitTask& w) {
+  double best = P.ln_tc;
+  int code = 0;
+  return select_winner_fp64_range<kMode>(P, E, ev, id, step, n, lnt, 0, 1, w, best, code);
 }
 
 // Exact FP64 acceptance ratio of Eq. (A.9) with the (1 - y) factor, for a
@@ -374,14 +388,17 @@ __device__ __forceinline__ void screen_group_reduce(Screen& sc) {
   }
 }
 
-// The rest of the cycle once the screen is known: the exact winner scale,
-// CheckCutoff, AcceptOrVeto and the decision hash.  Returns kCycleFinished
-// when the event left the active state (status written), kCycleAccepted
-// with `task` filled when an emission must be generated, kCycleVetoed
-// otherwise.
+// What the FP32 screen settles about a cycle: no trial above the cutoff, a
+// certain winner (its exact scale computed), or neither -- then the exact
+// FP64 selection decides (select_winner_fp64 / fallback_warp).
+enum : int { kScreenNone = 0, kScreenWinner = 1, kScreenUndecided = 2 };
+
+// The first part of the cycle once the screen is known: the cycle and work
+// counts, and the screen's verdict; for a certain winner its exact scale
+// (from the FP64 cache) and the winner's data in `task`.
 template <int kMode>
-__device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
-                                   double lnt, const Screen& sc, EmitTask& task) {
+__device__ inline int cycle_screen(const DevParams& P, const Events& E, int64_t ev, int step, double lnt,
+                                   const Screen& sc, EmitTask& task) {
   const float best_key = sc.best_key, best_m = sc.best_m, others_hi = sc.others_hi;
   const int best_code = sc.best_code;
   const uint32_t best_hi = sc.best_hi, best_lo = sc.best_lo;
@@ -394,10 +411,10 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   const float thr = P.lg2_tc_f - lt2;
   const float thr_m = 2e-6f * (1.0f + fabsf(lt2) + fabsf(P.lg2_tc_f));
 
-  bool have = false, decided = false;
   if (best_code < 0 || fmaxf(best_key + best_m, others_hi) < thr - thr_m) {
-    decided = true;  // certainly no trial above the cutoff
-  } else if (best_key - best_m > thr + thr_m && others_hi < best_key - best_m) {
+    return kScreenNone;  // certainly no trial above the cutoff
+  }
+  if (best_key - best_m > thr + thr_m && others_hi < best_key - best_m) {
     // Certain winner: its scale exactly, from the FP64 cache.
     const int dcode = best_code >> 3, kappa = best_code & 7;
     const int i = dcode >> 1, side = dcode & 1;
@@ -418,14 +435,85 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
       task.side = side;
       task.kappa = kappa;
       task.kind = kind;
-      have = decided = true;
+      return kScreenWinner;
     }
   }
-  if (!decided) {
-    atomicAdd(&E.counters[2], 1ull);  // screen undecided: full FP64 cycle
-    have = select_winner_fp64<kMode>(P, E, ev, id, step, n, lnt, task);
-  }
+  return kScreenUndecided;
+}
 
+// The exact FP64 selection for the undecided events of a warp, each computed
+// by the whole warp: for every lane whose `need` is set, in turn, lane l takes
+// partons l, l + 32, ... of that lane's event and the warp keeps the highest
+// scale (the first trial in loop order on ties), the serial selection's
+// winner.  The rare undecided cycle of an event with many partons thus takes
+// a thirty-second of the dependent loads and FP64 work on its lane, which a
+// whole launch or pool would otherwise wait for.  Sets have / task on the
+// needing lanes.  Every lane of the warp must call it.
+template <int kMode>
+__device__ __noinline__ void fallback_warp(const DevParams& P0, const Events& E, bool need, int64_t ev, uint32_t id,
+                                           int step, int n, double lnt, bool& have, EmitTask& task) {
+  const int lane = static_cast<int>(threadIdx.x & 31);
+  unsigned pending = __ballot_sync(0xffffffffu, need);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const long long sev = __shfl_sync(0xffffffffu, static_cast<long long>(ev), src);
+    const uint32_t sid = __shfl_sync(0xffffffffu, id, src);
+    const int sstep = __shfl_sync(0xffffffffu, step, src);
+    const int sn = __shfl_sync(0xffffffffu, n, src);
+    const double slnt = __shfl_sync(0xffffffffu, lnt, src);
+    const DevParams& P = params_of<kMode == kModeMulti>(P0, E, sev);
+    EmitTask w;
+    double best = P.ln_tc;
+    int code = 0x7fffffff;
+    const bool found = select_winner_fp64_range<kMode>(P, E, sev, sid, sstep, sn, slnt, lane, 32, w, best, code);
+    // the highest scale; equal scales go to the smallest code
+    double wb = best;
+    int wc = code;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, wb, off);
+      const int oc = __shfl_xor_sync(0xffffffffu, wc, off);
+      if (ob > wb || (ob == wb && oc < wc)) {
+        wb = ob;
+        wc = oc;
+      }
+    }
+    const unsigned own = __ballot_sync(0xffffffffu, found && code == wc);
+    if (own) {
+      const int ol = __ffs(own) - 1;
+      const double t_lnt = __shfl_sync(0xffffffffu, w.lnt, ol), t_q2 = __shfl_sync(0xffffffffu, w.q2, ol);
+      const double t_zp = __shfl_sync(0xffffffffu, w.zp, ol), t_inv = __shfl_sync(0xffffffffu, w.inv_ls, ol);
+      const uint32_t packed = __shfl_sync(0xffffffffu,
+                                          static_cast<uint32_t>(w.i) | (static_cast<uint32_t>(w.k) << 8) |
+                                              (static_cast<uint32_t>(w.side) << 16) |
+                                              (static_cast<uint32_t>(w.kappa) << 20) |
+                                              (static_cast<uint32_t>(w.kind) << 24),
+                                          ol);
+      if (lane == src) {
+        task.lnt = t_lnt;
+        task.q2 = t_q2;
+        task.zp = t_zp;
+        task.inv_ls = t_inv;
+        task.i = static_cast<uint8_t>(packed & 255u);
+        task.k = static_cast<uint8_t>((packed >> 8) & 255u);
+        task.side = static_cast<uint8_t>((packed >> 16) & 15u);
+        task.kappa = static_cast<uint8_t>((packed >> 20) & 15u);
+        task.kind = static_cast<uint8_t>(packed >> 24);
+      }
+    }
+    if (lane == src) have = own != 0u;
+  }
+}
+
+// The rest of the cycle once the winner is known (have: a trial above t_C,
+// with its data in task): CheckCutoff, AcceptOrVeto and the decision hash.
+// Returns kCycleFinished when the event left the active state (status
+// written), kCycleAccepted with `task` filled when an emission must be
+// generated, kCycleVetoed otherwise.
+template <int kMode>
+__device__ inline int cycle_conclude(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+                                     bool have, EmitTask& task) {
   // ---- CheckCutoff.
   if (!have) {
     finish_event(E, ev, GAPS_DONE, P.tc);
@@ -497,6 +585,19 @@ __device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t 
   task.n = n;
   task.step = step;
   return kCycleAccepted;
+}
+
+// The whole decision of a cycle in one thread, the exact selection serial.
+template <int kMode>
+__device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
+                                   double lnt, const Screen& sc, EmitTask& task) {
+  const int s = cycle_screen<kMode>(P, E, ev, step, lnt, sc, task);
+  bool have = s == kScreenWinner;
+  if (s == kScreenUndecided) {
+    atomicAdd(&E.counters[2], 1ull);  // screen undecided: full FP64 cycle
+    have = select_winner_fp64<kMode>(P, E, ev, id, step, n, lnt, task);
+  }
+  return cycle_conclude<kMode>(P, E, ev, id, step, n, have, task);
 }
 
 // Phase 1 of a cycle for active event ev, one thread: SelectWinnerEmission

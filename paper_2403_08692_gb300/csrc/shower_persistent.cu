@@ -191,6 +191,9 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
         if (limited) {
           finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
         } else {
+          // the rare undecided cycle takes its exact selection serially here:
+          // the warp-wide form (fallback_warp) measured slower in this kernel
+          // (its spills cost more than the waits it saves)
           r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
         }
         if (r == kCycleAccepted) {

@@ -226,12 +226,27 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     const bool lead = active && sub == 0;
     int r = kCycleFinished;
     EmitTask task;
+    // The screen's verdict; a cycle it leaves undecided gets the exact FP64
+    // selection from the whole warp.
+    int verdict = kScreenNone;
+    double lnt = 0.0;
+    uint32_t id = 0;
+    if (lead && !limited) {
+      const DevParams& P = job_params<kMulti>(P0, E, job);
+      lnt = E.lnt[ev];
+      id = event_id(P, E, ev);
+      verdict = cycle_screen<kMode>(P, E, ev, step, lnt, sc, task);
+      if (verdict == kScreenUndecided) atomicAdd(&E.counters[2], 1ull);  // full FP64 cycle
+    }
+    bool have = verdict == kScreenWinner;
+    if (__any_sync(0xffffffffu, verdict == kScreenUndecided))
+      fallback_warp<kMode>(P0, E, verdict == kScreenUndecided, ev, id, step, n, lnt, have, task);
     if (lead) {
       const DevParams& P = job_params<kMulti>(P0, E, job);
       if (limited) {
         finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
       } else {
-        r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+        r = cycle_conclude<kMode>(P, E, ev, id, step, n, have, task);
       }
       if (r == kCycleFinished) {
         atomicAdd(&E.counters[0], 1ull);
