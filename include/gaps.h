@@ -275,20 +275,26 @@ int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begi
 /* Enqueue n_cycles shower steps, numbered first_cycle.., over the live
  * events: each step runs the select/veto phase of the events in the active
  * list and the splittings the previous step accepted (gaps_shower's plain
- * form).  max_active bounds the live events (it sizes the grids).  No host
+ * form).  max_active bounds the live events (it sizes the grids).
+ * shared: NULL, or parameters that every live job of the pool was admitted
+ * with apart from its seed; the kernels then take the physics from `shared`
+ * and only each job's Philox key and event-id offset from the job table
+ * (the same events, faster).  A job whose other parameters differ from
+ * `shared` is showered with `shared`'s physics: pass NULL for a mix.  No host
  * synchronisation. */
 int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
-                     void* stream);
+                     const gaps_params* shared, void* stream);
 
 /* The same advance by the persistent form (time-sliced): one launch runs
  * every live event for up to `cycles` (1..255) more veto cycles in per-block
  * pools (cfg as for gaps_shower_persistent, NULL for the default), and the
  * events still active afterwards make up the next active list.  `round`
  * numbers the slices (the `cycle` of gaps_pool_admit and
- * gaps_pool_progress).  A pool is driven either by gaps_pool_cycles or by
- * gaps_pool_slice.  No host synchronisation. */
+ * gaps_pool_progress); shared as for gaps_pool_cycles.  A pool is driven
+ * either by gaps_pool_cycles or by gaps_pool_slice.  No host
+ * synchronisation. */
 int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64_t max_active,
-                    const gaps_persistent_config* cfg, void* stream);
+                    const gaps_persistent_config* cfg, const gaps_params* shared, void* stream);
 
 /* Read the number of live events before step `cycle` and, if job_done_out
  * is not NULL, the finished-event count of every job slot

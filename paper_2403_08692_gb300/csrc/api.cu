@@ -794,12 +794,22 @@ int gaps_pool_admit(const gaps_params* params, int32_t job_slot, int64_t ev_begi
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 
+// The launch parameters of a pool call: the live jobs' shared parameters
+// (the keyed modes) or none (every parameter from the job table).
+int pool_params(const gaps_params* shared, DevParams* P) {
+  if (!shared) return GAPS_OK;
+  if (gaps_check_params(shared) != GAPS_OK) return GAPS_ERR_INVALID;
+  *P = make_dev_params(*shared, 0);
+  P->shared_physics = 1;
+  return GAPS_OK;
+}
+
 int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycles, int64_t max_active,
-                     void* stream) {
+                     const gaps_params* shared, void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || first_cycle < 0 || n_cycles < 0 || max_active < 0 ||
-      max_active > pool->n_events)
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || pool_params(shared, &P) != GAPS_OK || first_cycle < 0 ||
+      n_cycles < 0 || max_active < 0 || max_active > pool->n_events)
     return GAPS_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t c = first_cycle; c < first_cycle + n_cycles; ++c) {
@@ -816,11 +826,11 @@ int gaps_pool_cycles(const gaps_batch* pool, int64_t first_cycle, int32_t n_cycl
 }
 
 int gaps_pool_slice(const gaps_batch* pool, int64_t round, int32_t cycles, int64_t max_active,
-                    const gaps_persistent_config* cfg, void* stream) {
+                    const gaps_persistent_config* cfg, const gaps_params* shared, void* stream) {
   DevParams P;
   Events E;
-  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || round < 0 || cycles < 1 || cycles > 255 || max_active < 0 ||
-      max_active > pool->n_events)
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || pool_params(shared, &P) != GAPS_OK || round < 0 ||
+      cycles < 1 || cycles > 255 || max_active < 0 || max_active > pool->n_events)
     return GAPS_ERR_INVALID;
   const gaps_persistent_config c = cfg ? *cfg : kDefaultPersistent;
   if (c.compact_period < 1 || !layout_ok(c.layout) || c.blocks_per_sm < 0) return GAPS_ERR_INVALID;

@@ -4,9 +4,16 @@
 // Layout of the work.  The finished events are first bucketed by parton
 // multiplicity (count, scan, scatter into an index list), so the threads of
 // a warp handle events of the same size: the O(n^3) loops of thrust and
-// Durham then run with no lane waiting on a larger neighbour.  One thread
-// handles one event, with per-thread arrays sized by the bucket (16, 32, 64,
-// 128 or 256 partons).
+// Durham then run with no lane waiting on a larger neighbour.  Events of up
+// to 8 partons take one thread each, with per-thread arrays.  Larger events
+// take a group of L lanes (8 lanes for 9..16 partons, a warp above): the
+// event's momenta sit in shared memory, the lanes split the O(n^2) pairs of
+// each search and reduce their partial results in the serial loop's order
+// (the first pair wins ties, as in the oracle), and the O(n) FP64 steps run
+// on every lane alike.  A single thread would take about 0.2 ms for one
+// 16-parton event, and every launch -- one per finished job when a serving
+// pool finalises its jobs one by one -- would wait that long for its largest
+// event; the groups cut that wait by L.
 //
 // Precision.  As in the shower, the searches run in FP32 and the answers in
 // FP64:
@@ -329,6 +336,378 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   for (int h = 0; h < 4; ++h) E.obs[h * E.stride + ev] = yres[h];
 }
 
+// ------------------------------------------------------- lane groups
+// Lanes of this thread's aligned group of L (L a power of two, <= 32).
+template <int L>
+__device__ __forceinline__ unsigned group_lanes() {
+  if constexpr (L == 32) {
+    return 0xffffffffu;
+  } else {
+    return ((1u << L) - 1u) << ((threadIdx.x & 31u) & ~static_cast<unsigned>(L - 1));
+  }
+}
+
+// The pairs (j, k), j < k < n, of one lane: positions sub, sub + L, ... of
+// the serial loop (j outer, k inner); p is the position.
+struct PairWalk {
+  int j, off, row, p;
+  __device__ __forceinline__ void start(int n, int sub) {
+    j = 0;
+    off = sub;
+    row = n - 1;
+    p = sub;
+    settle(n);
+  }
+  __device__ __forceinline__ void settle(int n) {
+    while (j < n - 1 && off >= row) {
+      off -= row;
+      ++j;
+      row = n - 1 - j;
+    }
+  }
+  __device__ __forceinline__ bool valid(int n) const { return j < n - 1; }
+  __device__ __forceinline__ int k() const { return j + 1 + off; }
+  template <int L>
+  __device__ __forceinline__ void next(int n) {
+    off += L;
+    p += L;
+    settle(n);
+  }
+};
+
+// The event's arrays in shared memory, one set per group.
+template <int MAXJ>
+struct GroupArrays {
+  double je[MAXJ], jx[MAXJ], jy[MAXJ], jz[MAXJ], ja[MAXJ];
+  float fx[MAXJ], fy[MAXJ], fz[MAXJ], fe2[MAXJ];
+};
+
+// thrust_fp64 over the group: each lane takes its pairs, the group keeps the
+// longest P and, on equal lengths, the first candidate in the serial loop's
+// order (pair position x 4 + sign choice), so the result is the serial one.
+template <int MAXJ, int L>
+__device__ double thrust_fp64_group(int n, const GroupArrays<MAXJ>& a, double sum_abs, int sub, unsigned gm,
+                                    double& ax, double& ay, double& az) {
+  double best2 = -1.0, bx = 0.0, by = 0.0, bz = 0.0;
+  int bidx = 0x7fffffff;
+  PairWalk w;
+  for (w.start(n, sub); w.valid(n); w.next<L>(n)) {
+    const int j = w.j, k = w.k();
+    const double nx = a.jy[j] * a.jz[k] - a.jz[j] * a.jy[k];
+    const double ny = a.jz[j] * a.jx[k] - a.jx[j] * a.jz[k];
+    const double nz = a.jx[j] * a.jy[k] - a.jy[j] * a.jx[k];
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) continue;
+    double px = 0.0, py = 0.0, pz = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == j || i == k) continue;
+      const double sg = (a.jx[i] * nx + a.jy[i] * ny + a.jz[i] * nz) >= 0.0 ? 1.0 : -1.0;
+      px += sg * a.jx[i];
+      py += sg * a.jy[i];
+      pz += sg * a.jz[i];
+    }
+    for (int c = 0; c < 4; ++c) {
+      const double fj = (c & 2) ? -1.0 : 1.0, fk = (c & 1) ? -1.0 : 1.0;
+      const double cx = px + fj * a.jx[j] + fk * a.jx[k];
+      const double cy = py + fj * a.jy[j] + fk * a.jy[k];
+      const double cz = pz + fj * a.jz[j] + fk * a.jz[k];
+      const double c2 = cx * cx + cy * cy + cz * cz;
+      if (c2 > best2) {  // within a lane the positions rise: the first wins ties
+        best2 = c2;
+        bidx = 4 * w.p + c;
+        bx = cx;
+        by = cy;
+        bz = cz;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < L; off <<= 1) {
+    const double o2 = __shfl_xor_sync(gm, best2, off);
+    const int oi = __shfl_xor_sync(gm, bidx, off);
+    const double ox = __shfl_xor_sync(gm, bx, off), oy = __shfl_xor_sync(gm, by, off);
+    const double oz = __shfl_xor_sync(gm, bz, off);
+    if (o2 > best2 || (o2 == best2 && oi < bidx)) {
+      best2 = o2;
+      bidx = oi;
+      bx = ox;
+      by = oy;
+      bz = oz;
+    }
+  }
+  if (best2 < 0.0) {  // collinear: T = 1 along the first momentum
+    const double l = sqrt(a.jx[0] * a.jx[0] + a.jy[0] * a.jy[0] + a.jz[0] * a.jz[0]);
+    ax = a.jx[0] / l;
+    ay = a.jy[0] / l;
+    az = a.jz[0] / l;
+    return 1.0;
+  }
+  const double l = sqrt(best2), inv_l = 1.0 / l;
+  ax = bx * inv_l;
+  ay = by * inv_l;
+  az = bz * inv_l;
+  return l / sum_abs;
+}
+
+// event_shapes for one event by a group of L lanes (every lane of the group
+// calls it for the same event).  The searches give exactly the serial
+// results: each lane screens its pairs in the serial order, the group merges
+// the lanes' bests with the serial tie rule, and the O(n) FP64 steps (the
+// thrust sum, hemispheres, broadenings, the merged jets) run on every lane in
+// the serial order.  Lane 0 of the group writes the observables.
+template <int MAXJ, int L>
+__device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t ev, int n, GroupArrays<MAXJ>& a,
+                                   int sub, unsigned gm) {
+  const DevParams& P = params_of_event(P0, E, ev);
+  for (int i = sub; i < n; i += L) {
+    const size_t at = E.at(i, ev);
+    const double x = E.px[at], y = E.py[at], z = E.pz[at];
+    a.je[i] = E.e[at];
+    a.jx[i] = x;
+    a.jy[i] = y;
+    a.jz[i] = z;
+    a.fx[i] = f32_from_f64(x);
+    a.fy[i] = f32_from_f64(y);
+    a.fz[i] = f32_from_f64(z);
+    a.ja[i] = sqrt(x * x + y * y + z * z);
+  }
+  __syncwarp(gm);
+  double sum_abs = 0.0;
+  for (int i = 0; i < n; ++i) sum_abs += a.ja[i];
+  const float sum_absf = f32_from_f64(sum_abs);
+
+  // ---- thrust
+  double thrust = 1.0, ax = 0.0, ay = 0.0, az = 0.0;
+  bool decided = false;
+  if (n == 2) {
+    const double l = sqrt(a.jx[0] * a.jx[0] + a.jy[0] * a.jy[0] + a.jz[0] * a.jz[0]);
+    ax = a.jx[0] / l;
+    ay = a.jy[0] / l;
+    az = a.jz[0] / l;
+    decided = true;
+  } else if (n <= kMaskMax) {
+    Top2 top;
+    const unsigned long long full = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+    PairWalk w;
+    for (w.start(n, sub); w.valid(n); w.next<L>(n)) {
+      const int j = w.j, k = w.k();
+      const float nx = a.fy[j] * a.fz[k] - a.fz[j] * a.fy[k];
+      const float ny = a.fz[j] * a.fx[k] - a.fx[j] * a.fz[k];
+      const float nz = a.fx[j] * a.fy[k] - a.fy[j] * a.fx[k];
+      if (nx == 0.0f && ny == 0.0f && nz == 0.0f) continue;
+      float px = 0.0f, py = 0.0f, pz = 0.0f;
+      unsigned long long mask = 0ull;
+      for (int i = 0; i < n; ++i) {
+        if (i == j || i == k) continue;
+        if (a.fx[i] * nx + a.fy[i] * ny + a.fz[i] * nz >= 0.0f) {
+          px += a.fx[i];
+          py += a.fy[i];
+          pz += a.fz[i];
+          mask |= 1ull << i;
+        } else {
+          px -= a.fx[i];
+          py -= a.fy[i];
+          pz -= a.fz[i];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const bool pj = !(c & 2), pk = !(c & 1);
+        const float cx = px + (pj ? a.fx[j] : -a.fx[j]) + (pk ? a.fx[k] : -a.fx[k]);
+        const float cy = py + (pj ? a.fy[j] : -a.fy[j]) + (pk ? a.fy[k] : -a.fy[k]);
+        const float cz = pz + (pj ? a.fz[j] : -a.fz[j]) + (pk ? a.fz[k] : -a.fz[k]);
+        unsigned long long m = mask | (pj ? 1ull << j : 0ull) | (pk ? 1ull << k : 0ull);
+        if (m & 1ull) m = ~m & full;
+        top.add(cx * cx + cy * cy + cz * cz, m);
+      }
+    }
+    // The top two distinct partitions of the union: each lane's two entries
+    // added to the other's (the best score of every partition reaches the
+    // merged pair; only which of two equal scores is first can depend on
+    // the order, and equal scores leave the search to the exact FP64 pass).
+#pragma unroll
+    for (int off = 1; off < L; off <<= 1) {
+      const float s1 = __shfl_xor_sync(gm, top.s1, off), s2 = __shfl_xor_sync(gm, top.s2, off);
+      const unsigned long long m1 = __shfl_xor_sync(gm, top.m1, off), m2 = __shfl_xor_sync(gm, top.m2, off);
+      top.add(s1, m1);
+      top.add(s2, m2);
+    }
+    const float margin = 8.0f * static_cast<float>(n + 2) * 6.0e-8f * sum_absf * sum_absf;
+    if (top.s1 >= 0.0f && top.s2 < top.s1 - margin) {
+      double px = 0.0, py = 0.0, pz = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double sg = ((top.m1 >> i) & 1ull) ? 1.0 : -1.0;
+        px += sg * a.jx[i];
+        py += sg * a.jy[i];
+        pz += sg * a.jz[i];
+      }
+      const double l = sqrt(px * px + py * py + pz * pz), inv_l = 1.0 / l;
+      thrust = l / sum_abs;
+      ax = px * inv_l;
+      ay = py * inv_l;
+      az = pz * inv_l;
+      decided = true;
+    }
+  }
+  if (!decided) {
+    if (sub == 0) atomicAdd(&E.counters[4], 1ull);  // thrust decided by the exact FP64 search
+    thrust = thrust_fp64_group<MAXJ, L>(n, a, sum_abs, sub, gm, ax, ay, az);
+  }
+  double hp[4] = {0, 0, 0, 0}, hm[4] = {0, 0, 0, 0};
+  double bp = 0.0, bm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double x = a.jx[i], y = a.jy[i], z = a.jz[i];
+    const long long pn = __double_as_longlong(x * ax + y * ay + z * az);
+    const bool plus = pn >= 0 || pn == static_cast<long long>(0x8000000000000000ull);
+    double* h = plus ? hp : hm;
+    h[0] += a.je[i];
+    h[1] += x;
+    h[2] += y;
+    h[3] += z;
+    const double cx = y * az - z * ay, cy = z * ax - x * az, cz = x * ay - y * ax;
+    const double pt = sqrt(cx * cx + cy * cy + cz * cz);
+    if (plus) {
+      bp += pt;
+    } else {
+      bm += pt;
+    }
+  }
+  if (sub == 0) {
+    const double mp = hp[0] * hp[0] - hp[1] * hp[1] - hp[2] * hp[2] - hp[3] * hp[3];
+    const double mm = hm[0] * hm[0] - hm[1] * hm[1] - hm[2] * hm[2] - hm[3] * hm[3];
+    E.obs[4 * E.stride + ev] = 1.0 - thrust;
+    E.obs[5 * E.stride + ev] = fmax(mp, mm) * P.inv_s;
+    const double inv_2sum = 0.5 / sum_abs;
+    bp *= inv_2sum;
+    bm *= inv_2sum;
+    E.obs[6 * E.stride + ev] = bp + bm;
+    E.obs[7 * E.stride + ev] = fmax(bp, bm);
+  }
+
+  // ---- Durham (E-scheme)
+  __syncwarp(gm);  // every lane has read the FP32 momenta
+  for (int i = sub; i < n; i += L) {
+    const float e = f32_from_f64(a.je[i]);
+    a.fe2[i] = e * e;
+    const float r = rsqrtf(a.fx[i] * a.fx[i] + a.fy[i] * a.fy[i] + a.fz[i] * a.fz[i]);
+    a.fx[i] *= r;
+    a.fy[i] *= r;
+    a.fz[i] *= r;
+  }
+  __syncwarp(gm);
+  double yres[4] = {-1.0, -1.0, -1.0, -1.0};
+  auto y_exact = [&](int i, int j) {
+    const double cosij = (a.jx[i] * a.jx[j] + a.jy[i] * a.jy[j] + a.jz[i] * a.jz[j]) / (a.ja[i] * a.ja[j]);
+    return 2.0 * fmin(a.je[i] * a.je[i], a.je[j] * a.je[j]) * (1.0 - cosij) * P.inv_s;
+  };
+  auto bounds = [&](int i, int j, float& y, float& rel) {
+    const float dx = a.fx[i] - a.fx[j], dy = a.fy[i] - a.fy[j], dz = a.fz[i] - a.fz[j];
+    const float d = dx * dx + dy * dy + dz * dz;
+    y = fminf(a.fe2[i], a.fe2[j]) * d;
+    rel = 4.0e-6f + 1.0e-6f * rsqrtf(fmaxf(d, 1e-30f));
+  };
+  for (int m = n; m > 1; --m) {
+    // pass 1: the smallest FP32 upper bound, the first pair on ties
+    float ubest = INFINITY;
+    int up = 0x7fffffff, ui = 0, uj = 1;
+    PairWalk w;
+    for (w.start(m, sub); w.valid(m); w.next<L>(m)) {
+      float y, rel;
+      bounds(w.j, w.k(), y, rel);
+      const float ub = y * (1.0f + rel) + 1e-30f;
+      if (ub < ubest) {
+        ubest = ub;
+        up = w.p;
+        ui = w.j;
+        uj = w.k();
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < L; off <<= 1) {
+      const float ou = __shfl_xor_sync(gm, ubest, off);
+      const int op = __shfl_xor_sync(gm, up, off), oi = __shfl_xor_sync(gm, ui, off);
+      const int oj = __shfl_xor_sync(gm, uj, off);
+      if (ou < ubest || (ou == ubest && op < up)) {
+        ubest = ou;
+        up = op;
+        ui = oi;
+        uj = oj;
+      }
+    }
+    // pass 2: the pairs whose lower bound reaches it
+    int n_cand = 0;
+    for (w.start(m, sub); w.valid(m); w.next<L>(m)) {
+      float y, rel;
+      bounds(w.j, w.k(), y, rel);
+      n_cand += y * (1.0f - rel) <= ubest ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 1; off < L; off <<= 1) n_cand += __shfl_xor_sync(gm, n_cand, off);
+    double ymin = 0.0;
+    int bi = ui, bj = uj;
+    if (n_cand == 1) {
+      ymin = y_exact(ui, uj);
+    } else {
+      if (sub == 0) atomicAdd(&E.counters[5], 1ull);  // merges with several FP64 candidates
+      int bp_ = 0x7fffffff;
+      ymin = INFINITY;
+      for (w.start(m, sub); w.valid(m); w.next<L>(m)) {
+        float y, rel;
+        bounds(w.j, w.k(), y, rel);
+        if (y * (1.0f - rel) > ubest) continue;
+        const double yy = y_exact(w.j, w.k());
+        if (bp_ == 0x7fffffff || yy < ymin) {
+          ymin = yy;
+          bp_ = w.p;
+          bi = w.j;
+          bj = w.k();
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < L; off <<= 1) {
+        const double oy = __shfl_xor_sync(gm, ymin, off);
+        const int op = __shfl_xor_sync(gm, bp_, off), oi = __shfl_xor_sync(gm, bi, off);
+        const int oj = __shfl_xor_sync(gm, bj, off);
+        // lanes without a candidate hold position 0x7fffffff
+        if (op != 0x7fffffff && (bp_ == 0x7fffffff || oy < ymin || (oy == ymin && op < bp_))) {
+          ymin = oy;
+          bp_ = op;
+          bi = oi;
+          bj = oj;
+        }
+      }
+    }
+    const int idx = m - 3;
+    if (idx >= 0 && idx < 4) yres[idx] = ymin;
+    __syncwarp(gm);  // every lane is done reading the jets of this merge
+    if (sub == 0) {
+      a.je[bi] += a.je[bj];
+      a.jx[bi] += a.jx[bj];
+      a.jy[bi] += a.jy[bj];
+      a.jz[bi] += a.jz[bj];
+      a.je[bj] = a.je[m - 1];
+      a.jx[bj] = a.jx[m - 1];
+      a.jy[bj] = a.jy[m - 1];
+      a.jz[bj] = a.jz[m - 1];
+      a.ja[bj] = a.ja[m - 1];
+      a.ja[bi] = sqrt(a.jx[bi] * a.jx[bi] + a.jy[bi] * a.jy[bi] + a.jz[bi] * a.jz[bi]);
+      a.fe2[bj] = a.fe2[m - 1];
+      a.fx[bj] = a.fx[m - 1];
+      a.fy[bj] = a.fy[m - 1];
+      a.fz[bj] = a.fz[m - 1];
+      const float e = f32_from_f64(a.je[bi]);
+      a.fe2[bi] = e * e;
+      const float x = f32_from_f64(a.jx[bi]), y = f32_from_f64(a.jy[bi]), z = f32_from_f64(a.jz[bi]);
+      const float r = rsqrtf(x * x + y * y + z * z);
+      a.fx[bi] = x * r;
+      a.fy[bi] = y * r;
+      a.fz[bi] = z * r;
+    }
+    __syncwarp(gm);
+  }
+  if (sub == 0)
+    for (int h = 0; h < 4; ++h) E.obs[h * E.stride + ev] = yres[h];
+}
+
 // ------------------------------------------------------------- buckets
 // Parton count of event ev if it gets observables: finished, with 2 ..
 // capacity partons (the shower never writes another count; callers that pass
@@ -420,6 +799,36 @@ __global__ void __launch_bounds__(kShapeThreads) k_event_shapes(DevParams P, Eve
   }
 }
 
+// Events of buckets n_lo..n_hi (all with n <= MAXJ), L lanes per event, T
+// threads per block.
+template <int MAXJ, int L, int T>
+__global__ void __launch_bounds__(T) k_event_shapes_group(DevParams P, Events E, const int* order,
+                                                          const int* offsets, int n_lo, int n_hi) {
+  constexpr int G = T / L;
+  __shared__ GroupArrays<MAXJ> s_ev[G];
+  const int g = threadIdx.x / L, sub = threadIdx.x % L;
+  const unsigned gm = group_lanes<L>();
+  const int begin = offsets[n_lo], end = offsets[n_hi + 1 > 256 ? 256 : n_hi + 1];
+  for (int k = begin + blockIdx.x * G + g; k < end; k += gridDim.x * G) {
+    const int64_t ev = order[k];
+    event_shapes_group<MAXJ, L>(P, E, ev, E.n_partons[ev], s_ev[g], sub, gm);
+    __syncwarp(gm);  // the group's arrays are free for its next event
+  }
+}
+
+// Events of up to kThreadMax partons take one thread each in batches of at
+// least GAPS_SHAPES_GROUP_BELOW events (throughput), groups of
+// GAPS_SHAPES_SMALL_LANES lanes in smaller ones (a launch then waits for its
+// slowest event, not for the SMs).
+constexpr int kThreadMax = 8;
+#ifndef GAPS_SHAPES_GROUP_BELOW
+#define GAPS_SHAPES_GROUP_BELOW 0
+#endif
+#ifndef GAPS_SHAPES_SMALL_LANES
+#define GAPS_SHAPES_SMALL_LANES 4
+#endif
+constexpr int kSmallLanes = GAPS_SHAPES_SMALL_LANES;
+
 }  // namespace
 
 cudaError_t preload_observables() {
@@ -427,11 +836,13 @@ cudaError_t preload_observables() {
   cudaError_t e = cudaFuncGetAttributes(&a, k_bucket_count);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scan);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scatter);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<16>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<32>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<64>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<128>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<256>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<kThreadMax>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<kThreadMax, kSmallLanes, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<16, 8, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<32, 32, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<64, 32, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<128, 32, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<256, 32, 64>);
   return e;
 }
 
@@ -453,15 +864,22 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
   k_bucket_scan<<<1, 256, 0, s>>>(counts, offsets, cursor);
   k_bucket_scatter<<<grid_count, 256, 0, s>>>(E, cursor, order);
   // One launch per multiplicity class; grids cover the largest possible
-  // class and stride over the actual one.
-  const int64_t all = (E.n + kShapeThreads - 1) / kShapeThreads;
-  const unsigned big = static_cast<unsigned>(all < 16 * sms ? all : 16 * sms);
-  const unsigned small = static_cast<unsigned>(all < 2 * sms ? all : 2 * sms);
-  k_event_shapes<16><<<big, kShapeThreads, 0, s>>>(P, E, order, offsets, 0, 16);
-  if (E.cap > 16) k_event_shapes<32><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 17, 32);
-  if (E.cap > 32) k_event_shapes<64><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 33, 64);
-  if (E.cap > 64) k_event_shapes<128><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 65, 128);
-  if (E.cap > 128) k_event_shapes<256><<<small, kShapeThreads, 0, s>>>(P, E, order, offsets, 129, 255);
+  // class (blocks of one event per thread or per group) and stride over the
+  // actual one.
+  auto grid = [&](int per_block, int per_sm) {
+    const int64_t want = (E.n + per_block - 1) / per_block;
+    return static_cast<unsigned>(want < static_cast<int64_t>(per_sm) * sms ? want : static_cast<int64_t>(per_sm) * sms);
+  };
+  if (E.n < GAPS_SHAPES_GROUP_BELOW)
+    k_event_shapes_group<kThreadMax, kSmallLanes, 128>
+        <<<grid(128 / kSmallLanes, 8), 128, 0, s>>>(P, E, order, offsets, 0, kThreadMax);
+  else
+    k_event_shapes<kThreadMax><<<grid(kShapeThreads, 16), kShapeThreads, 0, s>>>(P, E, order, offsets, 0, kThreadMax);
+  if (E.cap > 8) k_event_shapes_group<16, 8, 128><<<grid(16, 8), 128, 0, s>>>(P, E, order, offsets, 9, 16);
+  if (E.cap > 16) k_event_shapes_group<32, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 17, 32);
+  if (E.cap > 32) k_event_shapes_group<64, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 33, 64);
+  if (E.cap > 64) k_event_shapes_group<128, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 65, 128);
+  if (E.cap > 128) k_event_shapes_group<256, 32, 64><<<grid(2, 2), 64, 0, s>>>(P, E, order, offsets, 129, 255);
   return cudaGetLastError();
 }
 

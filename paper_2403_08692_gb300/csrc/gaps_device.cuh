@@ -43,6 +43,10 @@ struct DevParams {
   uint32_t rk[20];
   int nf, fixed, max_steps;
   int trial_mode;  // GAPS_TRIALS_PER_KERNEL or GAPS_TRIALS_PER_DIPOLE
+  // Set on a pool launch whose live jobs all have these parameters apart
+  // from their seeds (and first events): the kernels then read only each
+  // job's Philox key and event-id offset from the job table.
+  int shared_physics;
   double ln_tc;                       // ln t_C
   double ln_s;                        // ln s, the starting scale of the evolution variable
   double inv_4tc;                     // 1 / (4 t_C)
@@ -192,21 +196,33 @@ __device__ __forceinline__ const DevParams& job_params(const DevParams& launch, 
 }
 
 // Compile-time policy of the shower kernels: a single job with one trial per
-// (dipole, kernel), a single job with one trial per dipole, or a multi-job
-// batch (parameters and trial mode read per event).  Single-job kernels then
-// carry no code of the mode they do not run.
-enum : int { kModeSingleKernel = 0, kModeSingleDipole = 1, kModeMulti = 2 };
+// (dipole, kernel), a single job with one trial per dipole, a multi-job
+// batch (parameters and trial mode read per event), or a multi-job batch
+// whose jobs share their parameters apart from the seed (keyed: the physics
+// from the launch, each event's Philox key and id offset from its job, with
+// one trial per kernel or per dipole).  Single-job kernels then carry no
+// code of the mode they do not run.
+enum : int { kModeSingleKernel = 0, kModeSingleDipole = 1, kModeMulti = 2, kModeKeyed = 3, kModeKeyedDipole = 4 };
+// Physics parameters from the job table (else from the launch).
+template <int kMode>
+constexpr bool kJobPhysics = kMode == kModeMulti;
+// Philox key and event-id offset from the job table (else from the launch).
+template <int kMode>
+constexpr bool kJobKey = kMode >= kModeMulti;
 template <int kMode>
 __device__ __forceinline__ bool per_dipole(const DevParams& P) {
   if constexpr (kMode == kModeMulti) {
     return P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
   } else {
-    return kMode == kModeSingleDipole;
+    return kMode == kModeSingleDipole || kMode == kModeKeyedDipole;
   }
 }
 // The mode of a launch.
 inline int launch_mode(const DevParams& P, const Events& E) {
-  return E.jobs ? kModeMulti : (P.trial_mode == GAPS_TRIALS_PER_DIPOLE ? kModeSingleDipole : kModeSingleKernel);
+  const bool dipole = P.trial_mode == GAPS_TRIALS_PER_DIPOLE;
+  if (!E.jobs) return dipole ? kModeSingleDipole : kModeSingleKernel;
+  if (!P.shared_physics) return kModeMulti;
+  return dipole ? kModeKeyedDipole : kModeKeyed;
 }
 
 // The same choice at run time, for kernels that read the parameters once per
@@ -264,15 +280,35 @@ __device__ __forceinline__ U4 philox10_seed(uint32_t c0, uint32_t c1, uint32_t c
   return U4{c0, c1, c2, c3};
 }
 
-// A draw of event-keyed counter (c0..c3) with a launch's parameters: round
-// keys from the parameter bank (single-job launches), or from the seed for
-// parameters read from the job table (kMulti).
-template <bool kMulti>
-__device__ __forceinline__ U4 philox_draw(const DevParams& P, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
-  if constexpr (kMulti) {
-    return philox10_seed(c0, c1, c2, c3, P.seed_lo, P.seed_hi);
+// An event's random stream: its Philox event id (the first counter word)
+// and key.  Single-job kernels take the round keys from the launch (P.rk)
+// and leave k0, k1 unused.
+struct EventKey {
+  uint32_t id, k0, k1;
+};
+
+// The stream of view event ev of job `job` (the job is read only in the
+// job-keyed modes; P: the event's physics parameters).
+template <int kMode>
+__device__ __forceinline__ EventKey event_key(const DevParams& P, const Events& E, int64_t ev, int job) {
+  if constexpr (kMode == kModeKeyed || kMode == kModeKeyedDipole) {
+    const DevParams& K = E.jobs[job];
+    return EventKey{static_cast<uint32_t>(E.base + ev + K.id_offset), K.seed_lo, K.seed_hi};
   } else {
-    return philox10(c0, c1, c2, c3, P.rk);
+    return EventKey{static_cast<uint32_t>(E.base + ev + P.id_offset), P.seed_lo, P.seed_hi};
+  }
+}
+
+// A draw of counter (event id, c1, c2, c3): round keys from the parameter
+// bank (single-job launches), or formed from the seed for keys read from the
+// job table.
+template <int kMode>
+__device__ __forceinline__ U4 philox_draw(const DevParams& P, const EventKey& key, uint32_t c1, uint32_t c2,
+                                          uint32_t c3) {
+  if constexpr (kJobKey<kMode>) {
+    return philox10_seed(key.id, c1, c2, c3, key.k0, key.k1);
+  } else {
+    return philox10(key.id, c1, c2, c3, P.rk);
   }
 }
 

@@ -9,7 +9,8 @@
 //      place and its events join the live active list;
 //   2. one round: every live event of every job runs up to cycles_per_round
 //      more veto cycles (one persistent launch of the time-sliced form, or
-//      that many plain-form steps);
+//      that many plain-form steps), in the keyed form when every live job has
+//      the same parameters apart from its seed;
 //   3. progress, read one round behind from pinned host memory (the live
 //      count and every job's finished-event count), so the GPU always has the
 //      next round queued while the host looks at the last one;
@@ -151,14 +152,34 @@ int admit(gaps_server* s) {
   return GAPS_OK;
 }
 
+// Whether two jobs shower with the same physics (every parameter but the
+// seed).
+bool same_physics(const gaps_params& a, const gaps_params& b) {
+  return a.sqrt_s == b.sqrt_s && a.alphas_mz == b.alphas_mz && a.t_cutoff == b.t_cutoff &&
+         a.n_flavours == b.n_flavours && a.fixed_alphas == b.fixed_alphas && a.max_steps == b.max_steps &&
+         a.trial_mode == b.trial_mode;
+}
+
+// The live jobs' common parameters, if they share their physics (the pool
+// kernels then read only each job's key), else NULL.
+const gaps_params* shared_physics(const gaps_server* s) {
+  if (s->live.empty()) return nullptr;
+  const gaps_params& first = s->live.begin()->second.job.params;
+  for (const auto& kv : s->live)
+    if (!same_physics(kv.second.job.params, first)) return nullptr;
+  return &first;
+}
+
 int launch_round(gaps_server* s) {
   const int64_t bound = std::min(s->bound, s->pool.n_events);
+  const gaps_params* shared = shared_physics(s);
   int rc;
   if (s->mode == GAPS_SERVE_SLICE) {
-    rc = gaps_pool_slice(&s->pool, s->cycle, s->cycles_per_round, bound, s->has_cfg ? &s->cfg : nullptr, s->stream);
+    rc = gaps_pool_slice(&s->pool, s->cycle, s->cycles_per_round, bound, s->has_cfg ? &s->cfg : nullptr, shared,
+                         s->stream);
     s->cycle += 1;  // slices number the rotation of the pool's lists
   } else {
-    rc = gaps_pool_cycles(&s->pool, s->cycle, s->cycles_per_round, bound, s->stream);
+    rc = gaps_pool_cycles(&s->pool, s->cycle, s->cycles_per_round, bound, shared, s->stream);
     s->cycle += s->cycles_per_round;
   }
   if (rc != GAPS_OK) return rc;

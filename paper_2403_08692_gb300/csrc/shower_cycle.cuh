@@ -164,7 +164,7 @@ __device__ __forceinline__ int choose_kernel(const DevParams& P, double zp, doub
 // in loop order on ties; code = (2 i + side) * 8 + kappa orders the trials
 // as the loop does); returns whether one was found.
 template <int kMode>
-__device__ inline bool select_winner_fp64_range(const DevParams& P, const Events& E, int64_t ev, uint32_t id,
+__device__ inline bool select_winner_fp64_range(const DevParams& P, const Events& E, int64_t ev, const EventKey& key,
                                                 int step, int n, double lnt, int first, int stride, EmitTask& w,
                                                 double& best, int& code) {
   bool found = false;
@@ -179,8 +179,8 @@ __device__ inline bool select_winner_fp64_range(const DevParams& P, const Events
       const DipoleEntry d = make_dipole(P, 2.0 * mdot(pi, load_p(E, k, ev)));
       if (d.screen.x < 0.0f) continue;
       for (int kp = 0; kp < nk; kp += 2) {
-        const U4 r = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step),
-                                                      static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
+        const U4 r = philox_draw<kMode>(P, key, static_cast<uint32_t>(step),
+                                        static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
         for (int h = 0; h < 2 && kp + h < nk; ++h) {
           const int kappa = kp + h;
           const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
@@ -211,11 +211,11 @@ __device__ inline bool select_winner_fp64_range(const DevParams& P, const Events
 // The serial form: every parton in one thread.  Returns false if no trial
 // is above t_C.
 template <int kMode>
-__device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
-                                   double lnt, EmitTask& w) {
+__device__ inline bool select_winner_fp64(const DevParams& P, const Events& E, int64_t ev, const EventKey& key, int step,
+                                   int n, double lnt, EmitTask& w) {
   double best = P.ln_tc;
   int code = 0;
-  return select_winner_fp64_range<kMode>(P, E, ev, id, step, n, lnt, 0, 1, w, best, code);
+  return select_winner_fp64_range<kMode>(P, E, ev, key, step, n, lnt, 0, 1, w, best, code);
 }
 
 // Exact FP64 acceptance ratio of Eq. (A.9) with the (1 - y) factor, for a
@@ -298,8 +298,8 @@ __device__ __forceinline__ PartonScreen load_parton_screen(const Events& E, int6
 // The loads of the next parton are issued before the trials of the current
 // one are generated, so their latency hides behind the Philox rounds.
 template <int kMode>
-__device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step,
-                                               int n, int first, int stride, Screen& sc,
+__device__ __forceinline__ void screen_partons(const DevParams& P, const Events& E, int64_t ev, const EventKey& key,
+                                               int step, int n, int first, int stride, Screen& sc,
                                                const PartonScreen* first_loaded = nullptr) {
   screen_none(sc);
   if (first >= n) return;
@@ -320,8 +320,8 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
       // per-dipole trial of a gluon: 1/c of all its kernels (a few ulp)
       const float inv_sum = combined ? 1.0f / (static_cast<float>(kCA) / d.x + static_cast<float>(P.nf) / d.y) : 0.0f;
       for (int kp = 0; kp < nk; kp += 2) {
-        const U4 r = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step),
-                                                      static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
+        const U4 r = philox_draw<kMode>(P, key, static_cast<uint32_t>(step),
+                                        static_cast<uint32_t>((2 * i + side) * 4 + kp / 2), kDrawTrial);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int kappa = kp + h;
@@ -450,23 +450,28 @@ __device__ inline int cycle_screen(const DevParams& P, const Events& E, int64_t 
 // whole launch or pool would otherwise wait for.  Sets have / task on the
 // needing lanes.  Every lane of the warp must call it.
 template <int kMode>
-__device__ __noinline__ void fallback_warp(const DevParams& P0, const Events& E, bool need, int64_t ev, uint32_t id,
-                                           int step, int n, double lnt, bool& have, EmitTask& task) {
+__device__ __noinline__ void fallback_warp(const DevParams& P0, const Events& E, bool need, int64_t ev, int job,
+                                           const EventKey& key, int step, int n, double lnt, bool& have,
+                                           EmitTask& task) {
   const int lane = static_cast<int>(threadIdx.x & 31);
   unsigned pending = __ballot_sync(0xffffffffu, need);
   while (pending) {
     const int src = __ffs(pending) - 1;
     pending &= pending - 1;
     const long long sev = __shfl_sync(0xffffffffu, static_cast<long long>(ev), src);
-    const uint32_t sid = __shfl_sync(0xffffffffu, id, src);
+    EventKey skey;
+    skey.id = __shfl_sync(0xffffffffu, key.id, src);
+    skey.k0 = kJobKey<kMode> ? __shfl_sync(0xffffffffu, key.k0, src) : 0u;
+    skey.k1 = kJobKey<kMode> ? __shfl_sync(0xffffffffu, key.k1, src) : 0u;
+    const int sjob = kJobPhysics<kMode> ? __shfl_sync(0xffffffffu, job, src) : 0;
     const int sstep = __shfl_sync(0xffffffffu, step, src);
     const int sn = __shfl_sync(0xffffffffu, n, src);
     const double slnt = __shfl_sync(0xffffffffu, lnt, src);
-    const DevParams& P = params_of<kMode == kModeMulti>(P0, E, sev);
+    const DevParams& P = job_params<kJobPhysics<kMode>>(P0, E, sjob);
     EmitTask w;
     double best = P.ln_tc;
     int code = 0x7fffffff;
-    const bool found = select_winner_fp64_range<kMode>(P, E, sev, sid, sstep, sn, slnt, lane, 32, w, best, code);
+    const bool found = select_winner_fp64_range<kMode>(P, E, sev, skey, sstep, sn, slnt, lane, 32, w, best, code);
     // the highest scale; equal scales go to the smallest code
     double wb = best;
     int wc = code;
@@ -512,8 +517,8 @@ __device__ __noinline__ void fallback_warp(const DevParams& P0, const Events& E,
 // written), kCycleAccepted with `task` filled when an emission must be
 // generated, kCycleVetoed otherwise.
 template <int kMode>
-__device__ inline int cycle_conclude(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
-                                     bool have, EmitTask& task) {
+__device__ inline int cycle_conclude(const DevParams& P, const Events& E, int64_t ev, const EventKey& key, int step,
+                                     int n, bool have, EmitTask& task) {
   // ---- CheckCutoff.
   if (!have) {
     finish_event(E, ev, GAPS_DONE, P.tc);
@@ -523,14 +528,14 @@ __device__ inline int cycle_conclude(const DevParams& P, const Events& E, int64_
   E.n_winners[ev] += 1;
   if (task.kind == kKindUnchosen) {
     // per-dipole trial of a gluon: its kernel from the winner's second draw
-    const U4 rk = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step), 1u, kDrawWinner);
+    const U4 rk = philox_draw<kMode>(P, key, static_cast<uint32_t>(step), 1u, kDrawWinner);
     const int kappa = choose_kernel(P, task.zp, task.inv_ls, to_unit(rk.z, rk.w));
     task.kappa = static_cast<uint8_t>(kappa);
     task.kind = static_cast<uint8_t>(kappa == 0 ? kGtoGG : kGtoQQ);
   }
 
   // ---- AcceptOrVeto: FP32 screen of Eq. (A.8)-(A.9), FP64 near the edge.
-  const U4 rw = philox_draw<kMode == kModeMulti>(P, id, static_cast<uint32_t>(step), 0u, kDrawWinner);
+  const U4 rw = philox_draw<kMode>(P, key, static_cast<uint32_t>(step), 0u, kDrawWinner);
   bool accept;
   {
     const float zpf = f32_from_f64(task.zp);
@@ -589,23 +594,24 @@ __device__ inline int cycle_conclude(const DevParams& P, const Events& E, int64_
 
 // The whole decision of a cycle in one thread, the exact selection serial.
 template <int kMode>
-__device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, uint32_t id, int step, int n,
-                                   double lnt, const Screen& sc, EmitTask& task) {
+__device__ inline int cycle_decide(const DevParams& P, const Events& E, int64_t ev, const EventKey& key, int step,
+                                   int n, double lnt, const Screen& sc, EmitTask& task) {
   const int s = cycle_screen<kMode>(P, E, ev, step, lnt, sc, task);
   bool have = s == kScreenWinner;
   if (s == kScreenUndecided) {
     atomicAdd(&E.counters[2], 1ull);  // screen undecided: full FP64 cycle
-    have = select_winner_fp64<kMode>(P, E, ev, id, step, n, lnt, task);
+    have = select_winner_fp64<kMode>(P, E, ev, key, step, n, lnt, task);
   }
-  return cycle_conclude<kMode>(P, E, ev, id, step, n, have, task);
+  return cycle_conclude<kMode>(P, E, ev, key, step, n, have, task);
 }
 
 // Phase 1 of a cycle for active event ev, one thread: SelectWinnerEmission
 // (the FP32 screen over every trial), then cycle_decide.
 template <int kMode>
 __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, int64_t ev, EmitTask& task) {
-  const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
-  const uint32_t id = event_id(P, E, ev);
+  const int job = kJobKey<kMode> ? static_cast<int>(E.job_of[ev]) : 0;
+  const DevParams& P = job_params<kJobPhysics<kMode>>(P0, E, job);
+  const EventKey key = event_key<kMode>(P, E, ev, job);
   const int n = E.n_partons[ev];
   const int step = E.n_steps[ev];
   const double lnt = E.lnt[ev];
@@ -614,8 +620,8 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
     return kCycleFinished;
   }
   Screen sc;
-  screen_partons<kMode>(P, E, ev, id, step, n, 0, 1, sc);
-  return cycle_decide<kMode>(P, E, ev, id, step, n, lnt, sc, task);
+  screen_partons<kMode>(P, E, ev, key, step, n, 0, 1, sc);
+  return cycle_decide<kMode>(P, E, ev, key, step, n, lnt, sc, task);
 }
 
 // Phase 2: GenerateEmission -- azimuth, the final-final dipole map, colours
@@ -623,16 +629,17 @@ __device__ inline int cycle_select_veto(const DevParams& P0, const Events& E, in
 // appended to the block's refresh list (jobs, *n_jobs) under task_index; the
 // caller recomputes them with refresh_dipole after a block barrier, spread
 // over all of its threads, so that this FP64-heavy step runs in full warps.
-template <bool kMulti>
+template <int kMode>
 __device__ inline void cycle_emit(const DevParams& P0, const Events& E, const EmitTask& w, int task_index,
                                   uint32_t* jobs, int* n_jobs) {
   const int64_t ev = w.ev;
-  const DevParams& P = params_of<kMulti>(P0, E, ev);
-  const uint32_t id = event_id(P, E, ev);
+  const int job = kJobKey<kMode> ? static_cast<int>(E.job_of[ev]) : 0;
+  const DevParams& P = job_params<kJobPhysics<kMode>>(P0, E, job);
+  const EventKey key = event_key<kMode>(P, E, ev, job);
   const double t = exp(w.lnt);
   const double z = z_fp64(w.kind, w.zp, 1.0 / w.inv_ls, to_unit(w.rz_hi, w.rz_lo));
   const double y = t / (w.q2 * z * (1.0 - z));
-  const U4 rphi = philox_draw<kMulti>(P, id, static_cast<uint32_t>(w.step), 1u, kDrawWinner);
+  const U4 rphi = philox_draw<kMode>(P, key, static_cast<uint32_t>(w.step), 1u, kDrawWinner);
   double sphi, cphi;
   sincospi(2.0 * to_unit(rphi.x, rphi.y), &sphi, &cphi);
   const V4 a = load_p(E, w.i, ev);

@@ -174,18 +174,20 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
       screen_none(sc);
       int n = 0, step = 0;
       bool limited = false;
+      int job = 0;
       if (live) {
-        const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
+        if (kJobKey<kMode>) job = E.job_of[ev];
+        const DevParams& P = job_params<kJobPhysics<kMode>>(P0, E, job);
         n = E.n_partons[ev];
         step = E.n_steps[ev];
         limited = step >= P.max_steps;
-        if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, lanes, sc);
+        if (!limited) screen_partons<kMode>(P, E, ev, event_key<kMode>(P, E, ev, job), step, n, sub, lanes, sc);
       }
       screen_group_reduce_n(sc, lanes);  // every lane of the block, one call site
       bool finished = false;
       if (live && sub == 0) {
         if constexpr (kSlice) s_cyc[slot] = static_cast<uint8_t>(s_cyc[slot] + 1);
-        const DevParams& P = params_of<kMode == kModeMulti>(P0, E, ev);
+        const DevParams& P = job_params<kJobPhysics<kMode>>(P0, E, job);
         EmitTask task;
         int r = kCycleFinished;
         if (limited) {
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
           // the rare undecided cycle takes its exact selection serially here:
           // the warp-wide form (fallback_warp) measured slower in this kernel
           // (its spills cost more than the waits it saves)
-          r = cycle_decide<kMode>(P, E, ev, event_id(P, E, ev), step, n, E.lnt[ev], sc, task);
+          r = cycle_decide<kMode>(P, E, ev, event_key<kMode>(P, E, ev, job), step, n, E.lnt[ev], sc, task);
         }
         if (r == kCycleAccepted) {
           task.pad0 = static_cast<uint8_t>(slot & 255);  // pool slot, to release it after the emission
@@ -215,9 +217,9 @@ __global__ void __launch_bounds__(T, persist_min_blocks(T))
     // before the pool is compacted (at most one per event: queued <= kPool).
     const int queued = s_count[1];
     if (queued > 0) {
-      for (int q = tid; q < queued; q += T) cycle_emit<kMode == kModeMulti>(P0, E, s_task[q], q, s_jobs, &s_count[4]);
+      for (int q = tid; q < queued; q += T) cycle_emit<kMode>(P0, E, s_task[q], q, s_jobs, &s_count[4]);
       __syncthreads();
-      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
+      for (int j = tid; j < s_count[4]; j += T) refresh_dipole<kJobPhysics<kMode>>(P0, E, s_task, s_jobs[j]);
       for (int q = tid; q < queued; q += T) s_alive[s_task[q].pad0 | (s_task[q].pad1 << 8)] = kSlotLive;
       __syncthreads();
     }
@@ -308,6 +310,12 @@ template <bool kSlice>
 cudaError_t launch_shape(const DevParams& P, const Events& E, const gaps_persistent_config& cfg, const SliceArgs& sl,
                          cudaStream_t s) {
   switch (launch_mode(P, E)) {
+    case kModeKeyed:
+      if constexpr (kSlice) return launch_shape_m<kModeKeyed, kSlice>(P, E, cfg, sl, s);
+      return launch_shape_m<kModeMulti, kSlice>(P, E, cfg, sl, s);  // the job table holds the same parameters
+    case kModeKeyedDipole:
+      if constexpr (kSlice) return launch_shape_m<kModeKeyedDipole, kSlice>(P, E, cfg, sl, s);
+      return launch_shape_m<kModeMulti, kSlice>(P, E, cfg, sl, s);
     case kModeMulti: return launch_shape_m<kModeMulti, kSlice>(P, E, cfg, sl, s);
     case kModeSingleDipole: return launch_shape_m<kModeSingleDipole, kSlice>(P, E, cfg, sl, s);
     default: return launch_shape_m<kModeSingleKernel, kSlice>(P, E, cfg, sl, s);

@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     }
   }
   __syncthreads();
-  if (tid < s_naccept) cycle_emit<kMode == kModeMulti>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
+  if (tid < s_naccept) cycle_emit<kMode>(P, E, s_task[tid], tid, s_jobs, &s_njobs);
   __syncthreads();
-  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMode == kModeMulti>(P, E, s_task, s_jobs[j]);
+  for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kJobPhysics<kMode>>(P, E, s_task, s_jobs[j]);
 }
 
 // Slot of this thread's item in an output list shared by the grid: one
@@ -201,14 +201,14 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     // are loaded together, not one after another: every listed event has
     // slot 0.
     // A multi-job batch's job index is loaded with them.
-    constexpr bool kMulti = kMode == kModeMulti;
+    constexpr bool kMulti = kJobPhysics<kMode>;
     int status = -1, n = 0, step = 0, job = 0;
     PartonScreen first{};
     if (ev >= 0) {
       status = E.status[ev];
       n = E.n_partons[ev];
       step = E.n_steps[ev];
-      if (kMulti) job = E.job_of[ev];
+      if (kJobKey<kMode>) job = E.job_of[ev];
       if (L == 1) first = load_parton_screen(E, ev, 0);
     }
     const bool active = status == GAPS_ACTIVE;
@@ -218,7 +218,8 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     if (active) {
       const DevParams& P = job_params<kMulti>(P0, E, job);
       limited = step >= P.max_steps;
-      if (!limited) screen_partons<kMode>(P, E, ev, event_id(P, E, ev), step, n, sub, L, sc, L == 1 ? &first : nullptr);
+      if (!limited)
+        screen_partons<kMode>(P, E, ev, event_key<kMode>(P, E, ev, job), step, n, sub, L, sc, L == 1 ? &first : nullptr);
     } else {
       n = step = 0;
     }
@@ -230,23 +231,23 @@ __device__ __forceinline__ void select_role(const DevParams& P0, const Events& E
     // selection from the whole warp.
     int verdict = kScreenNone;
     double lnt = 0.0;
-    uint32_t id = 0;
+    EventKey key{0u, 0u, 0u};
     if (lead && !limited) {
       const DevParams& P = job_params<kMulti>(P0, E, job);
       lnt = E.lnt[ev];
-      id = event_id(P, E, ev);
+      key = event_key<kMode>(P, E, ev, job);
       verdict = cycle_screen<kMode>(P, E, ev, step, lnt, sc, task);
       if (verdict == kScreenUndecided) atomicAdd(&E.counters[2], 1ull);  // full FP64 cycle
     }
     bool have = verdict == kScreenWinner;
     if (__any_sync(0xffffffffu, verdict == kScreenUndecided))
-      fallback_warp<kMode>(P0, E, verdict == kScreenUndecided, ev, id, step, n, lnt, have, task);
+      fallback_warp<kMode>(P0, E, verdict == kScreenUndecided, ev, job, key, step, n, lnt, have, task);
     if (lead) {
       const DevParams& P = job_params<kMulti>(P0, E, job);
       if (limited) {
         finish_event(E, ev, GAPS_STEP_LIMIT, exp(E.lnt[ev]));
       } else {
-        r = cycle_conclude<kMode>(P, E, ev, id, step, n, have, task);
+        r = cycle_conclude<kMode>(P, E, ev, key, step, n, have, task);
       }
       if (r == kCycleFinished) {
         atomicAdd(&E.counters[0], 1ull);
@@ -320,9 +321,9 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
     const bool has = k < len;
     if (has) s_task[tid] = tasks_in[k];
     __syncthreads();
-    if (has) cycle_emit<kMode == kModeMulti>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
+    if (has) cycle_emit<kMode>(P0, E, s_task[tid], tid, s_jobs, &s_njobs);
     __syncthreads();
-    for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kMode == kModeMulti>(P0, E, s_task, s_jobs[j]);
+    for (int j = tid; j < s_njobs; j += kStepThreads) refresh_dipole<kJobPhysics<kMode>>(P0, E, s_task, s_jobs[j]);
     if (has) E.status[s_task[tid].ev] = GAPS_ACTIVE;
     const int64_t at_list = warp_append_slot(has, list_count);
     if (at_list >= 0) list_out[at_list] = s_task[tid].ev;
@@ -377,6 +378,8 @@ cudaError_t launch_step_plain(const DevParams& P, const Events& E, const int* li
   const unsigned blocks = static_cast<unsigned>((n_in + kStepThreads - 1) / kStepThreads);
   switch (launch_mode(P, E)) {
     case kModeMulti:
+    case kModeKeyed:
+    case kModeKeyedDipole:  // the job table holds the same parameters
       k_step_plain<kModeMulti>
           <<<blocks, kStepThreads, 0, s>>>(P, E, list_in, n_in, n_in_dev, list_out, out_count, reset_count);
       break;
@@ -449,6 +452,12 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
   switch (launch_mode(P, E)) {
     case kModeMulti:
       GAPS_DEFERRED_SWITCH(kModeMulti)
+      break;
+    case kModeKeyed:
+      GAPS_DEFERRED_SWITCH(kModeKeyed)
+      break;
+    case kModeKeyedDipole:
+      GAPS_DEFERRED_SWITCH(kModeKeyedDipole)
       break;
     case kModeSingleDipole:
       GAPS_DEFERRED_SWITCH(kModeSingleDipole)

@@ -109,8 +109,9 @@ SIGNATURES = {
     "gaps_pool_reset": (C.c_int, [_P(Batch), C.c_void_p]),
     "gaps_pool_admit": (C.c_int, [_P(Params), C.c_int32, C.c_int64, C.c_int64, C.c_uint32, _P(Batch), C.c_int64,
                                   C.c_void_p]),
-    "gaps_pool_cycles": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, C.c_void_p]),
-    "gaps_pool_slice": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(PersistentConfig), C.c_void_p]),
+    "gaps_pool_cycles": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(Params), C.c_void_p]),
+    "gaps_pool_slice": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(PersistentConfig), _P(Params),
+                                  C.c_void_p]),
     "gaps_pool_progress": (C.c_int, [_P(Batch), C.c_int64, _P(C.c_int64), C.c_void_p, C.c_void_p]),
     "gaps_pool_finish": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_server_create": (C.c_int, [_P(Batch), C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(PersistentConfig),
@@ -422,18 +423,29 @@ def pool_admit(p, job_slot, ev_begin, n_events, first_event, ws, cycle, stream=N
                                   C.byref(_batch(ws)), int(cycle), _stream_handle(stream)), "gaps_pool_admit")
 
 
-def pool_cycles(ws, first_cycle, n_cycles, max_active, stream=None):
+def pool_cycles(ws, first_cycle, n_cycles, max_active, shared=None, stream=None):
+    """gaps_pool_cycles.  shared: Params every live job has apart from its
+    seed (the keyed kernels), or None."""
     _check(load().gaps_pool_cycles(C.byref(_batch(ws)), int(first_cycle), int(n_cycles), int(max_active),
-                                   _stream_handle(stream)), "gaps_pool_cycles")
+                                   _pp(shared), _stream_handle(stream)), "gaps_pool_cycles")
 
 
-def pool_slice(ws, round_index, cycles, max_active, cfg=None, stream=None):
+def pool_slice(ws, round_index, cycles, max_active, cfg=None, shared=None, stream=None):
     """gaps_pool_slice: every live event runs up to `cycles` more cycles in one
-    persistent launch.  cfg: PersistentConfig, a dict of its fields, or None."""
+    persistent launch.  cfg: PersistentConfig, a dict of its fields, or None;
+    shared as for pool_cycles."""
     cfg = persistent_config(cfg)
     ptr = C.byref(cfg) if cfg is not None else None
     _check(load().gaps_pool_slice(C.byref(_batch(ws)), int(round_index), int(cycles), int(max_active), ptr,
-                                  _stream_handle(stream)), "gaps_pool_slice")
+                                  _pp(shared), _stream_handle(stream)), "gaps_pool_slice")
+
+
+PHYSICS_FIELDS = ("sqrt_s", "alphas_mz", "t_cutoff", "n_flavours", "fixed_alphas", "max_steps", "trial_mode")
+
+
+def same_physics(a, b):
+    """Whether two Params differ at most in their seed."""
+    return all(getattr(a, f) == getattr(b, f) for f in PHYSICS_FIELDS)
 
 
 def pool_progress(ws, cycle, job_done=None, stream=None):
@@ -465,6 +477,7 @@ class CServer:
         self.ws = Workspace(pool_events, capacity)
         self.hist = torch.zeros((max_jobs, HIST_DOUBLES), dtype=torch.float64, device="cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream.wait_stream(torch.cuda.current_stream())  # the buffers' fills come first
         cfg = persistent_config(cfg)
         self._batch = _batch(self.ws)
         h = C.c_void_p()
@@ -540,6 +553,10 @@ class Workspace:
             raise ValueError("batch sizes out of range")
         # 256 extra bytes so the base can be aligned to 256
         self._raw = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device)
+        if self._raw.is_cuda:
+            # The fill ran on the current stream; library calls may come on
+            # any stream, so it must be complete before the first of them.
+            torch.cuda.current_stream(self._raw.device).synchronize()
         off = (-self._raw.data_ptr()) % 256
         self.buffer = self._raw[off:off + nbytes]
         self.layout = _workspace_layout(self.n_events, self.capacity)  # byte offsets of every array

@@ -120,7 +120,7 @@ class Server:
     stand-in and device "cpu")."""
 
     def __init__(self, pool_events=None, capacity=128, memory_budget=None, cycles_per_round=8, clock="wall",
-                 device="cuda", mode="slice", cfg=None, device_layer=None, layout=0):
+                 device="cuda", mode="slice", cfg=None, device_layer=None, layout=0, keyed=True):
         if device_layer is None:
             import torch
             device_layer = (gaps, torch)
@@ -141,11 +141,15 @@ class Server:
         self.clock = clock
         self.mode = mode
         self.cfg = cfg
+        self.keyed = keyed
         pin = (lambda t: t) if device == "cpu" else (lambda t: t.pin_memory())
         self.ws = G.Workspace(self.pool_events, self.capacity, device=device, layout=layout)
         self.stream = torch.cuda.Stream(device=device)
         self.hist = torch.zeros((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64, device=device)
         self.hist_host = pin(torch.empty((G.MAX_JOBS, G.HIST_DOUBLES), dtype=torch.float64))
+        # the buffers were filled on the current stream: the server's stream
+        # starts after those fills
+        self.stream.wait_stream(torch.cuda.current_stream(device))
         self._counters = self.ws.view("counters", torch.int64, (COUNTER_WORDS,))
         self._job_done = self.ws.view("job_done", torch.int64, (G.MAX_JOBS,))
         self._progress_host = [pin(torch.empty(COUNTER_WORDS + G.MAX_JOBS, dtype=torch.int64)) for _ in range(2)]
@@ -186,16 +190,26 @@ class Server:
             self.bound += job.n_events
         self.peak_live_jobs = max(self.peak_live_jobs, len(self.live))
 
+    def _shared_physics(self):
+        """The live jobs' common parameters when they differ only in their
+        seeds (the pool then runs its keyed kernels), else None."""
+        if not self.keyed or not self.live:
+            return None
+        jobs = [job for job, _, _, _ in self.live.values()]
+        first = jobs[0].params
+        return first if all(self._gaps.same_physics(j.params, first) for j in jobs[1:]) else None
+
     def _launch_round(self):
         torch = self._torch
         k = self.cycles_per_round
         bound = min(self.bound, self.pool_events)
+        shared = self._shared_physics()
         if self.mode == "slice":
             # self.cycle counts slices: the rotation index of the pool's lists
-            self._gaps.pool_slice(self.ws, self.cycle, k, bound, self.cfg, stream=self.stream)
+            self._gaps.pool_slice(self.ws, self.cycle, k, bound, self.cfg, shared=shared, stream=self.stream)
             self.cycle += 1
         else:
-            self._gaps.pool_cycles(self.ws, self.cycle, k, bound, stream=self.stream)
+            self._gaps.pool_cycles(self.ws, self.cycle, k, bound, shared=shared, stream=self.stream)
             self.cycle += k
         self.launched_cycles += k
         buf = self._progress_host[self.rounds % 2]

@@ -120,3 +120,32 @@ def test_wall_clock_poisson(g, mode):
     assert srv.alloc.free_events() == srv.pool_events
     s = g.latency_summary(results, max(r.finished for r in results))
     assert s["jobs"] == len(jobs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0.0
+
+
+@pytest.mark.parametrize("trial_mode", [0, 1])
+@pytest.mark.parametrize("mode", ["slice", "steps"])
+def test_keyed_rounds_equal_general_rounds(g, mode, trial_mode):
+    """Jobs that differ only in seed and first event: the pool runs its keyed
+    kernels (physics from the launch, key and id offset per job), and every
+    event and histogram is bitwise the one the general multi-job kernels give
+    and the job gives alone, for both trial modes."""
+    specs = [(21, 9000, 0, 0), (22, 4000, 123456, 0), (23, 1, 0, 1), (24, 7000, 0, 2)]
+
+    def serve(keyed):
+        jobs = [g.ServeJob(g.make_params(seed=s, trial_mode=trial_mode), n, first, float(arr), tag=k)
+                for k, (s, n, first, arr) in enumerate(specs)]
+        srv = g.Server(pool_events=16000, capacity=128, cycles_per_round=5, clock="rounds", mode=mode, keyed=keyed)
+        seen = {}
+        res = srv.serve(jobs, on_finish=lambda job, ws, b, st: seen.__setitem__(job.tag, _capture(ws, b, job.n_events)),
+                        max_rounds=100000)
+        return {r.tag: r.hist for r in res}, seen
+
+    hk, ek = serve(True)
+    hg, eg = serve(False)
+    for k, (s, n, first, arr) in enumerate(specs):
+        _assert_same_events(ek[k], eg[k], k)
+        assert np.array_equal(hk[k], hg[k]), k
+    s, n, first, _ = specs[1]
+    ev_alone, hist_alone = _alone(g, g.make_params(seed=s, trial_mode=trial_mode), n, first, 128)
+    _assert_same_events(ek[1], ev_alone, 1)
+    assert np.array_equal(hk[1], hist_alone)

@@ -28,6 +28,7 @@ class FakePool:
     def __init__(self, stuck=False):
         self.stuck = stuck
         self.finished_jobs = []
+        self.rounds_shared = []
 
     class _Workspace:
         def __init__(self, n, capacity, device="cpu"):
@@ -37,6 +38,7 @@ class FakePool:
             self.remaining = {}   # batch event -> cycles left
             self.owner = {}       # batch event -> job slot
             self.jobs = {}        # slot -> (begin, n, first_event, seed)
+            self.physics = {}     # slot -> the job's physics tag
 
         def view(self, name, dtype, shape):
             return {"counters": self.counters, "job_done": self.job_done}[name]
@@ -63,6 +65,7 @@ class FakePool:
             ws.remaining[e] = _cycles_needed(params.seed, first_event + e - begin)
             ws.owner[e] = slot
         ws.jobs[slot] = (begin, n, first_event, params.seed)
+        ws.physics[slot] = getattr(params, "physics", 0)
         ws.job_done[slot] = 0
 
     def _advance(self, ws, k, next_cycle):
@@ -75,12 +78,26 @@ class FakePool:
         ws.counters[10 + next_cycle % 3] = len(ws.remaining)
         ws.counters[18 + next_cycle % 3] = 0
 
-    def pool_slice(self, ws, cycle, k, bound, cfg, stream=None):
+    @staticmethod
+    def same_physics(a, b):
+        return getattr(a, "physics", 0) == getattr(b, "physics", 0)
+
+    def _check_shared(self, ws, shared):
+        # the keyed form only when every live job has the shared physics
+        live = {ws.owner[e] for e in ws.remaining}
+        phys = {ws.physics[slot] for slot in live}
+        self.rounds_shared.append(shared is not None)
+        if shared is not None:
+            assert phys <= {getattr(shared, "physics", 0)}, "keyed round over jobs of other physics"
+
+    def pool_slice(self, ws, cycle, k, bound, cfg, shared=None, stream=None):
         assert bound >= len(ws.remaining), "the grid bound must cover every live event"
+        self._check_shared(ws, shared)
         self._advance(ws, k, cycle + 1)
 
-    def pool_cycles(self, ws, cycle, k, bound, stream=None):
+    def pool_cycles(self, ws, cycle, k, bound, shared=None, stream=None):
         assert bound >= len(ws.remaining), "the grid bound must cover every live event"
+        self._check_shared(ws, shared)
         self._advance(ws, k, cycle + k)
 
     def pool_finish(self, slot, begin, n, ws, hist, stream=None):
@@ -109,10 +126,14 @@ class _Stream:
     def synchronize(self):
         pass
 
+    def wait_stream(self, other):
+        pass
+
 
 _fake_torch = types.SimpleNamespace(
     zeros=torch.zeros, empty=torch.empty, tensor=torch.tensor, float64=torch.float64, int64=torch.int64,
     cuda=types.SimpleNamespace(Stream=lambda device=None: _Stream(), Event=_Event,
+                               current_stream=lambda device=None: _Stream(),
                                stream=lambda s: contextlib.nullcontext()))
 
 
@@ -179,3 +200,27 @@ def test_memory_budget_sizes_the_pool():
     srv = serving.Server(memory_budget=123_456, capacity=8, clock="rounds", device="cpu",
                          device_layer=(FakePool(), _fake_torch))
     assert srv.pool_events == 123
+
+
+def test_keyed_rounds_only_for_shared_physics():
+    """Rounds run the keyed kernels (shared parameters passed) while every live
+    job has the same physics, and the general ones once a job of other physics
+    is live; the schedule and the results do not change."""
+    rng = np.random.default_rng(3)
+    jobs = _jobs(rng, 12, 40)
+    pool = FakePool()
+    srv = _server(pool, 200)
+    srv.serve(jobs, max_rounds=10000)
+    assert pool.rounds_shared and all(pool.rounds_shared)
+    mixed = _jobs(rng, 12, 40)
+    for i, j in enumerate(mixed):
+        j.params.physics = i % 2
+    pool2 = FakePool()
+    srv2 = _server(pool2, 200)
+    res = srv2.serve(mixed, max_rounds=10000)
+    assert len(res) == len(mixed)
+    assert not all(pool2.rounds_shared)
+    off = _server(FakePool(), 200)
+    off.keyed = False
+    off.serve(_jobs(rng, 4, 40), max_rounds=10000)
+    assert not any(off._gaps.rounds_shared)
