@@ -156,6 +156,8 @@ typedef struct gaps_layout {
   int64_t job_begin;      /* int64 [GAPS_MAX_JOBS + 1]: first batch event of every job */
   int64_t job_of;         /* uint16 [n_events]: job of every event of a multi-job batch */
   int64_t job_done;       /* uint64 [GAPS_MAX_JOBS]: finished events per job slot */
+  int64_t finish;         /* int64 [2][GAPS_MAX_JOBS + 1]: scratch of gaps_pool_finish_jobs (the
+                             position prefix and first event of every range) */
   int64_t total_bytes;
 } gaps_layout;
 
@@ -307,6 +309,19 @@ int gaps_pool_progress(const gaps_batch* pool, int64_t cycle, int64_t* active_ou
  * cleared).  Asynchronous. */
 int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const gaps_batch* pool,
                      double* hist_device, void* stream);
+
+/* Validation, observables and histograms of n_jobs finished jobs at once
+ * (0 <= n_jobs <= GAPS_MAX_JOBS): job i holds pool range [ev_begins[i],
+ * ev_begins[i] + n_events[i]) and job slot job_slots[i]; the ranges are
+ * disjoint and the slots distinct.  The same results as one gaps_pool_finish
+ * per job, in one sequence of launches over all of their events: a launch
+ * lasts as long as its slowest event, so finalising the jobs of a round
+ * together pays that latency once.  Job i's histograms are added to
+ * hist_device + job_slots[i] * GAPS_HIST_DOUBLES (not cleared).  job_slots,
+ * ev_begins and n_events are host arrays, read before the call returns.
+ * Asynchronous. */
+int gaps_pool_finish_jobs(const int32_t* job_slots, const int64_t* ev_begins, const int64_t* n_events,
+                          int32_t n_jobs, const gaps_batch* pool, double* hist_device, void* stream);
 
 /* ------------------------------------------- serving: the C scheduler */
 

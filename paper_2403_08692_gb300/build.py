@@ -21,7 +21,11 @@ LIB = os.path.join(BUILD, "libgaps.so")
 PROBE_LIB = os.path.join(BUILD, "libgaps_probe.so")
 PROBE_DIR = os.path.join(CSRC, "probe")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+# -fmad=false: no multiply-add is fused unless the source asks for it (fma),
+# so an expression rounds the same way in every kernel that inlines it (the
+# shower forms, the pool's job modes and the observables' thread and group
+# forms give bitwise the same events).
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 
 

@@ -76,6 +76,7 @@ void compute_layout(int64_t n, int32_t cap, gaps_layout* L) {
   L->job_begin = take(8 * (GAPS_MAX_JOBS + 1));
   L->job_of = take(2 * n);
   L->job_done = take(8 * GAPS_MAX_JOBS);
+  L->finish = take(8 * 2 * (GAPS_MAX_JOBS + 1));
   L->total_bytes = off;
 }
 
@@ -879,6 +880,54 @@ int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const
   H.jobs = nullptr;
   H.job_of = nullptr;
   if (e == cudaSuccess) e = launch_histograms(P, E.jobs + job_slot, H, hist_device, s);
+  return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
+}
+
+int gaps_pool_finish_jobs(const int32_t* job_slots, const int64_t* ev_begins, const int64_t* n_events,
+                          int32_t n_jobs, const gaps_batch* pool, double* hist_device, void* stream) {
+  DevParams P;
+  Events E;
+  if (prepare(nullptr, pool, &P, &E, true) != GAPS_OK || !hist_device || n_jobs < 0 || n_jobs > GAPS_MAX_JOBS ||
+      (n_jobs > 0 && (!job_slots || !ev_begins || !n_events)))
+    return GAPS_ERR_INVALID;
+  // The position prefix and the first events, checked: slots in range and
+  // distinct, ranges inside the pool and disjoint.
+  std::vector<int64_t> table(2 * (static_cast<size_t>(n_jobs) + 1), 0);
+  int64_t* prefix = table.data();
+  int64_t* begin = prefix + n_jobs + 1;
+  std::vector<std::pair<int64_t, int64_t>> spans;
+  std::vector<char> slot_used(GAPS_MAX_JOBS, 0);
+  for (int j = 0; j < n_jobs; ++j) {
+    const int32_t slot = job_slots[j];
+    const int64_t b = ev_begins[j], n = n_events[j];
+    if (slot < 0 || slot >= GAPS_MAX_JOBS || slot_used[slot] || b < 0 || n < 0 || b + n > pool->n_events)
+      return GAPS_ERR_INVALID;
+    slot_used[slot] = 1;
+    prefix[j + 1] = prefix[j] + n;
+    begin[j] = b;
+    if (n > 0) spans.emplace_back(b, b + n);
+  }
+  std::sort(spans.begin(), spans.end());
+  for (size_t k = 1; k < spans.size(); ++k)
+    if (spans[k].first < spans[k - 1].second) return GAPS_ERR_INVALID;
+  const int64_t total = prefix[n_jobs];
+  if (total == 0) return GAPS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gaps_layout L;
+  compute_layout(pool->n_events, pool->capacity, &L);
+  int64_t* dev = reinterpret_cast<int64_t*>(static_cast<char*>(pool->workspace) + L.finish);
+  // a pageable host-to-device copy returns once the source has been staged
+  cudaError_t e = cudaMemcpyAsync(dev, table.data(), table.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  const Ranges R{dev, dev + n_jobs + 1, n_jobs};
+  Events U = E;  // positions 0 .. total - 1 over the ranges, pool events
+  U.n = total;
+  if (e == cudaSuccess) e = launch_validate(P, U, s, R);
+  if (e == cudaSuccess) e = launch_observables(P, U, E.buckets, E.order, s, R);
+  // every job's histograms in its slot's set, at its own scales
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(E.hist_fixed, 0, static_cast<size_t>(GAPS_MAX_JOBS) * GAPS_HIST_FIXED_WORDS * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_hist_fixed(P, nullptr, U, E.hist_fixed, s, R);
+  if (e == cudaSuccess) e = launch_hist_finalize(P, nullptr, E.jobs, GAPS_MAX_JOBS, nullptr, E.hist_fixed, hist_device, s);
   return e == cudaSuccess ? GAPS_OK : cuda_fail(e);
 }
 

@@ -172,6 +172,30 @@ inline void set_layout(Events& E, int layout, int64_t n_events, int capacity) {
   }
 }
 
+// The events a finalisation kernel visits: positions t = 0 .. E.n - 1 of a
+// view, or of a list of disjoint event ranges (several finished jobs of a
+// serving pool at once): range j holds positions prefix[j] ..
+// prefix[j + 1] - 1, events begin[j] .. begin[j] + prefix[j + 1] - prefix[j]
+// - 1.  n = 0: the identity.
+struct Ranges {
+  const int64_t* prefix;  // [n + 1], prefix[0] = 0
+  const int64_t* begin;   // [n]
+  int n;
+  __device__ __forceinline__ int64_t event(int64_t t) const {
+    if (n == 0) return t;
+    int lo = 0, hi = n - 1;  // the last range whose first position is <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= t) {
+        lo = mid;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    return begin[lo] + (t - prefix[lo]);
+  }
+};
+
 // The parameters of event ev: its job's in a multi-job batch (kMulti), else
 // the launch's.  A compile-time choice, so that single-job kernels read
 // their parameters from the kernel-argument bank.
@@ -371,20 +395,26 @@ __device__ __forceinline__ double kernel_k(int kind) {
 }
 
 // Minkowski product.
+// Products and sums below are fused only where written as fma: the library
+// is compiled without automatic contraction, so each expression rounds the
+// same way wherever it is inlined.
 __device__ __forceinline__ double mdot(double ae, double ax, double ay, double az, double be, double bx,
                                        double by, double bz) {
-  return ae * be - ax * bx - ay * by - az * bz;
+  return fma(-az, bz, fma(-ay, by, fma(-ax, bx, ae * be)));
 }
 
 struct V4 {
   double e, x, y, z;
 };
 
-__device__ __forceinline__ double mdot(const V4& a, const V4& b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
+__device__ __forceinline__ double mdot(const V4& a, const V4& b) {
+  return fma(-a.z, b.z, fma(-a.y, b.y, fma(-a.x, b.x, a.e * b.e)));
+}
 
 __device__ __forceinline__ double det3(double a1, double a2, double a3, double b1, double b2, double b3,
                                        double c1, double c2, double c3) {
-  return a1 * (b2 * c3 - b3 * c2) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2 - b2 * c1);
+  const double m1 = fma(b2, c3, -(b3 * c2)), m2 = fma(b1, c3, -(b3 * c1)), m3 = fma(b1, c2, -(b2 * c1));
+  return fma(a3, m3, fma(-a2, m2, a1 * m1));
 }
 
 // Catani-Seymour final-final map for massless splitter a and spectator b:
@@ -409,8 +439,8 @@ __device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, d
     const V4 ref{1.0, r == 0 ? 1.0 : 0.0, r == 1 ? 1.0 : 0.0, r == 2 ? 1.0 : 0.0};
     const double cb = mdot(ref, b);
     const double ca = mdot(ref, a);
-    n1 = V4{ab - cb * a.e - ca * b.e, (r == 0 ? ab : 0.0) - cb * a.x - ca * b.x,
-            (r == 1 ? ab : 0.0) - cb * a.y - ca * b.y, (r == 2 ? ab : 0.0) - cb * a.z - ca * b.z};
+    n1 = V4{fma(-ca, b.e, fma(-cb, a.e, ab)), fma(-ca, b.x, fma(-cb, a.x, r == 0 ? ab : 0.0)),
+            fma(-ca, b.y, fma(-cb, a.y, r == 1 ? ab : 0.0)), fma(-ca, b.z, fma(-cb, a.z, r == 2 ? ab : 0.0))};
     if (fabs(mdot(n1, n1)) >= lim) break;
   }
   const double s1 = rsqrt(-mdot(n1, n1));
@@ -424,12 +454,12 @@ __device__ __forceinline__ void dipole_map(const V4& a, const V4& b, double z, d
   n2 = V4{n2.e * s2, n2.x * s2, n2.y * s2, n2.z * s2};
   const double kt = sqrt(z * (1.0 - z) * y * q2);
   const double kc = kt * cphi, ks = kt * sphi;
-  const V4 k{kc * n1.e + ks * n2.e, kc * n1.x + ks * n2.x, kc * n1.y + ks * n2.y, kc * n1.z + ks * n2.z};
+  const V4 k{fma(ks, n2.e, kc * n1.e), fma(ks, n2.x, kc * n1.x), fma(ks, n2.y, kc * n1.y), fma(ks, n2.z, kc * n1.z)};
   const double fa_i = z, fb_i = (1.0 - z) * y, fa_j = 1.0 - z, fb_j = z * y;
-  pi = V4{fa_i * a.e + fb_i * b.e + k.e, fa_i * a.x + fb_i * b.x + k.x, fa_i * a.y + fb_i * b.y + k.y,
-          fa_i * a.z + fb_i * b.z + k.z};
-  pj = V4{fa_j * a.e + fb_j * b.e - k.e, fa_j * a.x + fb_j * b.x - k.x, fa_j * a.y + fb_j * b.y - k.y,
-          fa_j * a.z + fb_j * b.z - k.z};
+  pi = V4{fma(fb_i, b.e, fa_i * a.e) + k.e, fma(fb_i, b.x, fa_i * a.x) + k.x, fma(fb_i, b.y, fa_i * a.y) + k.y,
+          fma(fb_i, b.z, fa_i * a.z) + k.z};
+  pj = V4{fma(fb_j, b.e, fa_j * a.e) - k.e, fma(fb_j, b.x, fa_j * a.x) - k.x, fma(fb_j, b.y, fa_j * a.y) - k.y,
+          fma(fb_j, b.z, fa_j * a.z) - k.z};
   const double r = 1.0 - y;
   pb = V4{r * b.e, r * b.x, r * b.y, r * b.z};
 }

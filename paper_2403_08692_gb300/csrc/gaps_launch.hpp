@@ -60,10 +60,14 @@ cudaError_t launch_shower_slice(const DevParams& P, const Events& E, const gaps_
                                 const int* list_in, int64_t n_in, const unsigned long long* n_in_dev,
                                 unsigned long long* cursor, int cycles, int* list_out, unsigned long long* out_count,
                                 cudaStream_t s);
-cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s);
+// The finalisation launchers visit positions 0 .. E.n - 1, mapped to events
+// by R (the identity by default; E's per-event arrays are then indexed by
+// the mapped event).
+cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s, const Ranges& R = Ranges{});
 // buckets: int32 scratch [769] (counts, offsets, cursors); order: int32
 // scratch [n_events].
-cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s);
+cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets, int* order, cudaStream_t s,
+                               const Ranges& R = Ranges{});
 // Make CUDA load the observables' kernels on the current device now (it
 // loads modules lazily by default, at their first use).
 cudaError_t preload_observables();
@@ -77,7 +81,12 @@ cudaError_t launch_histograms(const DevParams& P, const DevParams* scale_src, co
 // The exact fixed-point fills alone, added to acc (GAPS_HIST_FIXED_WORDS per
 // set, not cleared).
 cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, const Events& E, unsigned long long* acc,
-                              cudaStream_t s);
+                              cudaStream_t s, const Ranges& R = Ranges{});
+// Sets 0 .. n_sets - 1 of acc added to hist as doubles (set j at hist + j *
+// GAPS_HIST_DOUBLES; only sets with fills are touched).
+cudaError_t launch_hist_finalize(const DevParams& P, const DevParams* scale_src, const DevParams* jobs, int n_sets,
+                                 const unsigned long long* n_sets_dev, unsigned long long* acc, double* hist,
+                                 cudaStream_t s);
 cudaError_t launch_fill_job_of(uint16_t* job_of, const int64_t* begin, int n_jobs, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(const Events& E, gaps_stats* stats, cudaStream_t s);
 

@@ -22,9 +22,10 @@ __device__ __forceinline__ bool positive_finite_bits(double x) { return __double
 // momenta of the event's scale, so FP64 masslessness holds to ~eps E
 // sqrt(s)), 4 non-positive energy, 8 broken colour flow, 16 flavour
 // imbalance, 32 non-finite momentum.
-__global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
-  const int64_t ev = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (ev >= E.n) return;
+__global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges R) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= E.n) return;
+  const int64_t ev = R.event(t);
   const DevParams& P = params_of_event(P0, E, ev);
   const int n = E.n_partons[ev];
   int bits = 0;
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E) {
     sy += y;
     sz += z;
     if (!(finite_bits(e) ? positive_finite_bits(e) : e > 0.0)) bits |= 4;
-    if (fabs(e * e - x * x - y * y - z * z) > 1e-10 * e * P.sqrt_s) bits |= 2;
+    if (fabs(fma(-z, z, fma(-y, y, fma(-x, x, e * e)))) > 1e-10 * e * P.sqrt_s) bits |= 2;
     const int fl = E.flav[a];
     const int c = E.col[a], ac = E.acol[a];
     const int l0 = E.link[E.link_at(0, i, ev)], l1 = E.link[E.link_at(1, i, ev)];
@@ -177,7 +178,7 @@ __device__ __forceinline__ void add128(unsigned long long* acc, unsigned long lo
 // every event at its own job's scales.
 template <bool kJobs>
 __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams* scale_src, Events E,
-                                                    unsigned long long* acc) {
+                                                    unsigned long long* acc, Ranges R) {
   __shared__ unsigned long long sh[GAPS_HIST_FIXED_WORDS];
   __shared__ long long s_w[256], s_w2[256];
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
   const int64_t chunk = ((N + gridDim.x - 1) / gridDim.x + 31) & ~static_cast<int64_t>(31);
   const int64_t b0 = static_cast<int64_t>(blockIdx.x) * chunk;
   const int64_t b1 = b0 + chunk < N ? b0 + chunk : N;
-  const int home = kJobs && b0 < N ? static_cast<int>(E.job_of[b0]) : 0;
+  const int home = kJobs && b0 < N ? static_cast<int>(E.job_of[R.event(b0)]) : 0;
   double sc_w = P.hist_sw, sc_w2 = P.hist_sw2;
   if (!kJobs && scale_src) {
     sc_w = scale_src->hist_sw;
@@ -195,8 +196,9 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
   }
   // every lane of a warp runs the same iterations (the match needs them all)
   for (int64_t base = b0 + warp0; base < b1; base += blockDim.x) {
-    const int64_t ev = base + lane;
-    const bool fill = ev < b1 && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
+    const int64_t t = base + lane;
+    const int64_t ev = t < b1 ? R.event(t) : 0;
+    const bool fill = t < b1 && E.status[ev] == GAPS_DONE && E.valid[ev] == 0;
     const int job = kJobs && fill ? static_cast<int>(E.job_of[ev]) : home;
     if (kJobs && fill) {
       sc_w = E.jobs[job].hist_sw;
@@ -345,10 +347,10 @@ __global__ void __launch_bounds__(256) k_stats(Events E, gaps_stats* st) {
 
 }  // namespace
 
-cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s) {
+cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s, const Ranges& R) {
   if (E.n == 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
-  k_validate<<<blocks, 128, 0, s>>>(P, E);
+  k_validate<<<blocks, 128, 0, s>>>(P, E, R);
   return cudaGetLastError();
 }
 
@@ -359,7 +361,7 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s)
 #endif
 
 cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, const Events& E, unsigned long long* acc,
-                              cudaStream_t s) {
+                              cudaStream_t s, const Ranges& R) {
   if (E.n == 0) return cudaSuccess;
   int sms = 152;
   int dev = 0;
@@ -367,9 +369,9 @@ cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, co
   const int64_t want = (E.n + 255) / 256;
   const int64_t most = static_cast<int64_t>(GAPS_HIST_BLOCKS_PER_SM) * sms;
   if (E.jobs && E.job_of) {
-    k_hist_fixed<true><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, nullptr, E, acc);
+    k_hist_fixed<true><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, nullptr, E, acc, R);
   } else {
-    k_hist_fixed<false><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, scale_src, E, acc);
+    k_hist_fixed<false><<<static_cast<unsigned>(want < most ? want : most), 256, 0, s>>>(P, scale_src, E, acc, R);
   }
   return cudaGetLastError();
 }

@@ -14,9 +14,10 @@
 //   3. progress, read one round behind from pinned host memory (the live
 //      count and every job's finished-event count), so the GPU always has the
 //      next round queued while the host looks at the last one;
-//   4. a job whose events have all finished is finalised on its own range
-//      (validation, observables, its own histograms, copied to the host) and
-//      its range is reused at once, its slot once the copy has landed.
+//   4. the jobs whose events have all finished are finalised together on
+//      their ranges (validation, observables, each job's own histograms,
+//      copied to the host), and their ranges are reused at once, their slots
+//      once the copies have landed.
 // All arithmetic runs in the pool entry points (gaps_pool_*); this file keeps
 // only the schedule.  Every event equals the event a single-job batch of its
 // job produces (draws keyed by seed, event id and the event's own cycle), and
@@ -210,20 +211,30 @@ int read_round(gaps_server* s) {
   const int64_t active = static_cast<int64_t>(w[10 + f.cycle % 3] + w[18 + f.cycle % 3]);
   s->bound = active + (s->admitted_events - f.admitted_at_copy);
   const unsigned long long* done = w + gaps::kCounterWords;
-  for (auto it = s->live.begin(); it != s->live.end();) {
-    const int slot = it->first;
-    const Live& L = it->second;
+  // the jobs whose events have all finished, finalised together
+  std::vector<int32_t> slots;
+  std::vector<int64_t> begins, counts;
+  for (const auto& kv : s->live) {
+    const Live& L = kv.second;
     // a job admitted after this read was enqueued would see the finished
     // count of its slot's previous job
-    if (L.admitted_round > f.read_round || done[slot] < static_cast<unsigned long long>(L.job.n_events)) {
-      ++it;
-      continue;
-    }
-    double* h = s->hist_device + static_cast<size_t>(slot) * GAPS_HIST_DOUBLES;
-    e = cudaMemsetAsync(h, 0, GAPS_HIST_DOUBLES * sizeof(double), s->stream);
+    if (L.admitted_round > f.read_round || done[kv.first] < static_cast<unsigned long long>(L.job.n_events)) continue;
+    slots.push_back(kv.first);
+    begins.push_back(L.begin);
+    counts.push_back(L.job.n_events);
+  }
+  if (slots.empty()) return GAPS_OK;
+  for (int32_t slot : slots) {
+    e = cudaMemsetAsync(s->hist_device + static_cast<size_t>(slot) * GAPS_HIST_DOUBLES, 0,
+                        GAPS_HIST_DOUBLES * sizeof(double), s->stream);
     if (e != cudaSuccess) return fail(e);
-    const int rc = gaps_pool_finish(slot, L.begin, L.job.n_events, &s->pool, h, s->stream);
-    if (rc != GAPS_OK) return rc;
+  }
+  const int rc = gaps_pool_finish_jobs(slots.data(), begins.data(), counts.data(), static_cast<int32_t>(slots.size()),
+                                       &s->pool, s->hist_device, s->stream);
+  if (rc != GAPS_OK) return rc;
+  for (int32_t slot : slots) {
+    const Live& L = s->live.at(slot);
+    const double* h = s->hist_device + static_cast<size_t>(slot) * GAPS_HIST_DOUBLES;
     if (!s->staging[slot] && (e = cudaMallocHost(&s->staging[slot], GAPS_HIST_DOUBLES * sizeof(double))) != cudaSuccess)
       return fail(e);
     Completion c{nullptr, slot, L.job.id};
@@ -235,7 +246,7 @@ int read_round(gaps_server* s) {
     // the range is free for admissions queued after the calls above (same
     // stream); the slot once its histograms are on the host
     free_range(s, L.begin, L.job.n_events);
-    it = s->live.erase(it);
+    s->live.erase(slot);
   }
   return GAPS_OK;
 }

@@ -186,7 +186,7 @@ __device__ inline bool select_winner_fp64_range(const DevParams& P, const Events
           const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
           const double u = h ? to_unit(r.z, r.w) : to_unit(r.x, r.y);
           const double inv_c = combined ? inv_c_sum_fp64(P, d.zp, d.inv_ls) : inv_c_fp64(P, kind, d.zp, d.inv_ls);
-          const double lt = lnt + log_fp64(u) * inv_c;
+          const double lt = fma(log_fp64(u), inv_c, lnt);
           if (lt > best) {
             best = lt;
             code = (2 * i + side) * 8 + kappa;
@@ -232,8 +232,8 @@ __device__ __forceinline__ double veto_ratio_fp64(const DevParams& P, int kind, 
 // kernels 1 - z = z+ (z-/z+)^r, i.e. z = z- - z+ expm1(-r ln(z+/z-)).
 __device__ __forceinline__ double z_fp64(int kind, double zp, double lsoft, double r) {
   const double zm = 1.0 - zp;
-  if (kind == kGtoQQ) return zm + (zp - zm) * r;
-  return zm - zp * expm1(-r * lsoft);
+  if (kind == kGtoQQ) return fma(zp - zm, r, zm);
+  return fma(-zp, expm1(-r * lsoft), zm);
 }
 
 enum : int { kCycleVetoed = 0, kCycleFinished = 1, kCycleAccepted = 2 };
@@ -330,7 +330,7 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
           const float lg2u = __log2f(unit_float(whi, wlo));
           const float invc = combined ? inv_sum : (!gluon ? d.x * kInvCF2 : (kappa == 0 ? d.x * kInvCA : d.y));
           const float key = lg2u * invc;
-          const float m = kKeyRelInvc * invc + kKeyRelKey * fabsf(key);
+          const float m = fmaf(kKeyRelKey, fabsf(key), kKeyRelInvc * invc);
           ++sc.trials;
           if (key > sc.best_key) {
             sc.others_hi = fmaxf(sc.others_hi, sc.best_key + sc.best_m);
@@ -424,7 +424,7 @@ __device__ inline int cycle_screen(const DevParams& P, const Events& E, int64_t 
     const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
     const double zp = E.dzp[a], inv_ls = E.dinv[a];
     const double inv_c = combined ? inv_c_sum_fp64(P, zp, inv_ls) : inv_c_fp64(P, kind, zp, inv_ls);
-    const double lt = lnt + log_fp64(to_unit(best_hi, best_lo)) * inv_c;
+    const double lt = fma(log_fp64(to_unit(best_hi, best_lo)), inv_c, lnt);
     if (lt > P.ln_tc) {
       task.lnt = lt;
       task.q2 = E.dq2[a];

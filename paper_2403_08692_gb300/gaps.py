@@ -54,7 +54,7 @@ _LAYOUT_FIELDS = ["px", "py", "pz", "e", "flav", "col", "acol", "link", "dip", "
                   "n_dipoles", "next_colour", "me_flavour", "valid", "obs", "buckets", "order", "active", "tasks",
                   "counters",
                   "hist", "hist_fixed",
-                  "stats", "jobs", "job_begin", "job_of", "job_done", "total_bytes"]
+                  "stats", "jobs", "job_begin", "job_of", "job_done", "finish", "total_bytes"]
 
 
 MAX_JOBS = 1024
@@ -112,6 +112,8 @@ SIGNATURES = {
     "gaps_pool_cycles": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(Params), C.c_void_p]),
     "gaps_pool_slice": (C.c_int, [_P(Batch), C.c_int64, C.c_int32, C.c_int64, _P(PersistentConfig), _P(Params),
                                   C.c_void_p]),
+    "gaps_pool_finish_jobs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, _P(Batch), C.c_void_p,
+                                        C.c_void_p]),
     "gaps_pool_progress": (C.c_int, [_P(Batch), C.c_int64, _P(C.c_int64), C.c_void_p, C.c_void_p]),
     "gaps_pool_finish": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, _P(Batch), C.c_void_p, C.c_void_p]),
     "gaps_server_create": (C.c_int, [_P(Batch), C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(PersistentConfig),
@@ -456,6 +458,25 @@ def pool_progress(ws, cycle, job_done=None, stream=None):
     _check(load().gaps_pool_progress(C.byref(_batch(ws)), int(cycle), C.byref(active), ptr,
                                      _stream_handle(stream)), "gaps_pool_progress")
     return active.value
+
+
+def pool_finish_jobs(job_slots, ev_begins, n_events, ws, hist_device, stream=None):
+    """gaps_pool_finish_jobs: finalise several finished jobs at once; job i's
+    histograms are added to hist_device[job_slots[i]] (hist_device: MAX_JOBS x
+    HIST_DOUBLES or at least as many rows as the largest slot + 1)."""
+    import numpy as np
+    k = len(job_slots)
+    slots = np.ascontiguousarray(job_slots, dtype=np.int32)
+    begins = np.ascontiguousarray(ev_begins, dtype=np.int64)
+    counts = np.ascontiguousarray(n_events, dtype=np.int64)
+    if len(begins) != k or len(counts) != k:
+        raise ValueError("one begin and one count per job")
+    if k and int(slots.max()) >= hist_device.shape[0]:
+        raise ValueError("hist_device has no row for a job slot")
+    _check(load().gaps_pool_finish_jobs(C.c_void_p(slots.ctypes.data), C.c_void_p(begins.ctypes.data),
+                                        C.c_void_p(counts.ctypes.data), int(k), C.byref(_batch(ws)),
+                                        C.c_void_p(hist_device.data_ptr()), _stream_handle(stream)),
+           "gaps_pool_finish_jobs")
 
 
 def pool_finish(job_slot, ev_begin, n_events, ws, hist_device, stream=None):

@@ -12,7 +12,8 @@ per-block pools (mode "slice"), or a few launches of the plain form's step
 over the active list (mode "steps").  A job whose events
 have all reached the cutoff is finalised on its own range (validation,
 observables, its own histograms), its histograms go back to the host, and its
-range and slot are reused.
+range and slot are reused (the jobs that finish in the same round are
+finalised together, in one sequence of launches).
 
 All of the arithmetic runs in the library's kernels (gaps_pool_* in
 include/gaps.h); this module only keeps the schedule: the arrival queue, the
@@ -229,15 +230,22 @@ class Server:
         active = int(buf[10 + cycle % 3]) + int(buf[18 + cycle % 3])
         self.bound = active + (self.admitted_events - admitted_at_copy)
         done = buf[COUNTER_WORDS:].numpy()
-        for slot in list(self.live):
-            job, begin, admitted, admitted_round = self.live[slot]
-            # A job admitted after this read was enqueued would see the
-            # finished count of its slot's previous job.
-            if admitted_round > read_round or done[slot] < job.n_events:
-                continue
-            with torch.cuda.stream(self.stream):
+        # A job admitted after this read was enqueued would see the finished
+        # count of its slot's previous job.
+        finished = [slot for slot, (job, _, _, admitted_round) in self.live.items()
+                    if admitted_round <= read_round and done[slot] >= job.n_events]
+        if not finished:
+            return
+        with torch.cuda.stream(self.stream):
+            for slot in finished:
                 self.hist[slot].zero_()
-                self._gaps.pool_finish(slot, begin, job.n_events, self.ws, self.hist[slot], stream=self.stream)
+            # every job finished this round, finalised in one sequence of launches
+            self._gaps.pool_finish_jobs(finished, [self.live[k][1] for k in finished],
+                                        [self.live[k][0].n_events for k in finished], self.ws, self.hist,
+                                        stream=self.stream)
+        for slot in finished:
+            job, begin, admitted, _ = self.live[slot]
+            with torch.cuda.stream(self.stream):
                 if on_finish is not None:
                     on_finish(job, self.ws, begin, self.stream)
                 self.hist_host[slot].copy_(self.hist[slot], non_blocking=True)

@@ -149,3 +149,45 @@ def test_keyed_rounds_equal_general_rounds(g, mode, trial_mode):
     ev_alone, hist_alone = _alone(g, g.make_params(seed=s, trial_mode=trial_mode), n, first, 128)
     _assert_same_events(ek[1], ev_alone, 1)
     assert np.array_equal(hk[1], hist_alone)
+
+
+def test_finish_jobs_equals_finish_one_by_one(g):
+    """gaps_pool_finish_jobs over several finished jobs (disjoint ranges,
+    other live ranges between them) gives bitwise the validation bits,
+    observables and per-slot histograms of one gaps_pool_finish per job."""
+    import torch
+    specs = [(91.2, 1.0, 31, 3000, 0, 5), (200.0, 0.5, 32, 2500, 3500, 2), (133.0, 2.0, 33, 1, 7000, 9),
+             (91.2, 1.0, 34, 4000, 8000, 0)]  # (sqrt_s, t_C, seed, n, begin, slot)
+    ws = g.Workspace(20000, 128)
+    g.pool_reset(ws)
+    for rs, tc, seed, n, b, slot in specs:
+        g.pool_admit(g.make_params(sqrt_s=rs, t_cutoff=tc, seed=seed), slot, b, n, 0, ws, 0)
+    total = sum(sp[3] for sp in specs)
+    r = 0
+    while True:
+        g.pool_slice(ws, r, 16, total)
+        r += 1
+        if g.pool_progress(ws, r) == 0:
+            break
+    one = torch.zeros((g.MAX_JOBS, g.HIST_DOUBLES), dtype=torch.float64, device="cuda")
+    for rs, tc, seed, n, b, slot in specs:
+        g.pool_finish(slot, b, n, ws, one[slot])
+    torch.cuda.synchronize()
+    sc = ws.scalars()
+    valid1 = sc["valid"].clone()
+    obs1 = ws.obs().clone()
+    sc["valid"].fill_(-7)
+    ws.obs().fill_(-7.0)
+    both = torch.zeros_like(one)
+    g.pool_finish_jobs([sp[5] for sp in specs], [sp[4] for sp in specs], [sp[3] for sp in specs], ws, both)
+    torch.cuda.synchronize()
+    for rs, tc, seed, n, b, slot in specs:
+        assert torch.equal(sc["valid"][b:b + n], valid1[b:b + n]), slot
+        assert torch.equal(ws.obs()[:, b:b + n], obs1[:, b:b + n]), slot
+        assert torch.equal(both[slot], one[slot]), slot
+        assert float(both[slot].reshape(g.N_OBS, g.HIST_ROW, 3)[4, :, 2].sum()) > 0.0 or n == 1
+    untouched = [k for k in range(g.MAX_JOBS) if k not in {sp[5] for sp in specs}]
+    assert float(both[untouched].abs().sum()) == 0.0
+    # the events between the ranges were not visited
+    gap = sc["valid"][3000:3500]
+    assert bool((gap == -7).all())

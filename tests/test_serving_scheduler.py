@@ -100,6 +100,13 @@ class FakePool:
         self._check_shared(ws, shared)
         self._advance(ws, k, cycle + k)
 
+    def pool_finish_jobs(self, slots, begins, counts, ws, hist, stream=None):
+        assert len(set(slots)) == len(slots), "a slot finalised twice in one call"
+        spans = sorted((b, b + n) for b, n in zip(begins, counts))
+        assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:])), "overlapping ranges"
+        for slot, b, n in zip(slots, begins, counts):
+            self.pool_finish(slot, b, n, ws, hist[slot], stream)
+
     def pool_finish(self, slot, begin, n, ws, hist, stream=None):
         assert ws.jobs[slot][:2] == (begin, n)
         assert int(ws.job_done[slot]) == n, "finalised before all of its events finished"
