@@ -456,12 +456,17 @@ def main():
 
     STAGES = ("me", "shower", "validate", "observables", "histograms")
 
-    def step(marks=None):
-        # marks: CUDA events recorded after each stage (per-stage times)
+    def step(marks=None, kernel_times=False):
+        # marks: CUDA events recorded after each stage (per-stage times);
+        # kernel_times: time every step launch with its own events (a pass
+        # that does so runs a little slower, so the timed passes do not)
         g.generate_me(p, ws, stream)
         if marks:
             marks[0].record(stream)
-        rc, launches, kms = g.shower_timed(p, ws, g.SHOWER_PLAIN, stream)
+        if kernel_times:
+            rc, launches, kms = g.shower_timed(p, ws, g.SHOWER_PLAIN, stream)
+        else:
+            (rc, launches), kms = g.shower(p, ws, g.SHOWER_PLAIN, stream), 0.0
         if marks:
             marks[1].record(stream)
         g.validate(p, ws, stream)
@@ -505,11 +510,18 @@ def main():
             stage_ms[name].append(prev.elapsed_time(m))
             prev = m
         launches_total += launches
-        kernel_ms_total += kms
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     total_ms = sharding.job_time_ms(sum(step_ms), dist, dev)
+    # the step kernels' own time (for the roofline), from as many more passes
+    # with every launch bracketed by events
+    for _ in range(args.steps):
+        flush.zero_()
+        hist_dev.zero_()
+        torch.cuda.synchronize()
+        kernel_ms_total += step(kernel_times=True)[1]
+    torch.cuda.synchronize()
 
     # FP32-screen fallbacks of the last pass (cycles redone in FP64, vetoes
     # decided in FP64)

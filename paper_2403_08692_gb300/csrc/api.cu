@@ -513,7 +513,8 @@ int shower_impl(const gaps_params* params, const gaps_batch* batch, int mode, in
     if (kernel_ms_out && (err = cudaEventRecord(tev[2 * c + 1], s)) != cudaSuccess) return err;
     // While the list is long, put it back in event order (appends scatter
     // it); the same events, so its length stands.
-    if (bound * GAPS_REBUILD_DIV >= E.n && (err = launch_list_active(E, list_out, &E.counters[7], s)) != cudaSuccess)
+    if (bound * GAPS_REBUILD_DIV >= E.n &&
+        (err = launch_list_active(E, list_out, &E.counters[kListScratchWord], s)) != cudaSuccess)
       return err;
     return cudaSuccess;
   };

@@ -832,17 +832,13 @@ __global__ void __launch_bounds__(T) k_event_shapes_group(DevParams P, Events E,
   }
 }
 
-// Events of up to kThreadMax partons take one thread each in batches of at
-// least GAPS_SHAPES_GROUP_BELOW events (throughput), groups of
+// Events of up to 16 partons take one thread each in batches of at least
+// GAPS_SHAPES_GROUP_BELOW events (throughput), groups of
 // GAPS_SHAPES_SMALL_LANES lanes in smaller ones (a launch then waits for its
 // slowest event, not for the SMs).  At 10^6 LEP events one thread per event
 // up to 16 partons measured 1.04 ms for the observables, against 1.47 ms with
-// 9..16-parton events in groups of 8.
-#ifndef GAPS_SHAPES_THREAD_MAX
-#define GAPS_SHAPES_THREAD_MAX 16
-#endif
-constexpr int kThreadMax = GAPS_SHAPES_THREAD_MAX;
-static_assert(kThreadMax == 8 || kThreadMax == 16, "per-thread class of 8 or 16 partons");
+// 9..16-parton events in groups of 8 and 1.36 ms with the per-thread events
+// in two launches (up to 8 partons, 9..16).
 #ifndef GAPS_SHAPES_GROUP_BELOW
 #define GAPS_SHAPES_GROUP_BELOW 50000
 #endif
@@ -858,9 +854,8 @@ cudaError_t preload_observables() {
   cudaError_t e = cudaFuncGetAttributes(&a, k_bucket_count);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scan);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bucket_scatter);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<kThreadMax>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<kThreadMax, kSmallLanes, 128>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<16, 8, 128>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes<16>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<16, kSmallLanes, 128>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<32, 32, 128>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<64, 32, 128>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_event_shapes_group<128, 32, 128>);
@@ -893,13 +888,11 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
     const int64_t want = (E.n + per_block - 1) / per_block;
     return static_cast<unsigned>(want < static_cast<int64_t>(per_sm) * sms ? want : static_cast<int64_t>(per_sm) * sms);
   };
-  if (E.n < GAPS_SHAPES_GROUP_BELOW)
-    k_event_shapes_group<kThreadMax, kSmallLanes, 128>
-        <<<grid(128 / kSmallLanes, 8), 128, 0, s>>>(P, E, order, offsets, 0, kThreadMax);
-  else
-    k_event_shapes<kThreadMax><<<grid(kShapeThreads, 16), kShapeThreads, 0, s>>>(P, E, order, offsets, 0, kThreadMax);
-  if (kThreadMax < 16 && E.cap > 8)
-    k_event_shapes_group<16, 8, 128><<<grid(16, 8), 128, 0, s>>>(P, E, order, offsets, 9, 16);
+  if (E.n < GAPS_SHAPES_GROUP_BELOW) {
+    k_event_shapes_group<16, kSmallLanes, 128><<<grid(128 / kSmallLanes, 8), 128, 0, s>>>(P, E, order, offsets, 0, 16);
+  } else {
+    k_event_shapes<16><<<grid(kShapeThreads, 16), kShapeThreads, 0, s>>>(P, E, order, offsets, 0, 16);
+  }
   if (E.cap > 16) k_event_shapes_group<32, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 17, 32);
   if (E.cap > 32) k_event_shapes_group<64, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 33, 64);
   if (E.cap > 64) k_event_shapes_group<128, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 65, 128);

@@ -81,6 +81,8 @@ constexpr int kCounterWords = 32;
 constexpr int kPlainListWord = 21;
 constexpr int kPlainTaskWord = 24;
 constexpr int kRebuildWord = 27;
+// The plain form's list rebuild cursor (cleared by every step launch).
+constexpr int kListScratchWord = 7;
 constexpr int kSliceCursorWord = 28;
 // The deferred step's emission-task cursor, rotating like the lengths:
 // plain form words 29..31, serving pool words 13..15.

@@ -45,7 +45,8 @@ cudaError_t launch_step_deferred(const DevParams& P, const Events& E, const int*
                                  unsigned long long* reset_tasks, unsigned long long* emit_cursor,
                                  unsigned long long* reset_cursor, StepPublish pub, cudaStream_t s);
 // The active list of a batch rebuilt in event order (events with status
-// GAPS_ACTIVE); *count is a scratch counter.
+// GAPS_ACTIVE); *count is a scratch counter that must be zero (the step
+// launch before it clears counter word kListScratchWord).
 cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_append_range(int* list, unsigned long long* count, int64_t base, int64_t n, cudaStream_t s);
 cudaError_t launch_set_job(uint16_t* job_of, int64_t base, int64_t n, int job, cudaStream_t s);

@@ -30,9 +30,12 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
   const int n = E.n_partons[ev];
   int bits = 0;
   double se = 0, sx = 0, sy = 0, sz = 0;
-  int fsum[6] = {0, 0, 0, 0, 0, 0};
+  // quark minus antiquark count of flavour f at weight 256^f in one integer:
+  // with at most 255 partons every count is below 256 in magnitude, so the
+  // sum is zero exactly when every count is (a register, not an indexed
+  // array in local memory)
+  long long fsum = 0;
   bool colour_ok = true;
-  int n_quarks = 0;
   for (int i = 0; i < n; ++i) {
     const size_t a = E.at(i, ev);
     const double e = E.e[a], x = E.px[a], y = E.py[a], z = E.pz[a];
@@ -51,11 +54,10 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
       colour_ok &= c > 0 && ac > 0;
     } else if (fl >= 1 && fl <= 5) {
       colour_ok &= c > 0 && ac == 0;
-      fsum[fl] += 1;
-      ++n_quarks;
+      fsum += 1ll << (8 * fl);
     } else if (fl <= -1 && fl >= -5) {
       colour_ok &= c == 0 && ac > 0;
-      fsum[-fl] -= 1;
+      fsum -= 1ll << (-8 * fl);
     } else {
       colour_ok = false;
     }
@@ -100,9 +102,7 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
   }
   if (!colour_ok) bits |= 8;
   if (fabs(se - P.sqrt_s) > 1e-10 || fabs(sx) > 1e-10 || fabs(sy) > 1e-10 || fabs(sz) > 1e-10) bits |= 1;
-  for (int f = 1; f <= 5; ++f)
-    if (fsum[f] != 0) bits |= 16;
-  (void)n_quarks;
+  if (fsum != 0) bits |= 16;
   E.valid[ev] = bits;
 }
 
@@ -357,7 +357,7 @@ cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s,
 // Blocks per SM of the single-job histogram kernel: each block merges its
 // shared-memory histograms into the global ones at the end.
 #ifndef GAPS_HIST_BLOCKS_PER_SM
-#define GAPS_HIST_BLOCKS_PER_SM 2
+#define GAPS_HIST_BLOCKS_PER_SM 4
 #endif
 
 cudaError_t launch_hist_fixed(const DevParams& P, const DevParams* scale_src, const Events& E, unsigned long long* acc,

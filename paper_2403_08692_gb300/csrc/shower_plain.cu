@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) k_me(DevParams P0, Events E) {
 #endif
 constexpr int kStepThreads = GAPS_STEP_THREADS;
 
+
 // One veto cycle over the events list_in[0 .. n_in): the list holds the
 // active events only (the previous launch wrote it), so every thread of a
 // full block has an event to shower.  Without a list (the first cycle, or a
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid == 0) {
+    E.counters[kListScratchWord] = 0ull;  // the cursor of a list rebuild after this launch
     if (reset_list) *reset_list = 0ull;
     if (reset_tasks) *reset_tasks = 0ull;
     if (reset_cursor) *reset_cursor = 0ull;
@@ -493,8 +495,6 @@ __global__ void __launch_bounds__(256) k_set_job(uint16_t* job_of, int64_t base,
 
 cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s) {
   if (E.n <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
   k_list_active<<<static_cast<unsigned>((E.n + 255) / 256), 256, 0, s>>>(E, E.n, list, count);
   return cudaGetLastError();
 }
