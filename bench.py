@@ -81,20 +81,23 @@ def step_kernel_profile():
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if h.hexdigest() != want:
             return None
-        keys = ("dram_bytes_per_event_cycle", "fp64_pipe_active_frac", "issue_active_frac", "sm_active_frac")
+        keys = ("dram_bytes_per_event_cycle", "dram_bytes_per_event_cycle_warm", "fp64_pipe_active_frac",
+                "issue_active_frac", "sm_active_frac")
         return {k: float(re.search(k + r":\s*([0-9.]+)", text).group(1)) for k in keys}
     except (OSError, AttributeError, ValueError):
         return None
 
 
-def step_kernel_traffic(event_cycles_per_launch):
+def step_kernel_traffic(event_cycles_per_launch, warm=False):
     """DRAM bytes per launch of the plain-form step kernel: the per-event-cycle
     traffic of the committed ncu capture (all step launches of one pass at
-    10^5 events, the deferred emissions included) times this run's
+    10^5 events, the deferred emissions included; cold caches as ncu runs by
+    default, or warm: caches as the pass leaves them) times this run's
     event-cycles per launch; None once the kernel sources differ from the
     captured ones."""
     prof = step_kernel_profile()
-    return None if prof is None else prof["dram_bytes_per_event_cycle"] * event_cycles_per_launch
+    key = "dram_bytes_per_event_cycle_warm" if warm else "dram_bytes_per_event_cycle"
+    return None if prof is None else prof[key] * event_cycles_per_launch
 
 
 def pipe_fractions():
@@ -869,8 +872,11 @@ def main():
                      "dram_over_algorithmic": (None if step_kernel_traffic(1.0) is None else
                                                step_kernel_traffic(float(st.sum_steps)) / record_bytes),
                      "traffic": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass)),
+                     "traffic_warm": step_kernel_traffic(st.sum_steps / max(1.0, launches_per_pass), warm=True),
                      "traffic_source": "profiles/k_step_deferred_1e5.md: DRAM bytes per event-cycle from one ncu "
-                                       "capture x this run's event-cycles per launch",
+                                       "capture x this run's event-cycles per launch (traffic: caches flushed "
+                                       "before each launch, ncu's default; traffic_warm: caches as the pass "
+                                       "leaves them, which at 10^5 events hold most of the record)",
                      "pipes": pipe_fractions(),
                      "peak_source": f"FP64 unit count x clock: {DFMA_PER_SM_PER_CLOCK} DFMA/SM/clock x {sms} SMs "
                                     f"x {clock_mhz:.0f} MHz (median SM clock under load) x 2 flops; "

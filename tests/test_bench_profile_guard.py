@@ -35,6 +35,7 @@ def test_profile_figures_follow_the_source_hash(tmp_path):
     copy = tmp_path / "tree"
     shutil.copytree(os.path.join(ROOT, "profiles"), copy / "profiles")
     shutil.copytree(os.path.join(ROOT, "paper_2403_08692_gb300", "csrc"), copy / "paper_2403_08692_gb300" / "csrc")
+    shutil.copy(os.path.join(ROOT, "paper_2403_08692_gb300", "build.py"), copy / "paper_2403_08692_gb300" / "build.py")
     shutil.copy(os.path.join(ROOT, "bench.py"), copy / "bench.py")
     _stamp(str(copy))
     b = _bench_module(str(copy))
@@ -48,3 +49,10 @@ def test_profile_figures_follow_the_source_hash(tmp_path):
     src.write_text(src.read_text() + "\n// edited\n")
     assert b.step_kernel_profile() is None
     assert b.step_kernel_traffic(10.0) is None and b.pipe_fractions() is None
+    # and so does a change of the build flags
+    _stamp(str(copy))
+    assert b.step_kernel_profile() is not None
+    assert b.step_kernel_traffic(10.0, warm=True) == b.step_kernel_profile()["dram_bytes_per_event_cycle_warm"] * 10.0
+    flags = copy / "paper_2403_08692_gb300" / "build.py"
+    flags.write_text(flags.read_text().replace('"-fmad=false", ', ""))
+    assert b.step_kernel_profile() is None
