@@ -144,7 +144,7 @@ def parse():
                     help="oracle events for the CPU baseline on all host cores (about 10 s on 16 Grace cores; "
                          "one core gets 1/16 of them)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-variants", action="store_true", help="skip the persistent-form variants")
     ap.add_argument("--batched-events", type=int, default=10_000_000,
                     help="events of the batched persistent variant (0: skip it)")
@@ -812,6 +812,8 @@ def main():
     # end to end through the C ABI with host buffers: params in, histograms and
     # statistics out, every step
     host_hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64).pin_memory()
+    for _ in range(max(3, args.warmup)):  # the same warm-up as the device-timed passes
+        g.run(p, ws, host_hist, g.SHOWER_PLAIN, stream)
     e2e_times = []
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
