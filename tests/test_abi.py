@@ -103,3 +103,37 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(G._build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError):
         G.load(build_if_missing=False)
+
+
+def test_pool_calls_reject_bad_arguments_before_any_device_work(g):
+    """gaps_pool_finish_jobs checks its job list (slots in range and distinct,
+    ranges inside the pool and disjoint, array pointers) and gaps_pool_slice /
+    gaps_pool_cycles their shared parameters on the host, before any device
+    call: a bad list or bad parameters give GAPS_ERR_INVALID here, without a
+    GPU (the workspace pointer is never dereferenced)."""
+    L = g.load()
+    n, cap = 1000, 128
+    batch = g.gaps.Batch(C.c_void_p(1 << 20), n, cap, 0, 0, 0)  # aligned, never touched
+    hist = C.c_void_p(1 << 21)
+
+    def finish(slots, begins, counts, k=None):
+        S = (C.c_int32 * max(1, len(slots)))(*slots)
+        B = (C.c_int64 * max(1, len(begins)))(*begins)
+        N = (C.c_int64 * max(1, len(counts)))(*counts)
+        k = len(slots) if k is None else k
+        return L.gaps_pool_finish_jobs(C.cast(S, C.c_void_p), C.cast(B, C.c_void_p), C.cast(N, C.c_void_p), k,
+                                       C.byref(batch), hist, None)
+
+    INVALID = -1
+    assert finish([0, 0], [0, 100], [10, 10]) == INVALID            # one slot twice
+    assert finish([0, 1], [0, 5], [10, 10]) == INVALID              # overlapping ranges
+    assert finish([0], [995], [10]) == INVALID                      # past the pool's end
+    assert finish([0], [-1], [10]) == INVALID                       # negative begin
+    assert finish([0], [0], [-3]) == INVALID                        # negative count
+    assert finish([g.MAX_JOBS], [0], [10]) == INVALID               # slot out of range
+    assert finish([0], [0], [10], k=g.MAX_JOBS + 1) == INVALID      # too many jobs
+    assert L.gaps_pool_finish_jobs(None, None, None, 1, C.byref(batch), hist, None) == INVALID
+    assert finish([], [], [], k=0) == 0                             # nothing to do
+    bad = g.make_params(t_cutoff=0.0)
+    assert L.gaps_pool_slice(C.byref(batch), 0, 8, 10, None, C.byref(bad), None) == INVALID
+    assert L.gaps_pool_cycles(C.byref(batch), 0, 8, 10, C.byref(bad), None) == INVALID
