@@ -126,9 +126,10 @@ def dfma_equivalents(counts, rates, library_log=False):
 def kernels_outside_shower(capacity):
     """Library kernels per pass besides the shower cycles: matrix element,
     validation, the three bucketing kernels and one event-shape kernel per
-    multiplicity class (16, 32, 64, 128, 256 slots), histograms."""
+    multiplicity class (16, 32, 64, 128, 256 slots), the fixed-point
+    histogram fill and its conversion."""
     classes = sum(1 for lo in (0, 16, 32, 64, 128) if capacity > lo)
-    return 1 + 1 + 3 + classes + 1
+    return 1 + 1 + 3 + classes + 2
 
 
 def parse():

@@ -191,3 +191,34 @@ def test_finish_jobs_equals_finish_one_by_one(g):
     # the events between the ranges were not visited
     gap = sc["valid"][3000:3500]
     assert bool((gap == -7).all())
+
+
+def test_observables_thread_and_group_forms_agree(g):
+    """The observables of events of up to 16 partons run one thread per event
+    in large batches and in groups of lanes in small ones (a finished serving
+    round, one job): the same events give bitwise the same observables either
+    way (one finalisation over two 30 000-event ranges, against one per
+    range)."""
+    import torch
+    ws = g.Workspace(70000, 128)
+    g.pool_reset(ws)
+    specs = [(41, 30000, 0, 0), (42, 30000, 35000, 1)]  # seed, n, begin, slot
+    for seed, n, b, slot in specs:
+        g.pool_admit(g.make_params(seed=seed), slot, b, n, 0, ws, 0)
+    r = 0
+    while True:
+        g.pool_slice(ws, r, 32, 60000, None, shared=g.make_params(seed=41))
+        r += 1
+        if g.pool_progress(ws, r) == 0:
+            break
+    hist = torch.zeros((g.MAX_JOBS, g.HIST_DOUBLES), dtype=torch.float64, device="cuda")
+    g.pool_finish_jobs([sp[3] for sp in specs], [sp[2] for sp in specs], [sp[1] for sp in specs], ws, hist)
+    torch.cuda.synchronize()
+    together = ws.obs().clone()
+    ws.obs().fill_(-7.0)
+    for seed, n, b, slot in specs:
+        g.pool_finish_jobs([slot], [b], [n], ws, hist)  # 30 000 events: the lane-group form
+    torch.cuda.synchronize()
+    for seed, n, b, slot in specs:
+        assert torch.equal(ws.obs()[:, b:b + n], together[:, b:b + n]), slot
+    assert bool((ws.obs()[:, 30000:35000] == -7.0).all())
