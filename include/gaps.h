@@ -319,7 +319,8 @@ int gaps_pool_finish(int32_t job_slot, int64_t ev_begin, int64_t n_events, const
  * together pays that latency once.  Job i's histograms are added to
  * hist_device + job_slots[i] * GAPS_HIST_DOUBLES (not cleared).  job_slots,
  * ev_begins and n_events are host arrays, read before the call returns.
- * Asynchronous. */
+ * The list goes to a small table in the pool's workspace, so calls on one
+ * pool must be ordered (one stream), as all pool calls are.  Asynchronous. */
 int gaps_pool_finish_jobs(const int32_t* job_slots, const int64_t* ev_begins, const int64_t* n_events,
                           int32_t n_jobs, const gaps_batch* pool, double* hist_device, void* stream);
 
