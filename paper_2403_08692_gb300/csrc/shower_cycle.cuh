@@ -264,6 +264,7 @@ struct Screen {
   float best_key, best_m, others_hi;
   int best_code;  // (2 i + side) * 8 + kappa, -1: no trial
   uint32_t best_hi, best_lo;
+  uint32_t best_aux;  // the best trial's partner slot (bits 0-7) and gluon splitter (bit 8), as screened
   int trials, dipoles;
 };
 
@@ -273,6 +274,7 @@ __device__ __forceinline__ void screen_none(Screen& sc) {
   sc.others_hi = -INFINITY;
   sc.best_code = -1;
   sc.best_hi = sc.best_lo = 0;
+  sc.best_aux = 0;
   sc.trials = sc.dipoles = 0;
 }
 
@@ -339,6 +341,7 @@ __device__ __forceinline__ void screen_partons(const DevParams& P, const Events&
             sc.best_code = (2 * i + side) * 8 + kappa;
             sc.best_hi = whi;
             sc.best_lo = wlo;
+            sc.best_aux = static_cast<uint32_t>(side ? cur.link1 : cur.link0) | (gluon ? 256u : 0u);
           } else {
             sc.others_hi = fmaxf(sc.others_hi, key + m);
           }
@@ -364,6 +367,7 @@ __device__ __forceinline__ void screen_merge(Screen& sc, const Screen& o) {
     sc.best_code = o.best_code;
     sc.best_hi = o.best_hi;
     sc.best_lo = o.best_lo;
+    sc.best_aux = o.best_aux;
   }
   sc.trials += o.trials;
   sc.dipoles += o.dipoles;
@@ -382,6 +386,7 @@ __device__ __forceinline__ void screen_group_reduce(Screen& sc) {
     o.best_code = __shfl_xor_sync(0xffffffffu, sc.best_code, off);
     o.best_hi = __shfl_xor_sync(0xffffffffu, sc.best_hi, off);
     o.best_lo = __shfl_xor_sync(0xffffffffu, sc.best_lo, off);
+    o.best_aux = __shfl_xor_sync(0xffffffffu, sc.best_aux, off);
     o.trials = __shfl_xor_sync(0xffffffffu, sc.trials, off);
     o.dipoles = __shfl_xor_sync(0xffffffffu, sc.dipoles, off);
     screen_merge(sc, o);
@@ -419,7 +424,7 @@ __device__ inline int cycle_screen(const DevParams& P, const Events& E, int64_t 
     const int dcode = best_code >> 3, kappa = best_code & 7;
     const int i = dcode >> 1, side = dcode & 1;
     const size_t a = dip_at(E, side, i, ev);
-    const bool gluon = E.flav[E.at(i, ev)] == kGluon;
+    const bool gluon = (sc.best_aux & 256u) != 0u;  // as the screen read them: no second load
     const bool combined = gluon && per_dipole<kMode>(P);
     const int kind = combined ? kKindUnchosen : (gluon ? (kappa == 0 ? kGtoGG : kGtoQQ) : kQtoQG);
     const double zp = E.dzp[a], inv_ls = E.dinv[a];
@@ -431,7 +436,7 @@ __device__ inline int cycle_screen(const DevParams& P, const Events& E, int64_t 
       task.zp = zp;
       task.inv_ls = inv_ls;
       task.i = i;
-      task.k = E.link[E.link_at(side, i, ev)];
+      task.k = static_cast<uint8_t>(sc.best_aux & 255u);
       task.side = side;
       task.kappa = kappa;
       task.kind = kind;

@@ -34,6 +34,7 @@ __device__ __forceinline__ void screen_group_reduce_n(Screen& sc, int lanes) {
     o.best_code = __shfl_xor_sync(0xffffffffu, sc.best_code, off);
     o.best_hi = __shfl_xor_sync(0xffffffffu, sc.best_hi, off);
     o.best_lo = __shfl_xor_sync(0xffffffffu, sc.best_lo, off);
+    o.best_aux = __shfl_xor_sync(0xffffffffu, sc.best_aux, off);
     o.trials = __shfl_xor_sync(0xffffffffu, sc.trials, off);
     o.dipoles = __shfl_xor_sync(0xffffffffu, sc.dipoles, off);
     screen_merge(sc, o);
