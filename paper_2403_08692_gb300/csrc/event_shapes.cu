@@ -50,6 +50,33 @@ __device__ __forceinline__ double dot3(double ax, double ay, double az, double b
   return fma(az, bz, fma(ay, by, ax * bx));
 }
 __device__ __forceinline__ double cross(double a, double b, double c, double d) { return fma(a, b, -(c * d)); }
+// sqrt(x) of the observables' lengths (|p|, |P|, |p x n_T|) to 1.5e-13
+// relative: the FP32 reciprocal square root y0 = x^-1/2 (1 + e0) (two FP32
+// ulps, plus the rounding of x to FP32: |e0| < 2.5 2^-23) refined by one
+// Newton step in FP64, which leaves sqrt(x) (1 - 1.5 e0^2 + O(e0^3)) plus
+// the step's own roundings.  Three FP64 operations against the ten-FMA cost
+// of a correctly rounded FP64 square root on this part.  What it moves: T
+// by 3e-13 at most; on y_ij = 2 min(E^2) (1 - cos)/s the cosine by 3e-13
+// absolute, so y by 2 min(E^2)/s x 3e-13 <= 1.5e-13 absolute; B_T and B_W
+// by 3e-13 relative.  Zero, negative, non-finite and extreme x (outside
+// 2^-120 .. 2^120, where the FP32 seed would leave FP32's normal range)
+// take the library square root.
+__device__ __forceinline__ double sqrt_obs(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned ex = static_cast<unsigned>(b >> 52);  // sign and exponent field
+  if (ex < 1023u - 120u || ex > 1023u + 120u) return sqrt(x);
+  const unsigned y0f = __float_as_uint(rsqrtf(f32_from_f64(x)));
+  // y0 and y0 / 2 as doubles, assembled from the FP32 bits (positive normal
+  // floats: exponent rebiased by 1023 - 127, mantissa moved up 29 bits)
+  const unsigned long long man = static_cast<unsigned long long>(y0f & 0x7fffffu) << 29;
+  const unsigned long long e64 = static_cast<unsigned long long>((y0f >> 23) + 896u);
+  const double y0 = __longlong_as_double(static_cast<long long>((e64 << 52) | man));
+  const double y0h = __longlong_as_double(static_cast<long long>(((e64 - 1ull) << 52) | man));
+  const double h = x * y0;                  // sqrt(x) (1 + e0)
+  const double rh = fma(-h, y0h, 0.5);      // (1 - x y0^2) / 2
+  return fma(h, rh, h);
+}
+
 // The squared mass of a four-vector (e, x, y, z).
 __device__ __forceinline__ double mass2(const double* h) {
   return fma(-h[3], h[3], fma(-h[2], h[2], fma(-h[1], h[1], h[0] * h[0])));
@@ -92,13 +119,13 @@ __device__ double thrust_fp64(int n, const double* jx, const double* jy, const d
     }
   }
   if (best2 < 0.0) {  // collinear: T = 1 along the first momentum
-    const double l = sqrt(dot3(jx[0], jy[0], jz[0], jx[0], jy[0], jz[0]));
+    const double l = sqrt_obs(dot3(jx[0], jy[0], jz[0], jx[0], jy[0], jz[0]));
     ax = jx[0] / l;
     ay = jy[0] / l;
     az = jz[0] / l;
     return 1.0;
   }
-  const double l = sqrt(best2), inv_l = 1.0 / l;
+  const double l = sqrt_obs(best2), inv_l = 1.0 / l;
   ax = bx * inv_l;
   ay = by * inv_l;
   az = bz * inv_l;
@@ -142,7 +169,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     fx[i] = f32_from_f64(jx[i]);
     fy[i] = f32_from_f64(jy[i]);
     fz[i] = f32_from_f64(jz[i]);
-    ja[i] = sqrt(dot3(jx[i], jy[i], jz[i], jx[i], jy[i], jz[i]));
+    ja[i] = sqrt_obs(dot3(jx[i], jy[i], jz[i], jx[i], jy[i], jz[i]));
     sum_abs += ja[i];
   }
   sum_absf = f32_from_f64(sum_abs);
@@ -152,10 +179,10 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
   bool decided = false;
   if (n == 2) {
     // no emission: the pair is back to back, T = 1 along the quark
-    const double l = sqrt(dot3(jx[0], jy[0], jz[0], jx[0], jy[0], jz[0]));
-    ax = jx[0] / l;
-    ay = jy[0] / l;
-    az = jz[0] / l;
+    const double inv_l = 1.0 / ja[0];
+    ax = jx[0] * inv_l;
+    ay = jy[0] * inv_l;
+    az = jz[0] * inv_l;
     decided = true;
   } else if (n <= kMaskMax) {
     Top2 top;
@@ -205,7 +232,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
         py = fma(sg, jy[i], py);
         pz = fma(sg, jz[i], pz);
       }
-      const double l = sqrt(dot3(px, py, pz, px, py, pz)), inv_l = 1.0 / l;
+      const double l = sqrt_obs(dot3(px, py, pz, px, py, pz)), inv_l = 1.0 / l;
       thrust = l / sum_abs;
       ax = px * inv_l;
       ay = py * inv_l;
@@ -233,7 +260,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     h[2] += jy[i];
     h[3] += jz[i];
     const double cx = cross(jy[i], az, jz[i], ay), cy = cross(jz[i], ax, jx[i], az), cz = cross(jx[i], ay, jy[i], ax);
-    const double pt = sqrt(dot3(cx, cy, cz, cx, cy, cz));
+    const double pt = sqrt_obs(dot3(cx, cy, cz, cx, cy, cz));
     if (plus) {
       bp += pt;
     } else {
@@ -333,7 +360,7 @@ __device__ void event_shapes(const DevParams& P0, const Events& E, int64_t ev, i
     jy[bj] = jy[m - 1];
     jz[bj] = jz[m - 1];
     ja[bj] = ja[m - 1];
-    ja[bi] = sqrt(dot3(jx[bi], jy[bi], jz[bi], jx[bi], jy[bi], jz[bi]));
+    ja[bi] = sqrt_obs(dot3(jx[bi], jy[bi], jz[bi], jx[bi], jy[bi], jz[bi]));
     fe2[bj] = fe2[m - 1];
     fx[bj] = fx[m - 1];
     fy[bj] = fy[m - 1];
@@ -450,13 +477,13 @@ __device__ double thrust_fp64_group(int n, const GroupArrays<MAXJ>& a, double su
     }
   }
   if (best2 < 0.0) {  // collinear: T = 1 along the first momentum
-    const double l = sqrt(dot3(a.jx[0], a.jy[0], a.jz[0], a.jx[0], a.jy[0], a.jz[0]));
+    const double l = sqrt_obs(dot3(a.jx[0], a.jy[0], a.jz[0], a.jx[0], a.jy[0], a.jz[0]));
     ax = a.jx[0] / l;
     ay = a.jy[0] / l;
     az = a.jz[0] / l;
     return 1.0;
   }
-  const double l = sqrt(best2), inv_l = 1.0 / l;
+  const double l = sqrt_obs(best2), inv_l = 1.0 / l;
   ax = bx * inv_l;
   ay = by * inv_l;
   az = bz * inv_l;
@@ -483,7 +510,7 @@ __device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t
     a.fx[i] = f32_from_f64(x);
     a.fy[i] = f32_from_f64(y);
     a.fz[i] = f32_from_f64(z);
-    a.ja[i] = sqrt(dot3(x, y, z, x, y, z));
+    a.ja[i] = sqrt_obs(dot3(x, y, z, x, y, z));
   }
   __syncwarp(gm);
   double sum_abs = 0.0;
@@ -494,10 +521,10 @@ __device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t
   double thrust = 1.0, ax = 0.0, ay = 0.0, az = 0.0;
   bool decided = false;
   if (n == 2) {
-    const double l = sqrt(dot3(a.jx[0], a.jy[0], a.jz[0], a.jx[0], a.jy[0], a.jz[0]));
-    ax = a.jx[0] / l;
-    ay = a.jy[0] / l;
-    az = a.jz[0] / l;
+    const double inv_l = 1.0 / a.ja[0];
+    ax = a.jx[0] * inv_l;
+    ay = a.jy[0] * inv_l;
+    az = a.jz[0] * inv_l;
     decided = true;
   } else if (n <= kMaskMax) {
     Top2 top;
@@ -555,7 +582,7 @@ __device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t
         py = fma(sg, a.jy[i], py);
         pz = fma(sg, a.jz[i], pz);
       }
-      const double l = sqrt(dot3(px, py, pz, px, py, pz)), inv_l = 1.0 / l;
+      const double l = sqrt_obs(dot3(px, py, pz, px, py, pz)), inv_l = 1.0 / l;
       thrust = l / sum_abs;
       ax = px * inv_l;
       ay = py * inv_l;
@@ -579,7 +606,7 @@ __device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t
     h[2] += y;
     h[3] += z;
     const double cx = cross(y, az, z, ay), cy = cross(z, ax, x, az), cz = cross(x, ay, y, ax);
-    const double pt = sqrt(dot3(cx, cy, cz, cx, cy, cz));
+    const double pt = sqrt_obs(dot3(cx, cy, cz, cx, cy, cz));
     if (plus) {
       bp += pt;
     } else {
@@ -704,7 +731,7 @@ __device__ void event_shapes_group(const DevParams& P0, const Events& E, int64_t
       a.jy[bj] = a.jy[m - 1];
       a.jz[bj] = a.jz[m - 1];
       a.ja[bj] = a.ja[m - 1];
-      a.ja[bi] = sqrt(dot3(a.jx[bi], a.jy[bi], a.jz[bi], a.jx[bi], a.jy[bi], a.jz[bi]));
+      a.ja[bi] = sqrt_obs(dot3(a.jx[bi], a.jy[bi], a.jz[bi], a.jx[bi], a.jy[bi], a.jz[bi]));
       a.fe2[bj] = a.fe2[m - 1];
       a.fx[bj] = a.fx[m - 1];
       a.fy[bj] = a.fy[m - 1];

@@ -16,6 +16,34 @@ __device__ __forceinline__ bool finite_bits(double x) {
 }
 // x > 0 for a finite x
 __device__ __forceinline__ bool positive_finite_bits(double x) { return __double_as_longlong(x) > 0; }
+// Unbiased binary exponent of |x| read from its exponent field (-1023 for
+// zero and subnormals, 1024 for inf and NaN).
+__device__ __forceinline__ int exponent_bits(double x) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ffull) - 1023;
+}
+
+// The on-shell test |m2| > 1e-10 e sqrt(s), decided from exponents where
+// they settle it.  For normal e > 0 and sqrt(s) > 0 with unbiased exponents
+// u_e, u_s (1e-10 > 2^-34): while both rounded products stay normal
+// (u_e >= -988 and u_e + u_s >= -987), the bound (1e-10 e) sqrt(s) is at
+// least 2^(-34 + u_e + u_s) (1 - 2^-53)^2 > 2^(-35 + u_e + u_s); and
+// |m2| < 2^(u_m + 1).  So u_m <= u_e + u_s - 36 puts |m2| below the bound
+// (zero and subnormal m2 included; inf and NaN never pass).  An on-shell
+// massless parton has |m2| at rounding level, 2^(2 u_e - 50) or less, and
+// u_e <= u_s, so it passes; the rest take the FP64 test.  Saves two
+// multiplies and a compare on the FP64 pipe.  u_s is kNoExponent when
+// sqrt(s) is not a positive normal number: then every parton takes the FP64
+// test.
+constexpr int kNoExponent = -4096;
+__device__ __forceinline__ int normal_exponent(double x) {
+  const int u = exponent_bits(x);
+  return positive_finite_bits(x) && u > -1023 && u < 1024 ? u : kNoExponent;
+}
+__device__ __forceinline__ bool off_shell(double m2, double e, double sqrt_s, int u_s) {
+  const int u_e = normal_exponent(e);
+  if (u_e >= -988 && u_e + u_s >= -987 && exponent_bits(m2) <= u_e + u_s - 36) return false;
+  return fabs(m2) > 1e-10 * e * sqrt_s;
+}
 
 // One thread per event.  Bits: 1 momentum not conserved to 1e-10 GeV, 2 a
 // parton off shell (|p^2| > 1e-10 E sqrt(s): every component is formed from
@@ -36,6 +64,7 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
   // array in local memory)
   long long fsum = 0;
   bool colour_ok = true;
+  const int u_s = normal_exponent(P.sqrt_s);
   for (int i = 0; i < n; ++i) {
     const size_t a = E.at(i, ev);
     const double e = E.e[a], x = E.px[a], y = E.py[a], z = E.pz[a];
@@ -46,7 +75,7 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
     sy += y;
     sz += z;
     if (!(finite_bits(e) ? positive_finite_bits(e) : e > 0.0)) bits |= 4;
-    if (fabs(fma(-z, z, fma(-y, y, fma(-x, x, e * e)))) > 1e-10 * e * P.sqrt_s) bits |= 2;
+    if (off_shell(fma(-z, z, fma(-y, y, fma(-x, x, e * e))), e, P.sqrt_s, u_s)) bits |= 2;
     const int fl = E.flav[a];
     const int c = E.col[a], ac = E.acol[a];
     const int l0 = E.link[E.link_at(0, i, ev)], l1 = E.link[E.link_at(1, i, ev)];
@@ -128,6 +157,13 @@ __device__ __noinline__ int hist_bin_fp64(int h, double o) {
   return f < 0.0 ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
 }
 
+// o > 0.0 from the bits of o (false for NaN, true for +inf): the FP64
+// pipe's compare costs as much as an FMA on this part.
+__device__ __forceinline__ bool positive_bits(double o) {
+  const long long b = __double_as_longlong(o);
+  return b > 0 && b <= 0x7ff0000000000000ll;
+}
+
 // The same bin from an FP32 position: MUFU log2 and the FP32 conversion put
 // the position within 1e-4 bins of the FP64 one (|log10 y| <= 10 at 2e-6
 // absolute, times 25 bins per decade; 1-T and rho_H at 6e-8 relative, times
@@ -135,11 +171,16 @@ __device__ __noinline__ int hist_bin_fp64(int h, double o) {
 // in the FP64 formula's bin; the others take the FP64 formula.
 __device__ __forceinline__ int hist_bin(int h, double o) {
   float f;
+  const bool pos = positive_bits(o);
   if (h < 4) {
-    if (!(o > 0.0)) return -1;
+    if (!pos) return -1;
     f = (__log2f(f32_from_f64(o)) * 0.30102999566f + 4.3f) * 25.0f;
   } else {
-    f = (o > 0.0 ? f32_from_f64(o) : 0.0f) * (h < 6 ? 200.0f : 250.0f);
+    // zero (2-parton events) and negative values are the first bin's: the
+    // FP64 formula takes x = 0 to position 0 exactly, an edge the screen
+    // below would send to the FP64 formula for every such event
+    if (!pos) return 1;
+    f = f32_from_f64(o) * (h < 6 ? 200.0f : 250.0f);
   }
   const float fr = f - floorf(f);
   if (!(fr > 1e-3f && fr < 1.0f - 1e-3f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);
@@ -151,8 +192,9 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
 // the histograms do not depend on the order of the fills (and merge exactly
 // across batches or ranks): w is taken in units of 2^-k_w (w 2^k_w rounded
 // to an integer, |w 2^k_w| <= 2^62 for every weight the job's matrix element
-// can give) and w^2 in units of 2^-k_w2; each cell sums them as 128-bit
-// two's-complement integers (low word, high word) and counts its entries.
+// can give) and w^2 in units of 2^-k_w2; each cell of acc sums them as
+// 128-bit two's-complement integers (low word, high word) and counts its
+// entries.
 constexpr int kCells = GAPS_N_OBS * GAPS_HIST_ROW;
 
 // Add the signed 128-bit value (lo, hi) to the accumulator at acc[0..1]:
@@ -164,21 +206,36 @@ __device__ __forceinline__ void add128(unsigned long long* acc, unsigned long lo
   if (up != 0) atomicAdd(acc + 1, static_cast<unsigned long long>(up));
 }
 
+// A block's partial sums of one cell in shared memory take a fill value v
+// (|v| <= 2^62) as its low 32 bits (unsigned) and its high part v >> 32
+// (signed), summed in separate 64-bit words: v = hi 2^32 + lo, and neither
+// sum can overflow for fewer than 2^31 fills, so the adds need no carry and
+// no returned value (fire-and-forget shared-memory atomics).  The sum is put
+// back together as a 128-bit integer when the block merges into acc.
+__device__ __forceinline__ void split_sum_to128(unsigned long long lo_sum, long long hi_sum, unsigned long long* lo,
+                                                long long* hi) {
+  // hi_sum 2^32 = (hi_sum >> 32) 2^64 + (hi_sum mod 2^32) 2^32
+  const unsigned long long low = (static_cast<unsigned long long>(hi_sum) << 32) + lo_sum;
+  *hi = (hi_sum >> 32) + (low < lo_sum ? 1 : 0);
+  *lo = low;
+}
+
 // Every finished valid event fills each observable's bin.  The lanes of a
 // warp that fill the same cell are merged first (match on the cell; the
-// first lane sums its peers' fixed-point weights from shared memory as
-// 128-bit integers), so a crowded bin costs one atomic per warp, not one per
-// event.  Each block takes a contiguous chunk of events and accumulates the
-// fills of its first event's job (the home job) in shared memory, merged
-// into that job's set of acc (acc + job * GAPS_HIST_FIXED_WORDS) once per
-// block.  Single-job batch (kJobs false): every fill is the home job's, at
-// the scales of P, or of *scale_src (a job-table entry on the device) when
+// first lane sums its peers' split fixed-point weights from shared memory),
+// so a crowded bin costs one set of atomics per warp, not one per event.
+// Each block takes a contiguous chunk of events and accumulates the fills of
+// its first event's job (the home job) in shared memory (split form, above),
+// merged into that job's set of acc (acc + job * GAPS_HIST_FIXED_WORDS) once
+// per block.  Single-job batch (kJobs false): every fill is the home job's,
+// at the scales of P, or of *scale_src (a job-table entry on the device) when
 // it is given.  Multi-job batch: a job's events lie together, so nearly
-// every fill is the home job's; the others go to global memory directly;
-// every event at its own job's scales.
+// every fill is the home job's; the others go to acc directly as 128-bit
+// adds; every event at its own job's scales.
 template <bool kJobs>
 __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams* scale_src, Events E,
                                                     unsigned long long* acc, Ranges R) {
+  // per cell: sum lo(w), sum hi(w), sum lo(w^2), sum hi(w^2), entries
   __shared__ unsigned long long sh[GAPS_HIST_FIXED_WORDS];
   __shared__ long long s_w[256], s_w2[256];
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
@@ -204,13 +261,18 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
       sc_w = E.jobs[job].hist_sw;
       sc_w2 = E.jobs[job].hist_sw2;
     }
+    // the event's observables, all loads in flight at once
+    double o[GAPS_N_OBS];
+#pragma unroll
+    for (int h = 0; h < GAPS_N_OBS; ++h) o[h] = fill ? E.obs[h * E.stride + ev] : -1.0;
     const double w = fill ? E.weight[ev] : 0.0;
     // exact scalings by powers of two, then one rounding to an integer
     s_w[tid] = __double2ll_rn(w * sc_w);
     s_w2[tid] = __double2ll_rn((w * w) * sc_w2);
     __syncwarp();
+#pragma unroll 1
     for (int h = 0; h < GAPS_N_OBS; ++h) {
-      const int bin = fill ? hist_bin(h, E.obs[h * E.stride + ev]) : -1;
+      const int bin = fill ? hist_bin(h, o[h]) : -1;
       const int cell = bin < 0 ? -1 : job * kCells + h * GAPS_HIST_ROW + bin;
       const unsigned peers = __match_any_sync(0xffffffffu, cell);
       if (cell >= 0 && lane == __ffs(peers) - 1) {
@@ -219,18 +281,28 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
         for (unsigned m = peers; m; m &= m - 1) {
           const int l = __ffs(m) - 1;
           const long long a = s_w[warp0 + l], b = s_w2[warp0 + l];
-          const unsigned long long n1 = lo1 + static_cast<unsigned long long>(a);
-          hi1 += (a < 0 ? -1 : 0) + (n1 < lo1 ? 1 : 0);
-          lo1 = n1;
-          const unsigned long long n2 = lo2 + static_cast<unsigned long long>(b);
-          hi2 += (b < 0 ? -1 : 0) + (n2 < lo2 ? 1 : 0);
-          lo2 = n2;
+          lo1 += static_cast<unsigned long long>(a) & 0xffffffffull;
+          hi1 += a >> 32;
+          lo2 += static_cast<unsigned long long>(b) & 0xffffffffull;
+          hi2 += b >> 32;
         }
-        unsigned long long* c = job == home ? sh + static_cast<size_t>(cell - home * kCells) * 5
-                                            : acc + static_cast<size_t>(cell) * 5;
-        add128(c + 0, lo1, hi1);
-        add128(c + 2, lo2, hi2);
-        atomicAdd(c + 4, static_cast<unsigned long long>(__popc(peers)));
+        if (job == home) {
+          unsigned long long* c = sh + static_cast<size_t>(cell - home * kCells) * 5;
+          atomicAdd(c + 0, lo1);
+          atomicAdd(c + 1, static_cast<unsigned long long>(hi1));
+          atomicAdd(c + 2, lo2);
+          atomicAdd(c + 3, static_cast<unsigned long long>(hi2));
+          atomicAdd(c + 4, static_cast<unsigned long long>(__popc(peers)));
+        } else {
+          unsigned long long* c = acc + static_cast<size_t>(cell) * 5;
+          unsigned long long l128;
+          long long h128;
+          split_sum_to128(lo1, hi1, &l128, &h128);
+          add128(c + 0, l128, h128);
+          split_sum_to128(lo2, hi2, &l128, &h128);
+          add128(c + 2, l128, h128);
+          atomicAdd(c + 4, static_cast<unsigned long long>(__popc(peers)));
+        }
       }
     }
     __syncwarp();
@@ -241,8 +313,12 @@ __global__ void __launch_bounds__(256) k_hist_fixed(DevParams P, const DevParams
     const unsigned long long* c = sh + cell * 5;
     if (c[4] == 0ull) continue;
     unsigned long long* g = g_home + cell * 5;
-    add128(g + 0, c[0], static_cast<long long>(c[1]));
-    add128(g + 2, c[2], static_cast<long long>(c[3]));
+    unsigned long long l128;
+    long long h128;
+    split_sum_to128(c[0], static_cast<long long>(c[1]), &l128, &h128);
+    add128(g + 0, l128, h128);
+    split_sum_to128(c[2], static_cast<long long>(c[3]), &l128, &h128);
+    add128(g + 2, l128, h128);
     atomicAdd(g + 4, c[4]);
   }
 }

@@ -88,6 +88,18 @@ def _plant(case, mom, info, rng):
         info[quarks[0], 0] = f % 5 + 1
     elif case == "nan":
         mom[n - 1, 2] = np.nan
+    elif case == "near_shell":
+        # parton 0 given a small mass^2 m2 on either side of where the
+        # kernel's exponent screen of the on-shell test stops deciding
+        # (2^(u_e + u_s - 36)) and on either side of the bound 1e-10 E sqrt(s)
+        e0, p2 = mom[0, 0], float(np.dot(mom[0, 1:], mom[0, 1:]))
+        u = np.frexp(e0)[1] - 1 + np.frexp(91.2)[1] - 1
+        m2 = rng.choice([1.5 * 2.0 ** (u - 36), 1.99 * 2.0 ** (u - 36), 1.01 * 2.0 ** (u - 35),
+                         0.5e-10 * e0 * 91.2, 3e-10 * e0 * 91.2])
+        mom[0, 0] = np.sqrt(p2 + m2)
+    elif case == "tiny_energy":
+        # a subnormal energy: the bound underflows and the FP64 test decides
+        mom[0] = (1e-310, 0.0, 0.0, 0.0)
     elif case == "renumbered":
         # a valid record: every colour line renamed by one permutation
         lines = np.unique(info[:, 1:][info[:, 1:] > 0])
@@ -100,7 +112,7 @@ def _plant(case, mom, info, rng):
 
 
 CASES = ["clean", "offset", "off_shell", "negative_energy", "zero_energy", "swapped_colour", "dangling",
-         "gluon_loop", "flavour", "nan", "renumbered"]
+         "gluon_loop", "flavour", "nan", "renumbered", "near_shell", "tiny_energy"]
 
 
 def test_validate_bits_match_oracle_on_broken_records(g, oracle_mod):
@@ -149,5 +161,7 @@ def test_validate_bits_match_oracle_on_broken_records(g, oracle_mod):
     for c, b in expected_bit.items():
         assert np.all(by_case[c] & b), c
     assert np.all(by_case["renumbered"] == 0)
+    # the near-shell partons fall on both sides of the bound
+    assert np.any(by_case["near_shell"] & 2) and np.any((by_case["near_shell"] & 2) == 0)
     clean = [j for j in range(n_ev) if j not in planted]
     assert np.all(bits[clean] == 0)
