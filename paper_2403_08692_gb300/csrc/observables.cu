@@ -166,9 +166,12 @@ __device__ __forceinline__ bool positive_bits(double o) {
 
 // The same bin from an FP32 position: MUFU log2 and the FP32 conversion put
 // the position within 1e-4 bins of the FP64 one (|log10 y| <= 10 at 2e-6
-// absolute, times 25 bins per decade; 1-T and rho_H at 6e-8 relative, times
-// 200 bins per unit), so a position more than 1e-3 bins from every edge is
-// in the FP64 formula's bin; the others take the FP64 formula.
+// absolute, times 25 bins per decade, plus the FP32 roundings of the
+// position, each at most 4e-6 bins; the event shapes at 6e-8 relative, times
+// 250 bins per unit at most), so a position more than 2.5e-4 bins from every
+// edge is in the FP64 formula's bin; the others (about one value in 2000)
+// take the FP64 formula, and with it the whole warp, whose FP64 instructions
+// cost the same with one lane active as with 32.
 __device__ __forceinline__ int hist_bin(int h, double o) {
   float f;
   const bool pos = positive_bits(o);
@@ -183,7 +186,7 @@ __device__ __forceinline__ int hist_bin(int h, double o) {
     f = f32_from_f64(o) * (h < 6 ? 200.0f : 250.0f);
   }
   const float fr = f - floorf(f);
-  if (!(fr > 1e-3f && fr < 1.0f - 1e-3f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);
+  if (!(fr > 2.5e-4f && fr < 1.0f - 2.5e-4f) || !(fabsf(f) < 1e6f)) return hist_bin_fp64(h, o);
   return f < 0.0f ? 0 : (f >= GAPS_N_BINS ? GAPS_N_BINS + 1 : 1 + static_cast<int>(f));
 }
 

@@ -63,3 +63,53 @@ def test_histograms_are_order_free_and_exact(g):
     assert np.array_equal(entries, h1.reshape(-1, 3)[:, 2])
     assert entries.sum() > 3 * n  # most events fill most observables
     assert 30 < k_w < 62 and 0 < k_w2 < k_w
+
+
+def _host_bins(x, h):
+    """The FP64 bin formula (underflow 0, overflow 101, -1 undefined)."""
+    if h < 4:
+        ok = x > 0
+        v, lo, hi = np.log10(np.where(ok, x, 1.0)), -4.3, -0.3
+    else:
+        ok = np.ones_like(x, dtype=bool)
+        v, lo, hi = np.maximum(np.nan_to_num(x, nan=0.0, posinf=np.inf, neginf=0.0), 0.0), 0.0, (0.5 if h < 6 else 0.4)
+    f = (v - lo) / (hi - lo) * 100
+    b = np.where(f < 0, 0, np.where(f >= 100, 101, 1 + np.floor(np.clip(f, 0, 99.999999)).astype(int)))
+    return np.where(ok, b, -1)
+
+
+def test_bins_near_edges(g):
+    """Values placed just off every bin edge (1e-5 bins: decided by the FP64
+    formula; 3e-4 and 5e-4 bins: by the FP32 position) and the special
+    values (zero, negative, NaN, above the range) land in the FP64 formula's
+    bins."""
+    import torch
+    offsets = np.array([-5e-4, -3e-4, -1e-5, 1e-5, 3e-4, 5e-4])
+    pos = (np.arange(1, 100)[:, None] + offsets[None, :]).ravel()
+    special = np.array([0.0, -0.0, -1e-3, np.nan, 1e3, 0.25])
+    n = len(pos) + len(special)
+    p = g.make_params(seed=3)
+    ws = g.Workspace(n, 128)
+    sc = ws.scalars()
+    sc["status"].fill_(g.DONE)
+    sc["valid"].zero_()
+    rng = np.random.default_rng(2)
+    w = rng.uniform(0.5, 2.0, n)
+    sc["weight"].copy_(torch.from_numpy(w))
+    obs = np.empty((g.N_OBS, n))
+    for h in range(g.N_OBS):
+        if h < 4:
+            x = 10.0 ** (pos / 25.0 - 4.3)
+        else:
+            x = pos / (200.0 if h < 6 else 250.0)
+        obs[h] = np.concatenate([x, special])
+    ws.obs().copy_(torch.from_numpy(obs))
+    hist = torch.zeros(g.HIST_DOUBLES, dtype=torch.float64, device="cuda")
+    g.histograms(p, ws, hist)
+    torch.cuda.synchronize()
+    hh = hist.cpu().numpy().reshape(g.N_OBS, g.HIST_ROW, 3)
+    for h in range(g.N_OBS):
+        b = _host_bins(obs[h], h)
+        ok = b >= 0
+        assert np.array_equal(hh[h, :, 2], np.bincount(b[ok], minlength=g.HIST_ROW).astype(float)), h
+        np.testing.assert_allclose(hh[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=g.HIST_ROW), rtol=1e-12)
