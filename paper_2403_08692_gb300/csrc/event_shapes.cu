@@ -831,13 +831,17 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Events E, int* cursor, i
   }
 }
 
-// Events of buckets n_lo..n_hi (all with n <= MAXJ).
+// Events of buckets n_lo..n_hi (all with n <= MAXJ), the largest first: the
+// order list holds the buckets by rising multiplicity, and the threads take
+// it from its end, so the blocks with the costliest events start first and
+// the cheap ones fill the SMs that free up (a launch otherwise waits for the
+// blocks of its largest events, dealt out last).
 template <int MAXJ>
 __global__ void __launch_bounds__(kShapeThreads) k_event_shapes(DevParams P, Events E, const int* order,
                                                                 const int* offsets, int n_lo, int n_hi) {
   const int begin = offsets[n_lo], end = offsets[n_hi + 1 > 256 ? 256 : n_hi + 1];
-  for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end; k += gridDim.x * blockDim.x) {
-    const int64_t ev = order[k];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < end - begin; j += gridDim.x * blockDim.x) {
+    const int64_t ev = order[end - 1 - j];
     event_shapes<MAXJ>(P, E, ev, E.n_partons[ev]);
   }
 }
@@ -865,7 +869,15 @@ __global__ void __launch_bounds__(T) k_event_shapes_group(DevParams P, Events E,
 // slowest event, not for the SMs).  At 10^6 LEP events one thread per event
 // up to 16 partons measured 1.04 ms for the observables, against 1.47 ms with
 // 9..16-parton events in groups of 8 and 1.36 ms with the per-thread events
-// in two launches (up to 8 partons, 9..16).
+// in two launches (up to 8 partons, 9..16).  The per-thread grid holds one
+// thread per event up to GAPS_SHAPES_BLOCKS_PER_SM blocks per SM (largest
+// events first, above): 0.919 ms at 10^6 events and 0.623 ms at 5x10^5,
+// against 0.967 and 0.702 ms for 16 blocks per SM striding over the events
+// in rising size, and 1.168 and 0.726 ms for a grid of the resident blocks
+// only.
+#ifndef GAPS_SHAPES_BLOCKS_PER_SM
+#define GAPS_SHAPES_BLOCKS_PER_SM 64
+#endif
 #ifndef GAPS_SHAPES_GROUP_BELOW
 #define GAPS_SHAPES_GROUP_BELOW 50000
 #endif
@@ -918,7 +930,7 @@ cudaError_t launch_observables(const DevParams& P, const Events& E, int* buckets
   if (E.n < GAPS_SHAPES_GROUP_BELOW) {
     k_event_shapes_group<16, kSmallLanes, 128><<<grid(128 / kSmallLanes, 8), 128, 0, s>>>(P, E, order, offsets, 0, 16);
   } else {
-    k_event_shapes<16><<<grid(kShapeThreads, 16), kShapeThreads, 0, s>>>(P, E, order, offsets, 0, 16);
+    k_event_shapes<16><<<grid(kShapeThreads, GAPS_SHAPES_BLOCKS_PER_SM), kShapeThreads, 0, s>>>(P, E, order, offsets, 0, 16);
   }
   if (E.cap > 16) k_event_shapes_group<32, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 17, 32);
   if (E.cap > 32) k_event_shapes_group<64, 32, 128><<<grid(4, 2), 128, 0, s>>>(P, E, order, offsets, 33, 64);
