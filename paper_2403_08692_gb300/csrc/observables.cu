@@ -45,15 +45,12 @@ __device__ __forceinline__ bool off_shell(double m2, double e, double sqrt_s, in
   return fabs(m2) > 1e-10 * e * sqrt_s;
 }
 
-// One thread per event.  Bits: 1 momentum not conserved to 1e-10 GeV, 2 a
+// The validation bits of one event: 1 momentum not conserved to 1e-10 GeV, 2 a
 // parton off shell (|p^2| > 1e-10 E sqrt(s): every component is formed from
 // momenta of the event's scale, so FP64 masslessness holds to ~eps E
 // sqrt(s)), 4 non-positive energy, 8 broken colour flow, 16 flavour
 // imbalance, 32 non-finite momentum.
-__global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges R) {
-  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= E.n) return;
-  const int64_t ev = R.event(t);
+__device__ __forceinline__ void validate_event(const DevParams& P0, const Events& E, int64_t ev) {
   const DevParams& P = params_of_event(P0, E, ev);
   const int n = E.n_partons[ev];
   int bits = 0;
@@ -133,6 +130,58 @@ __global__ void __launch_bounds__(128) k_validate(DevParams P0, Events E, Ranges
   if (fabs(se - P.sqrt_s) > 1e-10 || fabs(sx) > 1e-10 || fabs(sy) > 1e-10 || fabs(sz) > 1e-10) bits |= 1;
   if (fsum != 0) bits |= 16;
   E.valid[ev] = bits;
+}
+
+// One thread per event.  A block first sorts its events by parton count
+// (a counting sort in shared memory), so that each warp holds events of
+// about one size: a warp's loop over partons lasts as long as its largest
+// event's, and on this part an FP64 instruction costs a warp the same issue
+// time with one lane active as with 32.  Every event is validated alone, so
+// the order changes nothing in the results.  At 10^6 events: 0.200 ms with
+// blocks of 128, 0.221 with 256, 0.275 with 512, against 0.249 ms unsorted.
+#ifndef GAPS_VALIDATE_THREADS
+#define GAPS_VALIDATE_THREADS 128
+#endif
+constexpr int kValidateThreads = GAPS_VALIDATE_THREADS;
+
+__global__ void __launch_bounds__(kValidateThreads) k_validate(DevParams P0, Events E, Ranges R) {
+  __shared__ int s_bin[256];  // counts per parton count, then the first slot of each
+  __shared__ int s_pos[kValidateThreads];
+  const int tid = threadIdx.x;
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * kValidateThreads;
+  const int64_t t = first + tid;
+  for (int b = tid; b < 256; b += kValidateThreads) s_bin[b] = 0;
+  __syncthreads();
+  int key = -1, rank = 0;
+  if (t < E.n) {
+    key = min(max(E.n_partons[R.event(t)], 0), 255);
+    rank = atomicAdd(&s_bin[key], 1);
+  }
+  __syncthreads();
+  if (tid < 32) {  // exclusive scan of the 256 counts: 8 per lane, then across the warp
+    int c[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c[k] = s_bin[tid * 8 + k];
+      sum += c[k];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      s_bin[tid * 8 + k] = run;
+      run += c[k];
+    }
+  }
+  __syncthreads();
+  if (key >= 0) s_pos[s_bin[key] + rank] = tid;
+  __syncthreads();
+  if (first + tid < E.n) validate_event(P0, E, R.event(first + s_pos[tid]));
 }
 
 // ---------------------------------------------------------- histograms
@@ -428,8 +477,8 @@ __global__ void __launch_bounds__(256) k_stats(Events E, gaps_stats* st) {
 
 cudaError_t launch_validate(const DevParams& P, const Events& E, cudaStream_t s, const Ranges& R) {
   if (E.n == 0) return cudaSuccess;
-  const unsigned blocks = static_cast<unsigned>((E.n + 127) / 128);
-  k_validate<<<blocks, 128, 0, s>>>(P, E, R);
+  const unsigned blocks = static_cast<unsigned>((E.n + kValidateThreads - 1) / kValidateThreads);
+  k_validate<<<blocks, kValidateThreads, 0, s>>>(P, E, R);
   return cudaGetLastError();
 }
 
