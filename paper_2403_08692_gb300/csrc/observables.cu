@@ -52,7 +52,9 @@ __device__ __forceinline__ bool off_shell(double m2, double e, double sqrt_s, in
 // imbalance, 32 non-finite momentum.
 __device__ __forceinline__ void validate_event(const DevParams& P0, const Events& E, int64_t ev) {
   const DevParams& P = params_of_event(P0, E, ev);
-  const int n = E.n_partons[ev];
+  // the record holds at most cap partons: a count outside 0..cap (a record
+  // written by hand through the workspace views) reads no slot beyond it
+  const int n = min(max(E.n_partons[ev], 0), E.cap);
   int bits = 0;
   double se = 0, sx = 0, sy = 0, sz = 0;
   // quark minus antiquark count of flavour f at weight 256^f in one integer:
