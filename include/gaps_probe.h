@@ -3,9 +3,9 @@
  *
  * Nothing here is part of the method: an FP64 throughput probe that the
  * benchmark uses to express the shower's FP64 work in DFMA-equivalents
- * measured on the same device, and host and device builds of two numerical
- * building blocks of the shower kernels (their FP64 logarithm and their
- * double -> float conversion) for the accuracy tests.  Return codes are the
+ * measured on the same device, and builds of numerical building blocks of
+ * the kernels (the shower's FP64 logarithm and double -> float conversion,
+ * the observables' square root) for the accuracy tests.  Return codes are the
  * gaps_status codes of gaps.h.
  */
 #ifndef GAPS_PROBE_H
@@ -38,6 +38,13 @@ int gaps_log_fp64_host(const double* x, double* y, int64_t n);
  * GAPS_ERR_INVALID for n < 0 or a null array with n > 0. */
 int gaps_f32_from_f64_host(const double* x, float* y, int64_t n);
 int gaps_log_fp64_device(const double* x, double* y, int64_t n, void* stream);
+/* The square root the observables kernels take of lengths (|p|, |P|,
+ * |p x n_T|, Sec. 3.1 observables): the FP32 reciprocal square root refined
+ * by one Newton step in FP64, 1.5e-13 relative for x in 2^-120 .. 2^121;
+ * other inputs take the CUDA library's sqrt.  y[i] = sqrt(x[i]) for
+ * 0 <= i < n, device arrays, asynchronous on `stream`; GAPS_ERR_INVALID for
+ * n < 0 or a null array with n > 0.  Exported for the accuracy tests. */
+int gaps_sqrt_obs_device(const double* x, double* y, int64_t n, void* stream);
 /* The CUDA error string of the last failed call of this library. */
 const char* gaps_probe_last_cuda_error(void);
 

@@ -12,7 +12,7 @@ from .gaps import (  # noqa: F401
     PersistentConfig, shower_persistent, autotune_persistent, Job, set_jobs, MAX_JOBS,
     GapsError, Params, Stats, Workspace, check_params, generate_me, histograms, layout, load, shower_timed,
     make_params, observables, reduce_stats, run, shower, shower_step, validate, workspace_bytes,
-    event_shapes_noalloc, probe_fp64_rates, log_fp64_host, log_fp64_device, f32_from_f64_host, TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE, pool_reset, pool_admit, pool_cycles, pool_slice, pool_progress,
+    event_shapes_noalloc, probe_fp64_rates, log_fp64_host, log_fp64_device, sqrt_obs_device, f32_from_f64_host, TRIALS_PER_KERNEL, TRIALS_PER_DIPOLE, pool_reset, pool_admit, pool_cycles, pool_slice, pool_progress,
     pool_finish, pool_finish_jobs, same_physics, LAYOUT_SOA, LAYOUT_TILE8, LAYOUT_TILE32, LAYOUT_NAMES, persistent_config, CServer, SERVE_SLICE, SERVE_STEPS, HIST_FIXED_WORDS, histograms_fixed, hist_fixed_scales, hist_fixed_to_double,
 )
 from .serving import RangeAllocator, ServeJob, ServeResult, Server, latency_summary  # noqa: F401

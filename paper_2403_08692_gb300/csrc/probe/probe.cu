@@ -15,6 +15,7 @@
 #include "gaps.h"
 #include "gaps_probe.h"
 #include "log_fp64.cuh"
+#include "sqrt_obs.cuh"
 
 namespace gaps {
 
@@ -136,6 +137,11 @@ __global__ void __launch_bounds__(256) k_log_fp64(const double* x, double* y, in
   if (k < n) y[k] = log_fp64(x[k]);
 }
 
+__global__ void __launch_bounds__(256) k_sqrt_obs(const double* x, double* y, int64_t n) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = sqrt_obs(x[k]);
+}
+
 }  // namespace
 }  // namespace gaps
 
@@ -160,3 +166,11 @@ extern "C" int gaps_log_fp64_device(const double* x, double* y, int64_t n, void*
 }
 
 extern "C" const char* gaps_probe_last_cuda_error(void) { return g_probe_error; }
+
+extern "C" int gaps_sqrt_obs_device(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return GAPS_ERR_INVALID;
+  if (n == 0) return GAPS_OK;
+  k_sqrt_obs<<<static_cast<unsigned>((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GAPS_OK : record_cuda_error(e);
+}

@@ -135,6 +135,7 @@ PROBE_SIGNATURES = {
     "gaps_log_fp64_host": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64]),
     "gaps_f32_from_f64_host": (C.c_int, [_P(C.c_double), _P(C.c_float), C.c_int64]),
     "gaps_log_fp64_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "gaps_sqrt_obs_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "gaps_probe_last_cuda_error": (C.c_char_p, []),
 }
 
@@ -386,6 +387,17 @@ def log_fp64_device(x, stream=None):
     y = torch.empty_like(x)
     _check_probe(load_probe().gaps_log_fp64_device(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                                    int(x.numel()), _stream_handle(stream)), "gaps_log_fp64_device")
+    return y
+
+
+def sqrt_obs_device(x, stream=None):
+    """The observables' Newton-refined square root on a contiguous float64
+    CUDA tensor."""
+    import torch
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check_probe(load_probe().gaps_sqrt_obs_device(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                   int(x.numel()), _stream_handle(stream)), "gaps_sqrt_obs_device")
     return y
 
 
