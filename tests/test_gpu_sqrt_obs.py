@@ -36,7 +36,8 @@ def test_relative_error_bound(g):
 def test_outside_the_refined_range(g):
     x = np.array([0.0, -0.0, -4.0, np.inf, np.nan, 5e-324, 1e-300, 2.0 ** -121, 2.0 ** 122, 1e300])
     y = g.sqrt_obs_device(torch.from_numpy(x).cuda()).cpu().numpy()
-    want = np.sqrt(x)
+    with np.errstate(invalid="ignore"):
+        want = np.sqrt(x)  # NaN for the negative input, as on the GPU
     same = (y == want) | (np.isnan(y) & np.isnan(want))
     assert np.all(same), (y, want)
     assert np.signbit(y[1])  # sqrt(-0) = -0
