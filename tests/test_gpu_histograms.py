@@ -82,7 +82,7 @@ def test_bins_near_edges(g):
     """Values placed just off every bin edge (1e-5 bins: decided by the FP64
     formula; 3e-4 and 5e-4 bins: by the FP32 position) and the special
     values (zero, negative, NaN, above the range) land in the FP64 formula's
-    bins."""
+    bins; signed weights sum exactly."""
     import torch
     offsets = np.array([-5e-4, -3e-4, -1e-5, 1e-5, 3e-4, 5e-4])
     pos = (np.arange(1, 100)[:, None] + offsets[None, :]).ravel()
@@ -94,7 +94,7 @@ def test_bins_near_edges(g):
     sc["status"].fill_(g.DONE)
     sc["valid"].zero_()
     rng = np.random.default_rng(2)
-    w = rng.uniform(0.5, 2.0, n)
+    w = rng.uniform(-2.0, 2.0, n)  # negative weights too: the fixed-point sums are signed
     sc["weight"].copy_(torch.from_numpy(w))
     obs = np.empty((g.N_OBS, n))
     for h in range(g.N_OBS):
@@ -112,4 +112,7 @@ def test_bins_near_edges(g):
         b = _host_bins(obs[h], h)
         ok = b >= 0
         assert np.array_equal(hh[h, :, 2], np.bincount(b[ok], minlength=g.HIST_ROW).astype(float)), h
-        np.testing.assert_allclose(hh[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=g.HIST_ROW), rtol=1e-12)
+        np.testing.assert_allclose(hh[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=g.HIST_ROW),
+                                   rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(hh[h, :, 1], np.bincount(b[ok], weights=w[ok] ** 2, minlength=g.HIST_ROW),
+                                   rtol=1e-12)
