@@ -92,11 +92,33 @@ constexpr int kPoolEmitCursorWord = 13;
 constexpr int kJobCountWord = 9;
 
 // The signed 128-bit fixed-point value (lo, hi) times scale_inv (= 2^-k) as
-// a double: hi 2^64 + lo, each part converted, their sum rounded once (the
-// power-of-two scalings are exact).  Host and device run the same code.
+// a double, rounded once to nearest even (the power-of-two scalings are
+// exact).  The magnitude is taken first (two's complement), so a small
+// negative sum does not cancel against 2^64; a magnitude of 64 bits or
+// fewer converts directly, a larger one as its leading 64 bits with every
+// lower bit folded into the last (a sticky bit: the conversion rounds 11
+// bits above it, so the rounding is that of the whole value).  Host and
+// device run the same code.
 __host__ __device__ inline double fixed128_to_double(unsigned long long lo, unsigned long long hi, double scale_inv) {
-  const double h = static_cast<double>(static_cast<long long>(hi)) * 18446744073709551616.0;
-  return (h + static_cast<double>(lo)) * scale_inv;
+  const bool neg = static_cast<long long>(hi) < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  double mag;
+  if (hi == 0ull) {
+    mag = static_cast<double>(lo);
+  } else {
+#ifdef __CUDA_ARCH__
+    const int bits = 64 - __clzll(static_cast<long long>(hi));  // 1 .. 63
+#else
+    const int bits = 64 - __builtin_clzll(hi);
+#endif
+    const unsigned long long top = (hi << (64 - bits)) | (lo >> bits);
+    const unsigned long long sticky = (lo << (64 - bits)) != 0ull ? 1ull : 0ull;
+    mag = static_cast<double>(top | sticky) * static_cast<double>(1ull << bits);
+  }
+  return (neg ? -mag : mag) * scale_inv;
 }
 
 // Pointers into the workspace (gaps_layout) for one batch.

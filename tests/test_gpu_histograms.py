@@ -3,6 +3,8 @@ same events give the same bits whatever the order of the fills -- two runs,
 the plain and the persistent forms, and two half-batches merged by 128-bit
 addition -- and the double histograms are the fixed-point sums converted
 once.  Requires a GB300."""
+import math
+
 import numpy as np
 import pytest
 
@@ -108,11 +110,23 @@ def test_bins_near_edges(g):
     g.histograms(p, ws, hist)
     torch.cuda.synchronize()
     hh = hist.cpu().numpy().reshape(g.N_OBS, g.HIST_ROW, 3)
+    # the exact expectation: every fill w 2^k_w (and w^2 2^k_w2) rounded to
+    # an integer (nearest, ties to even), summed exactly, converted once
+    k_w, k_w2 = g.hist_fixed_scales(p)
+    q1 = [int(v) for v in np.rint(w * 2.0 ** k_w)]
+    q2 = [int(v) for v in np.rint((w * w) * 2.0 ** k_w2)]
     for h in range(g.N_OBS):
         b = _host_bins(obs[h], h)
         ok = b >= 0
         assert np.array_equal(hh[h, :, 2], np.bincount(b[ok], minlength=g.HIST_ROW).astype(float)), h
+        s1 = [0] * g.HIST_ROW
+        s2 = [0] * g.HIST_ROW
+        for i in np.nonzero(ok)[0]:
+            s1[b[i]] += q1[i]
+            s2[b[i]] += q2[i]
+        want1 = np.array([math.ldexp(float(v), -k_w) for v in s1])
+        want2 = np.array([math.ldexp(float(v), -k_w2) for v in s2])
+        assert np.array_equal(hh[h, :, 0], want1), (h, np.nonzero(hh[h, :, 0] != want1)[0][:5])
+        assert np.array_equal(hh[h, :, 1], want2), h
         np.testing.assert_allclose(hh[h, :, 0], np.bincount(b[ok], weights=w[ok], minlength=g.HIST_ROW),
-                                   rtol=1e-12, atol=1e-12)
-        np.testing.assert_allclose(hh[h, :, 1], np.bincount(b[ok], weights=w[ok] ** 2, minlength=g.HIST_ROW),
-                                   rtol=1e-12)
+                                   rtol=1e-9, atol=64 * 2.0 ** -k_w)
