@@ -40,7 +40,7 @@ def _links(info, n):
     return link
 
 
-def _plant(case, mom, info, rng):
+def _plant(case, mom, info, rng, sqrt_s=91.2):
     """One defect of kind `case` in an event (mom [n][4], info [n][3]);
     returns False when the event cannot carry it."""
     n = len(mom)
@@ -93,9 +93,9 @@ def _plant(case, mom, info, rng):
         # kernel's exponent screen of the on-shell test stops deciding
         # (2^(u_e + u_s - 36)) and on either side of the bound 1e-10 E sqrt(s)
         e0, p2 = mom[0, 0], float(np.dot(mom[0, 1:], mom[0, 1:]))
-        u = np.frexp(e0)[1] - 1 + np.frexp(91.2)[1] - 1
+        u = np.frexp(e0)[1] - 1 + np.frexp(sqrt_s)[1] - 1
         m2 = rng.choice([1.5 * 2.0 ** (u - 36), 1.99 * 2.0 ** (u - 36), 1.01 * 2.0 ** (u - 35),
-                         0.5e-10 * e0 * 91.2, 3e-10 * e0 * 91.2])
+                         0.5e-10 * e0 * sqrt_s, 3e-10 * e0 * sqrt_s])
         mom[0, 0] = np.sqrt(p2 + m2)
     elif case == "tiny_energy":
         # a subnormal energy: the bound underflows and the FP64 test decides
@@ -115,10 +115,11 @@ CASES = ["clean", "offset", "off_shell", "negative_energy", "zero_energy", "swap
          "gluon_loop", "flavour", "nan", "renumbered", "near_shell", "tiny_energy"]
 
 
-def test_validate_bits_match_oracle_on_broken_records(g, oracle_mod):
+@pytest.mark.parametrize("sqrt_s", [91.2, 200.0])
+def test_validate_bits_match_oracle_on_broken_records(g, oracle_mod, sqrt_s):
     import torch
-    n_ev, cap, sqrt_s = 4000, 128, 91.2
-    p = g.make_params(seed=31)
+    n_ev, cap = 4000, 128
+    p = g.make_params(seed=31, sqrt_s=sqrt_s)
     ws = g.Workspace(n_ev, cap)
     g.generate_me(p, ws)
     g.shower(p, ws)
@@ -138,7 +139,7 @@ def test_validate_bits_match_oracle_on_broken_records(g, oracle_mod):
             continue
         k = npart[j]
         m, i = mom[:k, j].copy(), info[:k, j].copy()
-        if not _plant(case, m, i, rng):
+        if not _plant(case, m, i, rng, sqrt_s):
             continue
         mom[:k, j], info[:k, j] = m, i
         link[:, :k, j] = _links(i, k)
