@@ -443,7 +443,10 @@ int gaps_shower_step(const gaps_params* params, const gaps_batch* batch, void* s
 /* Validation of the finished record (the paper's "Validate Events" stage):
  * sets valid bits 1 momentum not conserved to 1e-10 GeV, 2 a parton off
  * shell (|p^2| > 1e-10 E sqrt(s)), 4 non-positive energy, 8 broken colour flow,
- * 16 flavour imbalance, 32 non-finite momentum.  Asynchronous. */
+ * 16 flavour imbalance, 32 non-finite momentum, for every event of the
+ * batch (whatever its status).  A parton count outside 0..capacity (a record
+ * edited through the workspace) is read as its nearest bound, so no slot
+ * beyond the capacity is touched.  Asynchronous. */
 int gaps_validate(const gaps_params* params, const gaps_batch* batch, void* stream);
 
 /* Sec. 3.1: Durham y23..y56 (E-scheme), thrust 1-T (exact), heavy-jet mass
