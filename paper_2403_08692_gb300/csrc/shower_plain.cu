@@ -335,17 +335,38 @@ __global__ void __launch_bounds__(kStepThreads, GAPS_STEP_MIN_BLOCKS)
 // The active list rebuilt in event order: the events of [0, n) with status
 // GAPS_ACTIVE (live and without a pending emission), each block's in order,
 // one atomic per block.  Appends scatter a warp's events over the batch as
-// the cycles go by; in event order a warp's events sit in one window of 256,
-// so its loads of the slot-major record coalesce again.
+// the cycles go by; in event order a warp's events sit in one window of a
+// block's events, so its loads of the slot-major record coalesce again.
+// Each thread takes four consecutive events (one 16-byte load of their
+// statuses where the array allows it), a block of 256 threads 1024 events.
 __global__ void __launch_bounds__(256) k_list_active(Events E, int64_t n, int* list, unsigned long long* count) {
   __shared__ int s_warp[8];
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t ev = static_cast<int64_t>(blockIdx.x) * 256 + tid;
-  const bool live = ev < n && E.status[ev] == GAPS_ACTIVE;
+  const int64_t ev0 = (static_cast<int64_t>(blockIdx.x) * 256 + tid) * 4;
+  int st[4] = {-1, -1, -1, -1};
+  if (ev0 + 3 < n && (reinterpret_cast<uintptr_t>(E.status) & 15u) == 0u) {
+    const int4 v = *reinterpret_cast<const int4*>(E.status + ev0);
+    st[0] = v.x;
+    st[1] = v.y;
+    st[2] = v.z;
+    st[3] = v.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (ev0 + k < n) st[k] = E.status[ev0 + k];
+  }
   if (blockIdx.x == 0 && tid == 0) atomicAdd(&E.counters[kRebuildWord], 1ull);  // launches of this kernel
-  const unsigned mask = __ballot_sync(0xffffffffu, live);
-  if (lane == 0) s_warp[warp] = __popc(mask);
+  int mine = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mine += st[k] == GAPS_ACTIVE ? 1 : 0;
+  int incl = mine;  // inclusive scan of the live counts over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   if (tid == 0) {
     int run = 0;
@@ -357,7 +378,10 @@ __global__ void __launch_bounds__(256) k_list_active(Events E, int64_t n, int* l
     s_base = run ? atomicAdd(count, static_cast<unsigned long long>(run)) : 0ull;
   }
   __syncthreads();
-  if (live) list[s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(ev);
+  unsigned long long at = s_base + static_cast<unsigned long long>(s_warp[warp] + incl - mine);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (st[k] == GAPS_ACTIVE) list[at++] = static_cast<int>(ev0 + k);
 }
 
 }  // namespace
@@ -495,7 +519,7 @@ __global__ void __launch_bounds__(256) k_set_job(uint16_t* job_of, int64_t base,
 
 cudaError_t launch_list_active(const Events& E, int* list, unsigned long long* count, cudaStream_t s) {
   if (E.n <= 0) return cudaSuccess;
-  k_list_active<<<static_cast<unsigned>((E.n + 255) / 256), 256, 0, s>>>(E, E.n, list, count);
+  k_list_active<<<static_cast<unsigned>((E.n + 1023) / 1024), 256, 0, s>>>(E, E.n, list, count);
   return cudaGetLastError();
 }
 
