@@ -53,3 +53,30 @@ def test_conversion_rounds_once(g):
         assert out[c, 0] == math.ldexp(float(v), -k_w), (c, v, out[c, 0])
         assert out[c, 1] == math.ldexp(float(v), -k_w2), (c, v)
         assert out[c, 2] == 1.0
+
+
+def test_rank_merge_is_exact_for_signed_sums(g):
+    """sharding.add_fixed (the ranks' merge) adds the words as 128-bit
+    two's-complement integers, so signed partial sums combine exactly and in
+    any order; the merged set converts like the exact sum."""
+    from paper_2403_08692_gb300 import sharding
+    p = g.make_params(seed=1)
+    k_w, _ = g.hist_fixed_scales(p)
+    rng = np.random.default_rng(9)
+    cells = g.N_OBS * g.HIST_ROW
+    a_vals = [int(x) * (1 << 30) + int(y) for x, y in zip(rng.integers(-(1 << 62), 1 << 62, cells),
+                                                          rng.integers(0, 1 << 30, cells))]
+    b_vals = [-v + int(d) for v, d in zip(a_vals, rng.integers(-1000, 1000, cells))]  # near cancellation
+    acc_a = np.zeros(g.HIST_FIXED_WORDS, dtype=np.uint64)
+    acc_b = np.zeros(g.HIST_FIXED_WORDS, dtype=np.uint64)
+    for c in range(cells):
+        for acc, v in ((acc_a, a_vals[c]), (acc_b, b_vals[c])):
+            lo, hi = _words(v)
+            acc[5 * c], acc[5 * c + 1], acc[5 * c + 2], acc[5 * c + 3], acc[5 * c + 4] = lo, hi, lo, hi, 1
+    ab = sharding.add_fixed(acc_a, acc_b)
+    assert np.array_equal(ab, sharding.add_fixed(acc_b, acc_a))
+    out = g.hist_fixed_to_double(p, ab).reshape(-1, 3)
+    for c in range(cells):
+        lo, hi = _words(a_vals[c] + b_vals[c])
+        assert int(ab[5 * c]) == lo and int(ab[5 * c + 1]) == hi and int(ab[5 * c + 4]) == 2
+        assert out[c, 0] == math.ldexp(float(a_vals[c] + b_vals[c]), -k_w)
